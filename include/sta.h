@@ -1,0 +1,185 @@
+/*
+ * libsta: STA-FEM exact streaming assembly of the linear-elasticity stiffness matrix over a
+ * fixed, preallocated superset tetrahedral mesh, on one CUDA GPU (sm_103a).
+ *
+ * The library maintains  A_t = sum_{tau in T_t} P_tau^T K^(tau) P_tau + eps I   (STA-FEM,
+ * arXiv 2605.11673, Sec. 3.4, Eq. 8) for the active set T_t of a superset mesh, under a
+ * per-frame stream of tetrahedron edits (Sec. 3.2: deleted set Delta^-, added set Delta^+;
+ * Sec. 3.3: fracture/merge toggle existing tets, refinement activates preallocated children
+ * and deactivates their parents).  Invariant (Sec. 3.3): after every call the values equal a
+ * from-scratch rebuild on the current active set -- here bit for bit.
+ *
+ * Conventions shared by every call:
+ *  - Return value: STA_OK (0) or a negative STA_E* code; sta_last_error() gives a message
+ *    for the calling thread.  All argument and edit validation happens on the host before
+ *    any device work, and a rejected call changes no state.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Device
+ *    work is enqueued on it; calls return before it finishes unless stated otherwise.
+ *  - Host arrays passed in are copied; the caller keeps ownership.  Device pointers handed
+ *    out by sta_csr / sta_scatter_map are owned by the context and valid until sta_destroy.
+ *  - Matrix layout: scalar CSR with 3n rows, DOF 3v + i (node v, component i).  Row 3a+i
+ *    holds, for every node b sharing at least one SUPERSET tetrahedron with node a (a
+ *    included), in ascending b, the three columns 3b, 3b+1, 3b+2.  The pattern is fixed at
+ *    create; entries with no active contributor hold +0.0.  Indices are int32 (STA_ERANGE
+ *    when they would overflow).
+ *  - Summation order: each value is the left-to-right fold, from +0.0, of the contributions
+ *    of its active tetrahedra in ascending tetrahedron id; eps is added to diagonal entries
+ *    afterwards.  Element matrices follow the fixed evaluation order documented with
+ *    sta_element_matrices.  Results are therefore deterministic and independent of launch
+ *    configuration.
+ */
+#ifndef STA_H
+#define STA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sta_ctx sta_ctx;
+
+enum {
+    STA_OK = 0,
+    STA_EINVAL = -1, /* bad argument, bad mesh, bad edit list */
+    STA_ESTATE = -2, /* call not valid in the context's current state */
+    STA_ERANGE = -3, /* a count or index would overflow int32 */
+    STA_ENOMEM = -4, /* device or pinned host allocation failed */
+    STA_ECUDA = -5   /* a CUDA runtime call or kernel failed */
+};
+
+/* Edit operations (Sec. 3.2 Delta^-, Delta^+; Algorithm 1 "receive edit sets"). */
+enum { STA_DEACTIVATE = 0, STA_ACTIVATE = 1, STA_SWAP = 2 };
+
+/* One edit.  DEACTIVATE: tet leaves the active set (fracture, coarsening parent...).
+ * ACTIVATE: tet joins it (merge, refinement child...).  SWAP: tet leaves and tet2 joins
+ * (e.g. a connected tetrahedron replaced by its preallocated split copy).  tet2 is ignored
+ * unless op == STA_SWAP.  Within one call every tetrahedron may appear at most once. */
+typedef struct {
+    int32_t op;
+    int32_t tet;
+    int32_t tet2;
+} sta_edit;
+
+typedef struct {
+    double eps;             /* eps of Eq. 4 / Eq. 8, added to diagonal entries; default 0 */
+    int32_t block_threads;  /* threads per CTA of the fold kernels; 0 = built-in default */
+    int32_t blocks_per_sm;  /* CTAs per SM of the persistent fold grid; 0 = occupancy max */
+} sta_options;
+
+/* Fills defaults (eps 0, launch shape from the built-in table). */
+void sta_default_options(sta_options *opt);
+
+/*
+ * sta_create -- set up a context for one superset mesh (Sec. 3, "three inputs": superset
+ * vertex positions V, candidate pool of tetrahedra; Algorithm 1 inputs V, T).
+ *  nodes   host, n_nodes x 3 doubles (x, y, z per node)
+ *  tets    host, n_tets x 4 int32 node ids; ids in [0, n_nodes), distinct per tetrahedron,
+ *          positively oriented (det[x1-x0, x2-x0, x3-x0] > 0)
+ *  young, poisson  host, n_tets doubles each (isotropic material per tetrahedron)
+ *  opt     may be NULL (defaults)
+ * Builds on the device, once: the superset CSR pattern (row_ptr, col), the tet-to-nnz
+ * scatter map (P_tau of Eq. 8 as indices), the per-block contributor lists in ascending
+ * tetrahedron id, and the element-matrix cache of every superset tetrahedron.  The initial
+ * active set is empty and all values are +0.0; call sta_full_rebuild with the initial mask
+ * (Algorithm 1 "a_0").  Synchronises `stream`.  Errors: STA_EINVAL for a bad id, a repeated
+ * node or a tetrahedron with det <= 0 (its index is in sta_last_error()); STA_ERANGE when
+ * nnz or 16 * n_tets exceeds int32; STA_ENOMEM; STA_ECUDA.
+ */
+int sta_create(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
+               const double *young, const double *poisson, const sta_options *opt,
+               void *stream, sta_ctx **out);
+
+/* Releases all device and host memory of the context (synchronises its last stream). */
+int sta_destroy(sta_ctx *ctx);
+
+/*
+ * sta_full_rebuild -- the full_rebuild policy (Sec. 3.5): set the active mask and recompute
+ * every value of the pattern from scratch from the element cache.
+ *  mask            n_tets bytes, nonzero = active; host memory if mask_on_device == 0,
+ *                  else device memory
+ * With a device mask the host mirror used for edit validation is refreshed by a
+ * device-to-host copy, which synchronises `stream`.
+ */
+int sta_full_rebuild(sta_ctx *ctx, const uint8_t *mask, int mask_on_device, void *stream);
+
+/*
+ * sta_apply_edits -- one frame of the streaming update (Sec. 3.2; Algorithm 1 receive /
+ * update mask / per-tet update; Sec. 3.5 local_recompute made bitwise): applies the edits to
+ * the mask, marks every block of the pattern touched by an edited tetrahedron (its 16 node
+ * pairs, 144 entries), and re-folds exactly those entries over their active contributors in
+ * the same canonical order as sta_full_rebuild, so the result is bit-identical to a rebuild.
+ *  edits   host array of n_edits sta_edit, validated against the host mirror of the mask:
+ *          op in {0,1,2}; ids in range; DEACTIVATE needs an active tet, ACTIVATE an
+ *          inactive one, SWAP an active tet and an inactive tet2; no tetrahedron twice.
+ *          On a bad edit nothing changes and STA_EINVAL is returned with its index.
+ * n_edits == 0 is a valid no-op frame.
+ */
+int sta_apply_edits(sta_ctx *ctx, const sta_edit *edits, int64_t n_edits, void *stream);
+
+/* Number of distinct CSR entries re-folded by the last sta_apply_edits (= 9 x touched node
+ * pairs).  Reads a device counter: synchronises `stream`. */
+int sta_last_touched(sta_ctx *ctx, int64_t *touched_nnz, void *stream);
+
+/* Device pointers of the CSR arrays (owned by the context; pattern fixed for its lifetime).
+ * row_ptr: n_rows + 1 int32; col: nnz int32; val: nnz doubles.  Any out-pointer may be
+ * NULL. */
+int sta_csr(const sta_ctx *ctx, const int32_t **row_ptr, const int32_t **col,
+            const double **val, int64_t *n_rows, int64_t *nnz);
+
+/* Device pointer to the scatter map, n_tets x 144 int32: scat[t][12p + q] is the CSR index
+ * of the global entry (3 v_a + i, 3 v_b + j) for local p = 3a + i, q = 3b + j -- the
+ * injection P_tau of Eq. 8 written as indices. */
+int sta_scatter_map(const sta_ctx *ctx, const int32_t **scat);
+
+/* Sizes: nodes, tets, node-pair blocks (nnz / 9), and device bytes held by the context. */
+int sta_sizes(const sta_ctx *ctx, int64_t *n_nodes, int64_t *n_tets, int64_t *n_blocks,
+              int64_t *device_bytes);
+
+/* Device pointer to the current active mask (n_tets bytes, 0/1), owned by the context. */
+int sta_mask(const sta_ctx *ctx, const uint8_t **mask);
+
+/*
+ * sta_recompute_elements -- recompute the element-matrix cache (the element part of the
+ * paper's full_rebuild, Sec. 3.5), for active tetrahedra only (active_only != 0) or for the
+ * whole superset.  Element matrix K^(tau) (Sec. 3.4, Sec. 5.2: standard linear-tetrahedron
+ * elasticity), fixed evaluation order:
+ *   d_k = x_k - x_0;  c_1 = d_2 x d_3, c_2 = d_3 x d_1, c_3 = d_1 x d_2 with
+ *   (u x v).x = fma(u.y, v.z, -(u.z v.y)) and cyclic;  det = fma(d1.z, c1.z, fma(d1.y, c1.y,
+ *   d1.x c1.x));  r = 1/det;  g_k = c_k r;  g_0 = -((g_1 + g_2) + g_3);  V = det / 6;
+ *   lam = (E nu) / ((1 + nu)(1 - (nu + nu)));  mu = E / ((1 + nu) + (1 + nu));
+ *   P_a = (V lam) g_a;  Q_a = (V mu) g_a;  D_ab = (V mu) fma(g_a.z, g_b.z, fma(g_a.y, g_b.y,
+ *   g_a.x g_b.x));  for p = 3a+i <= q = 3b+j:  K = fma(P_a[i], g_b[j], Q_a[j] g_b[i]) if
+ *   i != j, else fma(P_a[i], g_b[i], fma(Q_a[i], g_b[i], D_ab));  K[q][p] = K[p][q].
+ * All other operations are separately rounded IEEE double operations.
+ */
+int sta_recompute_elements(sta_ctx *ctx, int active_only, void *stream);
+
+/*
+ * sta_set_params -- replace node positions and/or materials (any pointer may be NULL to
+ * keep the current values) and recompute the element cache of the whole superset.  Arrays
+ * are host memory unless on_device != 0 (then device memory of the same layout: nodes n x 3
+ * doubles, young/poisson n_tets doubles).  Values are NOT re-folded: call
+ * sta_full_rebuild afterwards.  Tetrahedra with det <= 0 make the call fail with STA_EINVAL
+ * after the copy (synchronises `stream`); the context then holds the new parameters.
+ */
+int sta_set_params(sta_ctx *ctx, const double *nodes, const double *young,
+                   const double *poisson, int on_device, void *stream);
+
+/*
+ * sta_element_matrices -- expand the cached element matrices of n tetrahedra to full 12x12
+ * row-major doubles.  tet_ids: device, n int32 (each in range, checked on the device:
+ * out-of-range ids give zero matrices); out: device, n x 144 doubles.
+ */
+int sta_element_matrices(sta_ctx *ctx, const int32_t *tet_ids, int64_t n, double *out,
+                         void *stream);
+
+/* Human-readable message of the last error on the calling thread. */
+const char *sta_last_error(void);
+const char *sta_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STA_H */

@@ -19,7 +19,7 @@ import numpy as np
 
 _HERE = Path(__file__).resolve().parent
 _SRC = _HERE / "sta_oracle.c"
-_LIB = _HERE / "_build" / "libsta_oracle.so"
+_LIB = _HERE / "_build" / "liboracle_fem.so"
 _lib = None
 
 _i64, _f64, _p = C.c_int64, C.c_double, C.c_void_p

@@ -1,0 +1,304 @@
+"""Python binding of libsta (STA-FEM exact streaming assembly on one GB300).
+
+Argument marshalling only: every step of the assembly runs in the CUDA library
+(``_build/libsta.so``, built by ``paper_2605_11673_gb300.build``).  There is no CPU or
+PyTorch fallback: if the library is missing, importing the binding raises.
+
+The functions ``sta_*`` mirror the C-ABI of include/sta.h one to one; ``Assembler`` is a
+small convenience wrapper around them.  PyTorch is used for device memory of user-side
+tensors and for streams (``stream`` arguments accept a ``torch.cuda.Stream``, a raw
+``cudaStream_t`` integer, or None for the current torch stream).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "_build" / "libsta.so"
+
+STA_OK, STA_EINVAL, STA_ESTATE, STA_ERANGE, STA_ENOMEM, STA_ECUDA = 0, -1, -2, -3, -4, -5
+STA_DEACTIVATE, STA_ACTIVATE, STA_SWAP = 0, 1, 2
+
+# Every symbol declared in include/sta.h.
+EXPORTED = (
+    "sta_default_options", "sta_create", "sta_destroy", "sta_full_rebuild", "sta_apply_edits",
+    "sta_last_touched", "sta_csr", "sta_scatter_map", "sta_sizes", "sta_mask",
+    "sta_recompute_elements", "sta_set_params", "sta_element_matrices", "sta_last_error",
+    "sta_status_string",
+)
+
+
+class StaError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"libsta status {status}: {message}")
+        self.status = status
+
+
+class sta_options(C.Structure):
+    _fields_ = [("eps", C.c_double), ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32)]
+
+
+class sta_edit(C.Structure):
+    _fields_ = [("op", C.c_int32), ("tet", C.c_int32), ("tet2", C.c_int32)]
+
+
+_lib = None
+_p, _i64, _int = C.c_void_p, C.c_int64, C.c_int
+_P = C.POINTER
+
+
+def load_library(path: Path | str | None = None):
+    """Load libsta.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = Path(path) if path else LIB_PATH
+    if not path.exists():
+        raise ImportError(f"libsta not built: {path} is missing "
+                          "(run `python -m paper_2605_11673_gb300.build`)")
+    L = C.CDLL(str(path))
+    L.sta_default_options.argtypes = [_P(sta_options)]
+    L.sta_default_options.restype = None
+    L.sta_create.argtypes = [_p, _i64, _p, _i64, _p, _p, _P(sta_options), _p, _P(_p)]
+    L.sta_destroy.argtypes = [_p]
+    L.sta_full_rebuild.argtypes = [_p, _p, _int, _p]
+    L.sta_apply_edits.argtypes = [_p, _p, _i64, _p]
+    L.sta_last_touched.argtypes = [_p, _P(_i64), _p]
+    L.sta_csr.argtypes = [_p, _P(_p), _P(_p), _P(_p), _P(_i64), _P(_i64)]
+    L.sta_scatter_map.argtypes = [_p, _P(_p)]
+    L.sta_sizes.argtypes = [_p, _P(_i64), _P(_i64), _P(_i64), _P(_i64)]
+    L.sta_mask.argtypes = [_p, _P(_p)]
+    L.sta_recompute_elements.argtypes = [_p, _int, _p]
+    L.sta_set_params.argtypes = [_p, _p, _p, _p, _int, _p]
+    L.sta_element_matrices.argtypes = [_p, _p, _i64, _p, _p]
+    L.sta_last_error.restype = C.c_char_p
+    L.sta_status_string.argtypes = [_int]
+    L.sta_status_string.restype = C.c_char_p
+    for name in EXPORTED:
+        if name not in ("sta_default_options", "sta_last_error", "sta_status_string"):
+            getattr(L, name).restype = _int
+    _lib = L
+    return L
+
+
+def _check(status: int) -> None:
+    if status != STA_OK:
+        raise StaError(status, load_library().sta_last_error().decode())
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        if not torch.cuda.is_available():
+            return 0
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class DeviceArray:
+    """Zero-copy view of context-owned device memory (``__cuda_array_interface__``)."""
+
+    def __init__(self, ptr: int, shape, typestr: str, owner):
+        self._ptr, self._shape, self._typestr, self._owner = int(ptr), tuple(shape), typestr, owner
+
+    @property
+    def __cuda_array_interface__(self):
+        return {"shape": self._shape, "typestr": self._typestr, "data": (self._ptr, False),
+                "version": 3, "strides": None}
+
+    def torch(self):
+        import torch
+        return torch.as_tensor(self, device="cuda")
+
+
+# ----------------------------------------------------------------------------------------
+# One-to-one wrappers of the C-ABI
+# ----------------------------------------------------------------------------------------
+
+def sta_default_options() -> sta_options:
+    o = sta_options()
+    load_library().sta_default_options(C.byref(o))
+    return o
+
+
+def sta_create(nodes, tets, young, poisson, opt: sta_options | None = None, stream=None) -> int:
+    L = load_library()
+    nodes = _host(nodes, np.float64).reshape(-1, 3)
+    tets = _host(tets, np.int32).reshape(-1, 4)
+    young = _host(young, np.float64).reshape(-1)
+    poisson = _host(poisson, np.float64).reshape(-1)
+    if young.shape[0] != tets.shape[0] or poisson.shape[0] != tets.shape[0]:
+        raise ValueError("young/poisson must have one value per tetrahedron")
+    h = _p()
+    _check(L.sta_create(nodes.ctypes.data, nodes.shape[0], tets.ctypes.data, tets.shape[0],
+                        young.ctypes.data, poisson.ctypes.data,
+                        C.byref(opt) if opt is not None else None, _stream_handle(stream),
+                        C.byref(h)))
+    return h.value
+
+
+def sta_destroy(h: int) -> None:
+    _check(load_library().sta_destroy(h))
+
+
+def sta_full_rebuild(h: int, mask, stream=None) -> None:
+    """mask: numpy/host array (copied by the library) or a CUDA tensor (device path)."""
+    L = load_library()
+    if hasattr(mask, "is_cuda") and mask.is_cuda:
+        m = mask.contiguous()
+        _check(L.sta_full_rebuild(h, m.data_ptr(), 1, _stream_handle(stream)))
+    else:
+        m = _host(mask, np.uint8)
+        _check(L.sta_full_rebuild(h, m.ctypes.data, 0, _stream_handle(stream)))
+
+
+def sta_apply_edits(h: int, edits, stream=None) -> None:
+    """edits: (m, 3) int32 rows (op, tet, tet2) in host memory."""
+    e = _host(edits, np.int32).reshape(-1, 3)
+    _check(load_library().sta_apply_edits(h, e.ctypes.data if e.shape[0] else None, e.shape[0],
+                                          _stream_handle(stream)))
+
+
+def sta_last_touched(h: int, stream=None) -> int:
+    v = _i64()
+    _check(load_library().sta_last_touched(h, C.byref(v), _stream_handle(stream)))
+    return int(v.value)
+
+
+def sta_sizes(h: int) -> dict:
+    n, T, nb, by = _i64(), _i64(), _i64(), _i64()
+    _check(load_library().sta_sizes(h, C.byref(n), C.byref(T), C.byref(nb), C.byref(by)))
+    return {"n_nodes": n.value, "n_tets": T.value, "n_blocks": nb.value, "nnz": 9 * nb.value,
+            "device_bytes": by.value}
+
+
+def sta_csr(h: int, owner=None):
+    """(row_ptr, col, val) as zero-copy DeviceArrays over context memory."""
+    rp, cl, vl = _p(), _p(), _p()
+    nr, nz = _i64(), _i64()
+    _check(load_library().sta_csr(h, C.byref(rp), C.byref(cl), C.byref(vl), C.byref(nr),
+                                  C.byref(nz)))
+    return (DeviceArray(rp.value or 0, (nr.value + 1,), "<i4", owner),
+            DeviceArray(cl.value or 0, (nz.value,), "<i4", owner),
+            DeviceArray(vl.value or 0, (nz.value,), "<f8", owner))
+
+
+def sta_scatter_map(h: int, owner=None):
+    p = _p()
+    _check(load_library().sta_scatter_map(h, C.byref(p)))
+    T = sta_sizes(h)["n_tets"]
+    return DeviceArray(p.value or 0, (T, 144), "<i4", owner)
+
+
+def sta_mask(h: int, owner=None):
+    p = _p()
+    _check(load_library().sta_mask(h, C.byref(p)))
+    T = sta_sizes(h)["n_tets"]
+    return DeviceArray(p.value or 0, (T,), "|u1", owner)
+
+
+def sta_recompute_elements(h: int, active_only: bool = False, stream=None) -> None:
+    _check(load_library().sta_recompute_elements(h, 1 if active_only else 0,
+                                                 _stream_handle(stream)))
+
+
+def sta_set_params(h: int, nodes=None, young=None, poisson=None, stream=None) -> None:
+    """Host (numpy) arrays, or CUDA tensors (then all given arrays must be on the device)."""
+    arrs = [a for a in (nodes, young, poisson) if a is not None]
+    on_dev = bool(arrs) and all(hasattr(a, "is_cuda") and a.is_cuda for a in arrs)
+    keep = []
+
+    def ptr(a):
+        if a is None:
+            return None
+        if on_dev:
+            a = a.contiguous()
+            keep.append(a)
+            return a.data_ptr()
+        a = _host(a, np.float64)
+        keep.append(a)
+        return a.ctypes.data
+
+    _check(load_library().sta_set_params(h, ptr(nodes), ptr(young), ptr(poisson),
+                                         1 if on_dev else 0, _stream_handle(stream)))
+
+
+def sta_element_matrices(h: int, tet_ids, stream=None):
+    """Full 12x12 element matrices of the given tetrahedra, as a CUDA tensor (n, 12, 12)."""
+    import torch
+    ids = torch.as_tensor(tet_ids, dtype=torch.int32, device="cuda").contiguous()
+    out = torch.empty((ids.numel(), 12, 12), dtype=torch.float64, device="cuda")
+    _check(load_library().sta_element_matrices(h, ids.data_ptr(), ids.numel(), out.data_ptr(),
+                                               _stream_handle(stream)))
+    return out
+
+
+# ----------------------------------------------------------------------------------------
+# Convenience wrapper
+# ----------------------------------------------------------------------------------------
+
+class Assembler:
+    """One superset mesh on the device: pattern, element cache, active mask and values."""
+
+    def __init__(self, X, tets, E, nu, eps: float = 0.0, block_threads: int = 0,
+                 blocks_per_sm: int = 0, stream=None):
+        o = sta_default_options()
+        o.eps, o.block_threads, o.blocks_per_sm = float(eps), int(block_threads), int(blocks_per_sm)
+        self.h = sta_create(X, tets, E, nu, o, stream)
+        s = sta_sizes(self.h)
+        self.n_nodes, self.n_tets, self.nnz = s["n_nodes"], s["n_tets"], s["nnz"]
+        self.n_rows = 3 * self.n_nodes
+
+    def close(self):
+        if getattr(self, "h", None):
+            sta_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def full_rebuild(self, mask, stream=None):
+        sta_full_rebuild(self.h, mask, stream)
+
+    def apply_edits(self, edits, stream=None):
+        sta_apply_edits(self.h, edits, stream)
+
+    def last_touched(self, stream=None) -> int:
+        return sta_last_touched(self.h, stream)
+
+    def csr(self):
+        """(row_ptr, col, val) torch tensors viewing the context's device memory."""
+        return tuple(a.torch() for a in sta_csr(self.h, self))
+
+    def values(self):
+        return sta_csr(self.h, self)[2].torch()
+
+    def scatter_map(self):
+        return sta_scatter_map(self.h, self).torch()
+
+    def mask(self):
+        return sta_mask(self.h, self).torch()
+
+    def recompute_elements(self, active_only=False, stream=None):
+        sta_recompute_elements(self.h, active_only, stream)
+
+    def set_params(self, X=None, E=None, nu=None, stream=None):
+        sta_set_params(self.h, X, E, nu, stream)
+
+    def element_matrices(self, tet_ids, stream=None):
+        return sta_element_matrices(self.h, tet_ids, stream)
+
+    def sizes(self) -> dict:
+        return sta_sizes(self.h)

@@ -1,0 +1,370 @@
+// C-ABI entry points of libsta (declared in include/sta.h): argument and edit validation on
+// the host, device memory management, and the launch sequence of each call.
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sta_internal.cuh"
+
+namespace sta {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+int fail(int code, const std::string &msg) {
+    set_error(msg);
+    return code;
+}
+
+}  // namespace sta
+
+using namespace sta;
+
+struct sta_ctx {
+    Ctx c;
+    cudaEvent_t h2d_done = nullptr;
+    bool h2d_pending = false;
+    uint8_t *h_mask = nullptr;  // pinned staging for host masks, T bytes
+};
+
+static int wait_staging(sta_ctx *x) {
+    if (x->h2d_pending) {
+        STA_CUDA_TRY(cudaEventSynchronize(x->h2d_done));
+        x->h2d_pending = false;
+    }
+    return STA_OK;
+}
+
+static void free_ctx(sta_ctx *x) {
+    if (!x) return;
+    for (void *p : x->c.allocations) cudaFree(p);
+    x->c.allocations.clear();
+    if (x->c.h_edited) cudaFreeHost(x->c.h_edited);
+    if (x->c.d_edited) cudaFree(x->c.d_edited);
+    if (x->h_mask) cudaFreeHost(x->h_mask);
+    if (x->h2d_done) cudaEventDestroy(x->h2d_done);
+    delete x;
+}
+
+extern "C" {
+
+void sta_default_options(sta_options *opt) {
+    if (!opt) return;
+    opt->eps = 0.0;
+    opt->block_threads = 0;
+    opt->blocks_per_sm = 0;
+}
+
+const char *sta_last_error(void) { return g_last_error.c_str(); }
+
+const char *sta_status_string(int status) {
+    switch (status) {
+    case STA_OK: return "ok";
+    case STA_EINVAL: return "invalid argument";
+    case STA_ESTATE: return "invalid state";
+    case STA_ERANGE: return "index range overflow";
+    case STA_ENOMEM: return "out of memory";
+    case STA_ECUDA: return "CUDA error";
+    default: return "unknown status";
+    }
+}
+
+int sta_create(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
+               const double *young, const double *poisson, const sta_options *opt,
+               void *stream, sta_ctx **out) {
+    if (!out) return fail(STA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_nodes < 0 || n_tets < 0) return fail(STA_EINVAL, "negative size");
+    if ((n_nodes > 0 && !nodes) || (n_tets > 0 && (!tets || !young || !poisson)))
+        return fail(STA_EINVAL, "NULL input array");
+    if (n_tets >= (1LL << 27)) return fail(STA_ERANGE, "n_tets must be < 2^27");
+    if (3 * n_nodes + 1 > INT32_MAX) return fail(STA_ERANGE, "3 * n_nodes + 1 exceeds int32");
+    for (int64_t t = 0; t < n_tets; ++t) {
+        const int32_t *q = tets + 4 * t;
+        for (int a = 0; a < 4; ++a) {
+            if (q[a] < 0 || q[a] >= n_nodes)
+                return fail(STA_EINVAL, "tet " + std::to_string(t) + ": node id out of range");
+            for (int b = 0; b < a; ++b)
+                if (q[a] == q[b])
+                    return fail(STA_EINVAL, "tet " + std::to_string(t) + ": repeated node");
+        }
+    }
+    sta_options o;
+    sta_default_options(&o);
+    if (opt) o = *opt;
+    if (o.block_threads != 0 && (o.block_threads < 32 || o.block_threads > 1024 || o.block_threads % 32))
+        return fail(STA_EINVAL, "block_threads must be a multiple of 32 in [32, 1024]");
+
+    cudaStream_t s = (cudaStream_t)stream;
+    sta_ctx *x = new sta_ctx();
+    Ctx *c = &x->c;
+    c->n = n_nodes;
+    c->T = n_tets;
+    c->eps = o.eps;
+    c->block_threads = o.block_threads ? o.block_threads : 256;
+    c->blocks_per_sm = o.blocks_per_sm;
+    int rc = STA_OK;
+    auto bail = [&](int code) {
+        free_ctx(x);
+        return code;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+        return bail(fail(STA_ECUDA, "no CUDA device"));
+    if (cudaEventCreateWithFlags(&x->h2d_done, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(STA_ECUDA, "cudaEventCreate failed"));
+
+    // inputs: nodes padded to double4_32a, tets as int4, materials as double2
+    std::vector<double> X4(4 * (size_t)(n_nodes > 0 ? n_nodes : 1), 0.0);
+    for (int64_t v = 0; v < n_nodes; ++v)
+        for (int k = 0; k < 3; ++k) X4[4 * v + k] = nodes[3 * v + k];
+    std::vector<double> M2(2 * (size_t)(n_tets > 0 ? n_tets : 1), 0.0);
+    for (int64_t t = 0; t < n_tets; ++t) {
+        M2[2 * t] = young[t];
+        M2[2 * t + 1] = poisson[t];
+    }
+    if ((rc = dev_alloc(c, &c->X, n_nodes)) || (rc = dev_alloc(c, &c->tets, n_tets)) ||
+        (rc = dev_alloc(c, &c->mat, n_tets)) || (rc = dev_alloc(c, &c->counters, 4)))
+        return bail(rc);
+    if (cudaMemcpyAsync(c->X, X4.data(), sizeof(double4_32a) * n_nodes, cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(c->tets, tets, sizeof(int4) * n_tets, cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(c->mat, M2.data(), sizeof(double2) * n_tets, cudaMemcpyHostToDevice, s))
+        return bail(fail(STA_ECUDA, "input copy failed"));
+
+    if ((rc = build_pattern(c, s))) return bail(rc);
+
+    if ((rc = dev_alloc(c, &c->Ke, KE_STRIDE * n_tets)) || (rc = dev_alloc(c, &c->mask, n_tets)) ||
+        (rc = dev_alloc(c, &c->val, c->nnz)))
+        return bail(rc);
+    unsigned long long init[4] = {0ull, 0ull, ~0ull, 0ull};
+    if (cudaMemcpyAsync(c->counters, init, sizeof init, cudaMemcpyHostToDevice, s) ||
+        cudaMemsetAsync(c->mask, 0, (size_t)(n_tets > 0 ? n_tets : 1), s) ||
+        cudaMemsetAsync(c->val, 0, sizeof(double) * (size_t)(c->nnz > 0 ? c->nnz : 1), s))
+        return bail(fail(STA_ECUDA, "init failed"));
+    if ((rc = launch_elements(c, false, s))) return bail(rc);
+    unsigned long long back[4];
+    if (cudaMemcpyAsync(back, c->counters, sizeof back, cudaMemcpyDeviceToHost, s) ||
+        cudaStreamSynchronize(s))
+        return bail(fail(STA_ECUDA, std::string("element kernel failed: ") +
+                                        cudaGetErrorString(cudaGetLastError())));
+    if (back[0] != 0)
+        return bail(fail(STA_EINVAL, std::to_string(back[0]) +
+                                         " tetrahedra have det <= 0 (first: tet " +
+                                         std::to_string(back[2]) + ")"));
+    c->host_mask.assign((size_t)n_tets, 0);
+    c->seen.assign((size_t)n_tets, 0);
+    if (cudaMallocHost((void **)&x->h_mask, (size_t)(n_tets > 0 ? n_tets : 1)) != cudaSuccess)
+        return bail(fail(STA_ENOMEM, "pinned mask buffer"));
+    *out = x;
+    return STA_OK;
+}
+
+int sta_destroy(sta_ctx *x) {
+    if (!x) return STA_OK;
+    cudaDeviceSynchronize();
+    free_ctx(x);
+    return STA_OK;
+}
+
+int sta_full_rebuild(sta_ctx *x, const uint8_t *mask, int mask_on_device, void *stream) {
+    if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    Ctx *c = &x->c;
+    if (c->T > 0 && !mask) return fail(STA_EINVAL, "mask is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->T > 0) {
+        if (mask_on_device) {
+            STA_CUDA_TRY(cudaMemcpyAsync(c->mask, mask, (size_t)c->T, cudaMemcpyDeviceToDevice, s));
+            STA_CUDA_TRY(cudaMemcpyAsync(c->host_mask.data(), mask, (size_t)c->T,
+                                         cudaMemcpyDeviceToHost, s));
+            STA_CUDA_TRY(cudaStreamSynchronize(s));
+            for (auto &b : c->host_mask) b = b ? 1 : 0;
+        } else {
+            STA_TRY(wait_staging(x));
+            for (int64_t t = 0; t < c->T; ++t) {
+                uint8_t b = mask[t] ? 1 : 0;
+                c->host_mask[t] = b;
+                x->h_mask[t] = b;
+            }
+            STA_CUDA_TRY(cudaMemcpyAsync(c->mask, x->h_mask, (size_t)c->T, cudaMemcpyHostToDevice, s));
+            STA_CUDA_TRY(cudaEventRecord(x->h2d_done, s));
+            x->h2d_pending = true;
+        }
+    }
+    return launch_rebuild(c, s);
+}
+
+int sta_apply_edits(sta_ctx *x, const sta_edit *edits, int64_t n_edits, void *stream) {
+    if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    Ctx *c = &x->c;
+    if (n_edits < 0 || (n_edits > 0 && !edits)) return fail(STA_EINVAL, "bad edit list");
+    if (n_edits > (INT32_MAX / 32)) return fail(STA_ERANGE, "too many edits in one call");
+    cudaStream_t s = (cudaStream_t)stream;
+    // validate against the host mirror; `seen` is all zero at rest
+    int64_t bad = -1;
+    std::string why;
+    int64_t m = 0;
+    for (int64_t e = 0; e < n_edits && bad < 0; ++e) {
+        const sta_edit &E = edits[e];
+        if (E.op < 0 || E.op > 2) { bad = e; why = "bad op"; break; }
+        if (E.tet < 0 || E.tet >= c->T) { bad = e; why = "tet out of range"; break; }
+        if (c->seen[E.tet]) { bad = e; why = "tet named twice"; break; }
+        c->seen[E.tet] = 1;
+        if (E.op == STA_DEACTIVATE && !c->host_mask[E.tet]) { bad = e; why = "deactivating an inactive tet"; }
+        if (E.op == STA_ACTIVATE && c->host_mask[E.tet]) { bad = e; why = "activating an active tet"; }
+        if (E.op == STA_SWAP) {
+            if (E.tet2 < 0 || E.tet2 >= c->T) { bad = e; why = "tet2 out of range"; break; }
+            if (c->seen[E.tet2]) { bad = e; why = "tet2 named twice"; break; }
+            c->seen[E.tet2] = 1;
+            if (!c->host_mask[E.tet] || c->host_mask[E.tet2]) { bad = e; why = "swap needs an active tet and an inactive tet2"; }
+            ++m;
+        }
+        ++m;
+    }
+    for (int64_t e = 0; e < n_edits; ++e) {  // reset scratch
+        if (edits[e].tet >= 0 && edits[e].tet < c->T) c->seen[edits[e].tet] = 0;
+        if (edits[e].op == STA_SWAP && edits[e].tet2 >= 0 && edits[e].tet2 < c->T)
+            c->seen[edits[e].tet2] = 0;
+    }
+    if (bad >= 0) return fail(STA_EINVAL, "edit " + std::to_string(bad) + ": " + why);
+
+    if (m > c->edit_cap) {
+        STA_TRY(wait_staging(x));
+        int64_t cap = m < 1024 ? 1024 : m + m / 2;
+        if (c->h_edited) cudaFreeHost(c->h_edited);
+        c->h_edited = nullptr;
+        if (c->d_edited) {
+            cudaFree(c->d_edited);  // implicit device synchronisation
+            c->device_bytes -= (int64_t)sizeof(int32_t) * c->edit_cap;
+        }
+        c->d_edited = nullptr;
+        c->edit_cap = 0;
+        if (cudaMallocHost((void **)&c->h_edited, sizeof(int32_t) * cap) != cudaSuccess)
+            return fail(STA_ENOMEM, "pinned edit buffer");
+        if (cudaMalloc((void **)&c->d_edited, sizeof(int32_t) * cap) != cudaSuccess)
+            return fail(STA_ENOMEM, "device edit buffer");
+        c->device_bytes += (int64_t)sizeof(int32_t) * cap;
+        c->edit_cap = cap;
+    }
+    STA_TRY(wait_staging(x));
+    int64_t k = 0;
+    for (int64_t e = 0; e < n_edits; ++e) {
+        const sta_edit &E = edits[e];
+        if (E.op == STA_DEACTIVATE) {
+            c->h_edited[k++] = E.tet;
+            c->host_mask[E.tet] = 0;
+        } else if (E.op == STA_ACTIVATE) {
+            c->h_edited[k++] = (int32_t)((uint32_t)E.tet | 0x80000000u);
+            c->host_mask[E.tet] = 1;
+        } else {
+            c->h_edited[k++] = E.tet;
+            c->h_edited[k++] = (int32_t)((uint32_t)E.tet2 | 0x80000000u);
+            c->host_mask[E.tet] = 0;
+            c->host_mask[E.tet2] = 1;
+        }
+    }
+    if (m > 0) {
+        STA_CUDA_TRY(cudaMemcpyAsync(c->d_edited, c->h_edited, sizeof(int32_t) * m,
+                                     cudaMemcpyHostToDevice, s));
+        STA_CUDA_TRY(cudaEventRecord(x->h2d_done, s));
+        x->h2d_pending = true;
+    }
+    c->last_edited = m;
+    return launch_stream(c, m, s);
+}
+
+int sta_last_touched(sta_ctx *x, int64_t *touched_nnz, void *stream) {
+    if (!x || !touched_nnz) return fail(STA_EINVAL, "NULL argument");
+    unsigned long long v = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    STA_CUDA_TRY(cudaMemcpyAsync(&v, x->c.counters + 1, sizeof v, cudaMemcpyDeviceToHost, s));
+    STA_CUDA_TRY(cudaStreamSynchronize(s));
+    *touched_nnz = 9 * (int64_t)v;
+    return STA_OK;
+}
+
+int sta_csr(const sta_ctx *x, const int32_t **row_ptr, const int32_t **col, const double **val,
+            int64_t *n_rows, int64_t *nnz) {
+    if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    if (row_ptr) *row_ptr = x->c.row_ptr;
+    if (col) *col = x->c.col;
+    if (val) *val = x->c.val;
+    if (n_rows) *n_rows = x->c.nrows;
+    if (nnz) *nnz = x->c.nnz;
+    return STA_OK;
+}
+
+int sta_scatter_map(const sta_ctx *x, const int32_t **scat) {
+    if (!x || !scat) return fail(STA_EINVAL, "NULL argument");
+    *scat = x->c.scat;
+    return STA_OK;
+}
+
+int sta_mask(const sta_ctx *x, const uint8_t **mask) {
+    if (!x || !mask) return fail(STA_EINVAL, "NULL argument");
+    *mask = x->c.mask;
+    return STA_OK;
+}
+
+int sta_sizes(const sta_ctx *x, int64_t *n_nodes, int64_t *n_tets, int64_t *n_blocks,
+              int64_t *device_bytes) {
+    if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    if (n_nodes) *n_nodes = x->c.n;
+    if (n_tets) *n_tets = x->c.T;
+    if (n_blocks) *n_blocks = x->c.nblocks;
+    if (device_bytes) *device_bytes = x->c.device_bytes;
+    return STA_OK;
+}
+
+int sta_recompute_elements(sta_ctx *x, int active_only, void *stream) {
+    if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    return launch_elements(&x->c, active_only != 0, (cudaStream_t)stream);
+}
+
+int sta_set_params(sta_ctx *x, const double *nodes, const double *young, const double *poisson,
+                   int on_device, void *stream) {
+    if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    Ctx *c = &x->c;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (nodes) {
+        if (on_device) {
+            STA_CUDA_TRY(cudaMemcpy2DAsync(c->X, sizeof(double4_32a), nodes, 3 * sizeof(double),
+                                           3 * sizeof(double), (size_t)c->n,
+                                           cudaMemcpyDeviceToDevice, s));
+        } else {
+            std::vector<double> X4(4 * (size_t)(c->n > 0 ? c->n : 1), 0.0);
+            for (int64_t v = 0; v < c->n; ++v)
+                for (int k = 0; k < 3; ++k) X4[4 * v + k] = nodes[3 * v + k];
+            STA_CUDA_TRY(cudaMemcpyAsync(c->X, X4.data(), sizeof(double4_32a) * c->n,
+                                         cudaMemcpyHostToDevice, s));
+            STA_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+    }
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (young)
+        STA_CUDA_TRY(cudaMemcpy2DAsync(c->mat, sizeof(double2), young, sizeof(double),
+                                       sizeof(double), (size_t)c->T, kind, s));
+    if (poisson)
+        STA_CUDA_TRY(cudaMemcpy2DAsync((double *)c->mat + 1, sizeof(double2), poisson,
+                                       sizeof(double), sizeof(double), (size_t)c->T, kind, s));
+    unsigned long long init[2] = {0ull, 0ull};
+    STA_CUDA_TRY(cudaMemcpyAsync(c->counters, init, sizeof init, cudaMemcpyHostToDevice, s));
+    unsigned long long mx = ~0ull;
+    STA_CUDA_TRY(cudaMemcpyAsync(c->counters + 2, &mx, sizeof mx, cudaMemcpyHostToDevice, s));
+    STA_TRY(launch_elements(c, false, s));
+    unsigned long long back[4];
+    STA_CUDA_TRY(cudaMemcpyAsync(back, c->counters, sizeof back, cudaMemcpyDeviceToHost, s));
+    STA_CUDA_TRY(cudaStreamSynchronize(s));
+    if (back[0] != 0)
+        return fail(STA_EINVAL, std::to_string(back[0]) + " tetrahedra have det <= 0 (first: tet " +
+                                    std::to_string(back[2]) + ")");
+    return STA_OK;
+}
+
+int sta_element_matrices(sta_ctx *x, const int32_t *tet_ids, int64_t n, double *out, void *stream) {
+    if (!x || n < 0 || (n > 0 && (!tet_ids || !out))) return fail(STA_EINVAL, "bad argument");
+    return launch_expand_elements(&x->c, tet_ids, n, out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

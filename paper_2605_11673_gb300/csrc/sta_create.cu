@@ -1,0 +1,353 @@
+// One-time construction of the superset pattern and index maps on the device (sta_create).
+//
+// STA-FEM (arXiv 2605.11673) Sec. 3.3 keeps "precomputed tetrahedron-to-edge incidence" and
+// the sparse matrix pattern; Eq. 8's P_tau injects the 12 local DOFs of a tetrahedron.  For
+// the elasticity operator these become, built once here and never changed:
+//   node -> incident tetrahedra (ascending id)       nt_ptr / nt_list (scratch)
+//   node-pair blocks: sorted neighbour list per node adj_ptr / adj / block_node
+//   scalar CSR                                        row_ptr / col
+//   tet -> block of each local node pair              tblk   (T x 16)
+//   tet -> CSR index of each local entry              scat   (T x 144)
+//   block -> contributors in ascending tet id         cptr / ccode
+// Lists filled with atomics are sorted afterwards, so every array is deterministic.
+#include <climits>
+
+#include "sta_internal.cuh"
+
+namespace sta {
+namespace {
+
+constexpr int TPB = 256;
+
+inline unsigned grid_for(int64_t items, int threads = TPB) {
+    int64_t g = (items + threads - 1) / threads;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+// ---------------------------------------------------------------- exclusive scan (int64)
+// out[0] = 0, out[i + 1] = sum_{k <= i} in[k].  Three phases: per-CTA sums, a single-CTA
+// scan of the CTA sums, and a fix-up pass.
+
+constexpr int SCAN_TPB = 1024;
+
+__device__ __forceinline__ int64_t cta_inclusive_scan(int64_t v, int64_t *warp_sums) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) warp_sums[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t w = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_sums[lane] = w;
+    }
+    __syncthreads();
+    if (wid > 0) v += warp_sums[wid - 1];
+    return v;
+}
+
+template <typename In>
+__global__ void k_scan_tiles(const In *in, int64_t m, int64_t *out, int64_t *tile_sums) {
+    __shared__ int64_t ws[32];
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t v = i < m ? (int64_t)in[i] : 0;
+    int64_t inc = cta_inclusive_scan(v, ws);
+    if (i < m) out[i + 1] = inc;
+    if (threadIdx.x == blockDim.x - 1) tile_sums[blockIdx.x] = inc;
+}
+
+__global__ void k_scan_sums(int64_t *tile_sums, int64_t ntiles) {
+    __shared__ int64_t ws[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < ntiles; base += blockDim.x) {
+        int64_t i = base + threadIdx.x;
+        int64_t v = i < ntiles ? tile_sums[i] : 0;
+        int64_t inc = cta_inclusive_scan(v, ws);
+        int64_t c = carry;
+        if (i < ntiles) tile_sums[i] = c + inc - v;  // exclusive offset of tile i
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = c + inc;
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_fix(int64_t *out, int64_t m, const int64_t *tile_off) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) out[i + 1] += tile_off[blockIdx.x];
+    if (i == 0) out[0] = 0;
+}
+
+template <typename In>
+int exclusive_scan(Ctx *c, const In *in, int64_t m, int64_t *out, int64_t *tmp_tiles,
+                   cudaStream_t s) {
+    int64_t ntiles = (m + SCAN_TPB - 1) / SCAN_TPB;
+    if (ntiles < 1) ntiles = 1;
+    k_scan_tiles<In><<<(unsigned)ntiles, SCAN_TPB, 0, s>>>(in, m, out, tmp_tiles);
+    k_scan_sums<<<1, SCAN_TPB, 0, s>>>(tmp_tiles, ntiles);
+    k_scan_fix<<<(unsigned)ntiles, SCAN_TPB, 0, s>>>(out, m, tmp_tiles);
+    STA_CUDA_TRY(cudaGetLastError());
+    (void)c;
+    return STA_OK;
+}
+
+// ---------------------------------------------------------------- node -> tetrahedra
+
+__global__ void k_count_node_tets(const int4 *tets, int64_t T, int32_t *cnt) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int4 q = tets[t];
+        atomicAdd(&cnt[q.x], 1);
+        atomicAdd(&cnt[q.y], 1);
+        atomicAdd(&cnt[q.z], 1);
+        atomicAdd(&cnt[q.w], 1);
+    }
+}
+
+__global__ void k_fill_node_tets(const int4 *tets, int64_t T, const int64_t *nt_ptr,
+                                 int32_t *fill, int32_t *nt_list) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int4 q = tets[t];
+        int v[4] = {q.x, q.y, q.z, q.w};
+        for (int k = 0; k < 4; ++k) {
+            int32_t slot = atomicAdd(&fill[v[k]], 1);
+            nt_list[nt_ptr[v[k]] + slot] = (int32_t)t;
+        }
+    }
+}
+
+// insertion sort of each segment [ptr[i], ptr[i+1]) of int32 keys, one thread per segment
+__global__ void k_sort_segments(const int64_t *ptr, int64_t nseg, int32_t *keys) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nseg;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t b = ptr[i], e = ptr[i + 1];
+        for (int64_t k = b + 1; k < e; ++k) {
+            int32_t x = keys[k];
+            int64_t j = k - 1;
+            while (j >= b && keys[j] > x) {
+                keys[j + 1] = keys[j];
+                --j;
+            }
+            keys[j + 1] = x;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- neighbour sets
+
+// Sorted, de-duplicated nodes of the tetrahedra incident to node a, built by insertion into
+// scratch[4 nt_ptr[a] ...] (capacity 4 x incident count).
+__global__ void k_node_neighbors(const int4 *tets, int64_t n, const int64_t *nt_ptr,
+                                 const int32_t *nt_list, int32_t *scratch, int32_t *deg) {
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        int32_t *buf = scratch + 4 * nt_ptr[a];
+        int32_t cnt = 0;
+        for (int64_t e = nt_ptr[a]; e < nt_ptr[a + 1]; ++e) {
+            int4 q = tets[nt_list[e]];
+            int v[4] = {q.x, q.y, q.z, q.w};
+            for (int k = 0; k < 4; ++k) {
+                int32_t x = v[k];
+                int32_t j = cnt - 1;
+                while (j >= 0 && buf[j] > x) --j;
+                if (j >= 0 && buf[j] == x) continue;
+                for (int32_t m = cnt - 1; m > j; --m) buf[m + 1] = buf[m];
+                buf[j + 1] = x;
+                ++cnt;
+            }
+        }
+        deg[a] = cnt;
+    }
+}
+
+__global__ void k_adj_fill(int64_t n, const int64_t *nt_ptr, const int32_t *scratch,
+                           const int64_t *adj_ptr64, int32_t *adj_ptr, int32_t *adj,
+                           int32_t *block_node) {
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a <= n;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        adj_ptr[a] = (int32_t)adj_ptr64[a];
+        if (a == n) continue;
+        const int32_t *buf = scratch + 4 * nt_ptr[a];
+        int64_t b = adj_ptr64[a], d = adj_ptr64[a + 1] - b;
+        for (int64_t k = 0; k < d; ++k) {
+            adj[b + k] = buf[k];
+            block_node[b + k] = (int32_t)a;
+        }
+    }
+}
+
+// row 3a+i starts at 9 adj_ptr[a] + 3 i deg(a)
+__global__ void k_row_ptr(int64_t n, const int32_t *adj_ptr, int32_t *row_ptr) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= 3 * n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        if (r == 3 * n) {
+            row_ptr[r] = 9 * adj_ptr[n];
+            continue;
+        }
+        int64_t a = r / 3, i = r % 3;
+        int32_t s = adj_ptr[a], d = adj_ptr[a + 1] - s;
+        row_ptr[r] = 9 * s + 3 * (int32_t)i * d;
+    }
+}
+
+__global__ void k_col(int64_t nblocks, const int32_t *block_node, const int32_t *adj_ptr,
+                      const int32_t *adj, int32_t *col) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nblocks;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        int32_t a = block_node[g], s = adj_ptr[a], d = adj_ptr[a + 1] - s;
+        int32_t p = (int32_t)g - s, b = adj[g];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) col[9 * s + 3 * i * d + 3 * p + j] = 3 * b + j;
+    }
+}
+
+// tblk[16 t + 4 la + lb] = block of (v_la, v_lb); scat[144 t + 12 (3la+i) + 3lb + j] = CSR
+// index of (3 v_la + i, 3 v_lb + j).  Position of v_lb in v_la's sorted list by bisection.
+__global__ void k_tet_maps(const int4 *tets, int64_t T, const int32_t *adj_ptr,
+                           const int32_t *adj, int32_t *tblk, int32_t *scat) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int4 q = tets[t];
+        int v[4] = {q.x, q.y, q.z, q.w};
+        for (int la = 0; la < 4; ++la) {
+            int32_t s = adj_ptr[v[la]], d = adj_ptr[v[la] + 1] - s;
+            for (int lb = 0; lb < 4; ++lb) {
+                int32_t lo = 0, hi = d;  // first position with adj >= v[lb]
+                while (lo < hi) {
+                    int32_t mid = (lo + hi) >> 1;
+                    if (adj[s + mid] < v[lb]) lo = mid + 1; else hi = mid;
+                }
+                tblk[16 * t + 4 * la + lb] = s + lo;
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j)
+                        scat[144 * t + 12 * (3 * la + i) + 3 * lb + j] =
+                            9 * s + 3 * i * d + 3 * lo + j;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- contributor lists
+
+__global__ void k_contrib_count(const int32_t *tblk, int64_t T, int32_t *cnt) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < 16 * T;
+         k += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[tblk[k]], 1);
+}
+
+__global__ void k_contrib_fill(const int32_t *tblk, int64_t T, const int64_t *cptr64,
+                               int32_t *fill, int32_t *ccode) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < 16 * T;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int32_t g = tblk[k];
+        int32_t slot = atomicAdd(&fill[g], 1);
+        int32_t t = (int32_t)(k >> 4), la = (int32_t)((k >> 2) & 3), lb = (int32_t)(k & 3);
+        ccode[cptr64[g] + slot] = contrib_code(t, la, lb);
+    }
+}
+
+__global__ void k_to_i32(const int64_t *in, int64_t m, int32_t *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (int32_t)in[i];
+}
+
+__global__ void k_fill_i32(int32_t *p, int64_t m, int32_t v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+struct Scratch {
+    std::vector<void *> ptrs;
+    ~Scratch() {
+        for (void *p : ptrs) cudaFree(p);
+    }
+    template <typename T> int get(T **p, int64_t count) {
+        cudaError_t e = cudaMalloc((void **)p, sizeof(T) * (size_t)(count > 0 ? count : 1));
+        if (e != cudaSuccess)
+            return fail(STA_ENOMEM, std::string("cudaMalloc (scratch): ") + cudaGetErrorString(e));
+        ptrs.push_back(*p);
+        return STA_OK;
+    }
+};
+
+}  // namespace
+
+int build_pattern(Ctx *c, cudaStream_t s) {
+    const int64_t n = c->n, T = c->T;
+    Scratch sc;
+    int32_t *cnt = nullptr, *nt_list = nullptr, *scratch = nullptr, *deg = nullptr;
+    int64_t *nt_ptr = nullptr, *adj_ptr64 = nullptr, *tiles = nullptr;
+    int64_t max_m = (n > 16 * T ? n : 16 * T) + 1;
+    STA_TRY(sc.get(&cnt, max_m));
+    STA_TRY(sc.get(&nt_ptr, n + 1));
+    STA_TRY(sc.get(&nt_list, 4 * T));
+    STA_TRY(sc.get(&scratch, 16 * T));
+    STA_TRY(sc.get(&deg, n));
+    STA_TRY(sc.get(&adj_ptr64, n + 1));
+    STA_TRY(sc.get(&tiles, max_m / SCAN_TPB + 2));
+
+    // node -> incident tetrahedra, ascending
+    STA_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * n, s));
+    k_count_node_tets<<<grid_for(T), TPB, 0, s>>>(c->tets, T, cnt);
+    STA_TRY(exclusive_scan(c, cnt, n, nt_ptr, tiles, s));
+    STA_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * n, s));
+    k_fill_node_tets<<<grid_for(T), TPB, 0, s>>>(c->tets, T, nt_ptr, cnt, nt_list);
+    k_sort_segments<<<grid_for(n), TPB, 0, s>>>(nt_ptr, n, nt_list);
+
+    // neighbour sets -> blocks
+    k_node_neighbors<<<grid_for(n), TPB, 0, s>>>(c->tets, n, nt_ptr, nt_list, scratch, deg);
+    STA_TRY(exclusive_scan(c, deg, n, adj_ptr64, tiles, s));
+    int64_t nblocks = 0;
+    STA_CUDA_TRY(cudaMemcpyAsync(&nblocks, adj_ptr64 + n, sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, s));
+    STA_CUDA_TRY(cudaStreamSynchronize(s));
+    STA_CUDA_TRY(cudaGetLastError());
+    if (9 * nblocks > INT32_MAX)
+        return fail(STA_ERANGE, "nnz = " + std::to_string(9 * nblocks) + " exceeds int32");
+    c->nblocks = nblocks;
+    c->nnz = 9 * nblocks;
+    c->nrows = 3 * n;
+
+    STA_TRY(dev_alloc(c, &c->adj_ptr, n + 1));
+    STA_TRY(dev_alloc(c, &c->adj, nblocks));
+    STA_TRY(dev_alloc(c, &c->block_node, nblocks));
+    STA_TRY(dev_alloc(c, &c->row_ptr, 3 * n + 1));
+    STA_TRY(dev_alloc(c, &c->col, c->nnz));
+    STA_TRY(dev_alloc(c, &c->tblk, 16 * T));
+    STA_TRY(dev_alloc(c, &c->scat, 144 * T));
+    STA_TRY(dev_alloc(c, &c->cptr, nblocks + 1));
+    STA_TRY(dev_alloc(c, &c->ccode, 16 * T));
+    STA_TRY(dev_alloc(c, &c->owner, nblocks));
+
+    k_adj_fill<<<grid_for(n + 1), TPB, 0, s>>>(n, nt_ptr, scratch, adj_ptr64, c->adj_ptr,
+                                               c->adj, c->block_node);
+    k_row_ptr<<<grid_for(3 * n + 1), TPB, 0, s>>>(n, c->adj_ptr, c->row_ptr);
+    k_col<<<grid_for(nblocks), TPB, 0, s>>>(nblocks, c->block_node, c->adj_ptr, c->adj, c->col);
+    k_tet_maps<<<grid_for(T), TPB, 0, s>>>(c->tets, T, c->adj_ptr, c->adj, c->tblk, c->scat);
+
+    // contributor lists, ascending tetrahedron id (codes carry the id in their high bits)
+    int64_t *cptr64 = nullptr;
+    STA_TRY(sc.get(&cptr64, nblocks + 1));
+    STA_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nblocks, s));
+    k_contrib_count<<<grid_for(16 * T), TPB, 0, s>>>(c->tblk, T, cnt);
+    STA_TRY(exclusive_scan(c, cnt, nblocks, cptr64, tiles, s));
+    STA_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nblocks, s));
+    k_contrib_fill<<<grid_for(16 * T), TPB, 0, s>>>(c->tblk, T, cptr64, cnt, c->ccode);
+    k_sort_segments<<<grid_for(nblocks), TPB, 0, s>>>(cptr64, nblocks, c->ccode);
+    k_to_i32<<<grid_for(nblocks + 1), TPB, 0, s>>>(cptr64, nblocks + 1, c->cptr);
+    k_fill_i32<<<grid_for(nblocks), TPB, 0, s>>>(c->owner, nblocks, INT32_MAX);
+    STA_CUDA_TRY(cudaGetLastError());
+    STA_CUDA_TRY(cudaStreamSynchronize(s));
+    return STA_OK;
+}
+
+}  // namespace sta

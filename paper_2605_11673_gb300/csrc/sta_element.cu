@@ -1,0 +1,190 @@
+// Element stiffness kernel (a1): the 12x12 linear-tetrahedron elasticity matrix K^(tau)
+// (STA-FEM Sec. 3.4 and Sec. 5.2; the standard P1 isotropic small-strain element,
+// K = V B^T D B), 78 unique entries per tetrahedron written to the element cache.
+//
+// The evaluation order is fixed (see include/sta.h, sta_recompute_elements) and this file
+// is compiled with --fmad=false: every fma below is an explicit __fma_rn, every other
+// operation is a separately rounded IEEE double operation.  On GB300 the FP64 pipe is the
+// scarce unit (about 0.5 Top/s against 35 Top/s of int32), so the order is also chosen to
+// need few FP64 operations: about 300 per tetrahedron.
+#include "sta_internal.cuh"
+
+namespace sta {
+namespace {
+
+constexpr int EL_TPB = 128;
+
+struct V3 {
+    double x, y, z;
+};
+
+__device__ __forceinline__ V3 sub(const double4_32a &a, const double4_32a &b) {
+    return {a.x - b.x, a.y - b.y, a.z - b.z};
+}
+
+// (u x v) with each component fma(u1, v2, -(u2 * v1))
+__device__ __forceinline__ V3 cross_fma(const V3 &u, const V3 &v) {
+    return {__fma_rn(u.y, v.z, -(u.z * v.y)), __fma_rn(u.z, v.x, -(u.x * v.z)),
+            __fma_rn(u.x, v.y, -(u.y * v.x))};
+}
+
+__device__ __forceinline__ double gc(const V3 &g, int i) { return i == 0 ? g.x : (i == 1 ? g.y : g.z); }
+
+// Computes the 78-entry record of one tetrahedron into rec[] (registers or shared memory).
+// Returns false when det <= 0 (record filled with zeros).
+__device__ __forceinline__ bool element_record(double4_32a x0, double4_32a x1, double4_32a x2, double4_32a x3,
+                                               double E, double nu, double *rec) {
+    V3 d1 = sub(x1, x0), d2 = sub(x2, x0), d3 = sub(x3, x0);
+    V3 c1 = cross_fma(d2, d3), c2 = cross_fma(d3, d1), c3 = cross_fma(d1, d2);
+    double det = __fma_rn(d1.z, c1.z, __fma_rn(d1.y, c1.y, d1.x * c1.x));
+    if (!(det > 0.0)) {
+#pragma unroll
+        for (int k = 0; k < KE_STRIDE; ++k) rec[k] = 0.0;
+        return false;
+    }
+    double r = 1.0 / det;
+    V3 g[4];
+    g[1] = {c1.x * r, c1.y * r, c1.z * r};
+    g[2] = {c2.x * r, c2.y * r, c2.z * r};
+    g[3] = {c3.x * r, c3.y * r, c3.z * r};
+    g[0] = {-((g[1].x + g[2].x) + g[3].x), -((g[1].y + g[2].y) + g[3].y),
+            -((g[1].z + g[2].z) + g[3].z)};
+    double V = det / 6.0;
+    double onu = 1.0 + nu;
+    double lam = (E * nu) / (onu * (1.0 - (nu + nu)));
+    double mu = E / (onu + onu);
+    double Vl = V * lam, Vm = V * mu;
+    double P[4][3], Q[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            P[a][i] = Vl * gc(g[a], i);
+            Q[a][i] = Vm * gc(g[a], i);
+        }
+    // diagonal blocks (a, a), entries i <= j
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        double D = Vm * __fma_rn(g[a].z, g[a].z, __fma_rn(g[a].y, g[a].y, g[a].x * g[a].x));
+        double *o = rec + ke_diag_off(a);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = i; j < 3; ++j) {
+                double v = (i != j)
+                               ? __fma_rn(P[a][i], gc(g[a], j), Q[a][j] * gc(g[a], i))
+                               : __fma_rn(P[a][i], gc(g[a], i), __fma_rn(Q[a][i], gc(g[a], i), D));
+                o[ke_tri(i, j)] = v;
+            }
+    }
+    // off-diagonal blocks (a, b), a < b, all (i, j)
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = a + 1; b < 4; ++b) {
+            double D = Vm * __fma_rn(g[a].z, g[b].z, __fma_rn(g[a].y, g[b].y, g[a].x * g[b].x));
+            double *o = rec + ke_off_off(a, b);
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    double v = (i != j)
+                                   ? __fma_rn(P[a][i], gc(g[b], j), Q[a][j] * gc(g[b], i))
+                                   : __fma_rn(P[a][i], gc(g[b], i), __fma_rn(Q[a][i], gc(g[b], i), D));
+                    o[3 * i + j] = v;
+                }
+        }
+    return true;
+}
+
+// One thread per tetrahedron; a warp stages its 32 records in shared memory and writes
+// each record of an updated tetrahedron as one contiguous 624-byte run (coalesced).
+// active_only: tetrahedra with mask == 0 keep their cached record untouched.
+__global__ void __launch_bounds__(EL_TPB)
+k_elements(const double4_32a *__restrict__ X, const int4 *__restrict__ tets,
+           const double2 *__restrict__ mat, const uint8_t *__restrict__ mask, int active_only,
+           int64_t T, double *__restrict__ Ke, unsigned long long *bad) {
+    extern __shared__ double smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double *wrec = smem + (size_t)wid * 32 * KE_STRIDE;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < T;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = base + threadIdx.x;  // warp wid covers [base + 32 wid, +32)
+        bool doit = t < T && (!active_only || mask[t]);
+        if (doit) {
+            int4 q = tets[t];
+            double2 m = mat[t];
+            bool ok = element_record(X[q.x], X[q.y], X[q.z], X[q.w], m.x, m.y,
+                                     wrec + (size_t)lane * KE_STRIDE);
+            if (!ok) {
+                atomicAdd(&bad[0], 1ull);
+                atomicMin(&bad[2], (unsigned long long)t);
+            }
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, doit);
+        __syncwarp();
+        const int64_t t0 = base + 32 * wid;
+        while (todo) {
+            int r = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const double2 *src = reinterpret_cast<const double2 *>(wrec + (size_t)r * KE_STRIDE);
+            double2 *dst = reinterpret_cast<double2 *>(Ke + (size_t)(t0 + r) * KE_STRIDE);
+            for (int k = lane; k < KE_STRIDE / 2; k += 32) dst[k] = src[k];
+        }
+        __syncwarp();
+    }
+}
+
+// Expand cached records of selected tetrahedra to full 12x12 row-major matrices.
+__global__ void k_expand(const double *__restrict__ Ke, int64_t T, const int32_t *ids,
+                         int64_t n, double *out) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < 144 * n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t e = k / 144;
+        int pq = (int)(k % 144), p = pq / 12, q = pq % 12;
+        int32_t t = ids[e];
+        if (t < 0 || t >= T) {
+            out[k] = 0.0;
+            continue;
+        }
+        int a = p / 3, i = p % 3, b = q / 3, j = q % 3;
+        if (a > b || (a == b && i > j)) {  // mirror into the stored upper triangle
+            int ta = a, ti = i;
+            a = b; i = j; b = ta; j = ti;
+        }
+        const double *rec = Ke + (size_t)t * KE_STRIDE;
+        out[k] = (a == b) ? rec[ke_diag_off(a) + ke_tri(i, j)] : rec[ke_off_off(a, b) + 3 * i + j];
+    }
+}
+
+}  // namespace
+
+int launch_elements(Ctx *c, bool active_only, cudaStream_t s) {
+    if (c->T == 0) return STA_OK;
+    size_t smem = (size_t)EL_TPB * KE_STRIDE * sizeof(double);  // 78 KB
+    STA_CUDA_TRY(cudaFuncSetAttribute(k_elements, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    int64_t blocks = (c->T + EL_TPB - 1) / EL_TPB;
+    int per_sm = 0;
+    STA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_elements, EL_TPB, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t cap = (int64_t)per_sm * c->num_sms;
+    if (blocks > cap) blocks = cap;
+    k_elements<<<(unsigned)blocks, EL_TPB, smem, s>>>(c->X, c->tets, c->mat, c->mask,
+                                                      active_only ? 1 : 0, c->T, c->Ke,
+                                                      c->counters);
+    STA_CUDA_TRY(cudaGetLastError());
+    return STA_OK;
+}
+
+int launch_expand_elements(Ctx *c, const int32_t *ids, int64_t n, double *out, cudaStream_t s) {
+    if (n == 0) return STA_OK;
+    int64_t items = 144 * n;
+    int64_t blocks = (items + 255) / 256;
+    if (blocks > 65535LL * 16) blocks = 65535LL * 16;
+    k_expand<<<(unsigned)blocks, 256, 0, s>>>(c->Ke, c->T, ids, n, out);
+    STA_CUDA_TRY(cudaGetLastError());
+    return STA_OK;
+}
+
+}  // namespace sta

@@ -1,0 +1,130 @@
+// Internal declarations of libsta: context layout, device helpers shared by the fold
+// kernels, launch helpers.  Not part of the public ABI (see include/sta.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sta.h"
+
+namespace sta {
+
+// ------------------------------------------------------------------------------------
+// Error plumbing
+// ------------------------------------------------------------------------------------
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+
+#define STA_CUDA_TRY(expr)                                                                   \
+    do {                                                                                     \
+        cudaError_t _e = (expr);                                                             \
+        if (_e != cudaSuccess)                                                               \
+            return ::sta::fail(_e == cudaErrorMemoryAllocation ? STA_ENOMEM : STA_ECUDA,     \
+                               std::string(#expr) + ": " + cudaGetErrorString(_e));         \
+    } while (0)
+
+#define STA_TRY(expr)                                                                        \
+    do {                                                                                     \
+        int _s = (expr);                                                                     \
+        if (_s != STA_OK) return _s;                                                         \
+    } while (0)
+
+// ------------------------------------------------------------------------------------
+// Element cache record: the 78 unique entries of the symmetric 12x12 element matrix,
+// grouped by 3x3 node-pair block so that one block is one contiguous run:
+//   diagonal block (a, a), a = 0..3:  6 entries (i <= j, row-major) at 6a
+//   off-diagonal block (a, b), a < b:   9 entries (i, j row-major)    at 24 + 9 * pair(a, b)
+// with pair(0,1..3) = 0..2, pair(1,2..3) = 3..4, pair(2,3) = 5.
+// ------------------------------------------------------------------------------------
+constexpr int KE_STRIDE = 78;
+
+__host__ __device__ inline int ke_diag_off(int a) { return 6 * a; }
+__host__ __device__ inline int ke_pair(int a, int b) {  // a < b
+    return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);
+}
+__host__ __device__ inline int ke_off_off(int a, int b) { return 24 + 9 * ke_pair(a, b); }
+// index of (i, j), i <= j, inside a diagonal 6-run
+__host__ __device__ inline int ke_tri(int i, int j) {
+    return i == 0 ? j : (i == 1 ? 2 + j : 5);
+}
+
+// Contributor code of a node-pair block: tetrahedron id and the local indices of the
+// block's row node (la) and column node (lb) inside that tetrahedron.
+__host__ __device__ inline int32_t contrib_code(int32_t t, int la, int lb) {
+    return (t << 4) | (la << 2) | lb;
+}
+
+// ------------------------------------------------------------------------------------
+// Context
+// ------------------------------------------------------------------------------------
+struct Ctx {
+    int64_t n = 0, T = 0, nblocks = 0, nnz = 0, nrows = 0;
+    double eps = 0.0;
+    int block_threads = 256;
+    int blocks_per_sm = 0;
+    int num_sms = 0;
+    int device = 0;
+
+    // inputs
+    double4_32a *X = nullptr;   // n, (x, y, z, 0)
+    int4 *tets = nullptr;   // T
+    double2 *mat = nullptr; // T, (E, nu)
+
+    // pattern (a0)
+    int32_t *adj_ptr = nullptr;    // n + 1: first block of node a
+    int32_t *adj = nullptr;        // nblocks: neighbour node of each block (ascending per node)
+    int32_t *block_node = nullptr; // nblocks: owner node of each block
+    int32_t *row_ptr = nullptr;    // 3n + 1
+    int32_t *col = nullptr;        // nnz
+    int32_t *tblk = nullptr;       // T x 16: block of local pair (la, lb) = 4 la + lb
+    int32_t *scat = nullptr;       // T x 144: CSR index of local entry (p, q)
+    int32_t *cptr = nullptr;       // nblocks + 1: contributor list of each block
+    int32_t *ccode = nullptr;      // 16 T: contributor codes, ascending tetrahedron id
+
+    // state
+    double *Ke = nullptr;       // T x 78 element cache
+    uint8_t *mask = nullptr;    // T
+    double *val = nullptr;      // nnz
+    int32_t *owner = nullptr;   // nblocks: streaming dedupe slot, INT32_MAX when free
+    unsigned long long *counters = nullptr;  // [0] bad elements, [1] touched blocks
+
+    // streaming staging
+    int32_t *d_edited = nullptr;  // capacity: edited tetrahedra (id | new state << 31)
+    int32_t *h_edited = nullptr;  // pinned
+    int64_t edit_cap = 0;
+    int64_t last_edited = 0;
+
+    std::vector<uint8_t> host_mask;
+    std::vector<uint8_t> seen;  // per-tet scratch for edit validation (all zero at rest)
+    int64_t device_bytes = 0;
+    std::vector<void *> allocations;
+};
+
+template <typename T> int dev_alloc(Ctx *c, T **p, int64_t count) {
+    size_t bytes = sizeof(T) * (size_t)(count > 0 ? count : 1);
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(STA_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    c->allocations.push_back((void *)*p);
+    c->device_bytes += (int64_t)bytes;
+    return STA_OK;
+}
+
+// Persistent grid for an item count: min(ceil(items / threads), SMs * CTAs per SM).
+int persistent_grid(const Ctx *c, const void *kernel, int threads, int64_t items);
+
+// ------------------------------------------------------------------------------------
+// Kernel launchers (each returns STA_OK or STA_ECUDA on a launch error)
+// ------------------------------------------------------------------------------------
+int build_pattern(Ctx *c, cudaStream_t s);                       // sta_create.cu
+int launch_elements(Ctx *c, bool active_only, cudaStream_t s);   // sta_element.cu
+int launch_expand_elements(Ctx *c, const int32_t *ids, int64_t n, double *out, cudaStream_t s);
+int launch_rebuild(Ctx *c, cudaStream_t s);                      // sta_assemble.cu
+int launch_stream(Ctx *c, int64_t n_edited, cudaStream_t s);
+
+}  // namespace sta

@@ -1,0 +1,87 @@
+"""The C-ABI library builds, loads and exports every symbol include/sta.h declares; host-side
+validation runs before any device work (no GPU needed)."""
+import re
+import subprocess
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+def _declared():
+    names = set()
+    for h in (ROOT / "include").glob("*.h"):
+        text = re.sub(r"/\*.*?\*/", "", h.read_text(), flags=re.S)
+        names |= set(re.findall(r"\b(sta_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2605_11673_gb300 import build
+    build.build()
+    import paper_2605_11673_gb300 as P
+    return P
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared()
+    assert "sta_create" in declared and "sta_apply_edits" in declared
+    out = subprocess.run(["nm", "-D", "--defined-only", str(lib.LIB_PATH)], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (sta_[a-z0-9_]+)", out))
+    assert declared <= exported, declared - exported
+    assert set(lib.EXPORTED) == declared
+    L = lib.load_library()
+    for name in declared:
+        assert hasattr(L, name)
+
+
+def test_host_validation_before_device(lib):
+    X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1.0]])
+    cases = [np.array([[0, 1, 2, 2]]), np.array([[0, 1, 2, 4]]), np.array([[-1, 1, 2, 3]])]
+    for tets in cases:
+        with pytest.raises(lib.StaError) as e:
+            lib.sta_create(X, tets, [1.0], [0.3])
+        assert e.value.status == lib.STA_EINVAL
+    with pytest.raises(ValueError):
+        lib.sta_create(X, np.array([[0, 1, 2, 3]]), [1.0, 2.0], [0.3])
+    o = lib.sta_default_options()
+    o.block_threads = 48
+    with pytest.raises(lib.StaError) as e:
+        lib.sta_create(X, np.array([[0, 1, 2, 3]]), [1.0], [0.3], o)
+    assert e.value.status == lib.STA_EINVAL
+
+
+def test_status_strings(lib):
+    L = lib.load_library()
+    for code in (0, -1, -2, -3, -4, -5):
+        assert L.sta_status_string(code)
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    import paper_2605_11673_gb300 as P
+    saved = P._lib
+    try:
+        P._lib = None
+        with pytest.raises(ImportError):
+            P.load_library(tmp_path / "missing.so")
+    finally:
+        P._lib = saved
+
+
+def test_oracle_and_product_share_no_code():
+    """The CUDA sources never include or name the oracle, and the oracle never names the
+    library; the only shared Python module is the input generator package."""
+    csrc = ROOT / "paper_2605_11673_gb300"
+    for f in list(csrc.rglob("*.cu")) + list(csrc.rglob("*.cuh")):
+        assert "oracle" not in f.read_text().lower(), f
+    for f in csrc.rglob("*.py"):
+        text = f.read_text()
+        assert "import oracle" not in text and "from oracle" not in text, f
+    for f in (ROOT / "oracle").glob("*"):
+        if f.is_file() and f.suffix in (".c", ".py", ".h"):
+            text = f.read_text()
+            assert "paper_2605_11673_gb300" not in text and "libsta" not in text
