@@ -104,6 +104,13 @@ int sta_destroy(sta_ctx *ctx);
 int sta_full_rebuild(sta_ctx *ctx, const uint8_t *mask, int mask_on_device, void *stream);
 
 /*
+ * sta_refold -- the full_rebuild policy (Sec. 3.5) on the maintained mask: recompute every
+ * value of the pattern from scratch from the current active mask and element cache (use it
+ * after sta_set_params / sta_recompute_elements, or to time a rebuild without a mask copy).
+ */
+int sta_refold(sta_ctx *ctx, void *stream);
+
+/*
  * sta_apply_edits -- one frame of the streaming update (Sec. 3.2; Algorithm 1 receive /
  * update mask / per-tet update; Sec. 3.5 local_recompute made bitwise): applies the edits to
  * the mask, marks every block of the pattern touched by an edited tetrahedron (its 16 node

@@ -25,7 +25,7 @@ STA_DEACTIVATE, STA_ACTIVATE, STA_SWAP = 0, 1, 2
 # Every symbol declared in include/sta.h.
 EXPORTED = (
     "sta_default_options", "sta_create", "sta_destroy", "sta_full_rebuild", "sta_apply_edits",
-    "sta_last_touched", "sta_csr", "sta_scatter_map", "sta_sizes", "sta_mask",
+    "sta_last_touched", "sta_refold", "sta_csr", "sta_scatter_map", "sta_sizes", "sta_mask",
     "sta_recompute_elements", "sta_set_params", "sta_element_matrices", "sta_last_error",
     "sta_status_string",
 )
@@ -67,6 +67,7 @@ def load_library(path: Path | str | None = None):
     L.sta_full_rebuild.argtypes = [_p, _p, _int, _p]
     L.sta_apply_edits.argtypes = [_p, _p, _i64, _p]
     L.sta_last_touched.argtypes = [_p, _P(_i64), _p]
+    L.sta_refold.argtypes = [_p, _p]
     L.sta_csr.argtypes = [_p, _P(_p), _P(_p), _P(_p), _P(_i64), _P(_i64)]
     L.sta_scatter_map.argtypes = [_p, _P(_p)]
     L.sta_sizes.argtypes = [_p, _P(_i64), _P(_i64), _P(_i64), _P(_i64)]
@@ -166,6 +167,10 @@ def sta_apply_edits(h: int, edits, stream=None) -> None:
     e = _host(edits, np.int32).reshape(-1, 3)
     _check(load_library().sta_apply_edits(h, e.ctypes.data if e.shape[0] else None, e.shape[0],
                                           _stream_handle(stream)))
+
+
+def sta_refold(h: int, stream=None) -> None:
+    _check(load_library().sta_refold(h, _stream_handle(stream)))
 
 
 def sta_last_touched(h: int, stream=None) -> int:
@@ -274,6 +279,9 @@ class Assembler:
 
     def apply_edits(self, edits, stream=None):
         sta_apply_edits(self.h, edits, stream)
+
+    def refold(self, stream=None):
+        sta_refold(self.h, stream)
 
     def last_touched(self, stream=None) -> int:
         return sta_last_touched(self.h, stream)

@@ -195,6 +195,11 @@ int sta_full_rebuild(sta_ctx *x, const uint8_t *mask, int mask_on_device, void *
     return launch_rebuild(c, s);
 }
 
+int sta_refold(sta_ctx *x, void *stream) {
+    if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    return launch_rebuild(&x->c, (cudaStream_t)stream);
+}
+
 int sta_apply_edits(sta_ctx *x, const sta_edit *edits, int64_t n_edits, void *stream) {
     if (!x) return fail(STA_EINVAL, "ctx is NULL");
     Ctx *c = &x->c;
