@@ -192,6 +192,7 @@ int sta_full_rebuild(sta_ctx *x, const uint8_t *mask, int mask_on_device, void *
             x->h2d_pending = true;
         }
     }
+    STA_TRY(launch_mask_bits(c, s));
     return launch_rebuild(c, s);
 }
 

@@ -18,13 +18,9 @@ namespace sta {
 namespace {
 
 struct FoldArgs {
-    const int32_t *__restrict__ cptr;
-    const int32_t *__restrict__ ccode;
-    const uint8_t *__restrict__ mask;
+    const int4 *__restrict__ bmeta;     // per block: value offset, row stride/diag, c0, c1
+    const int32_t *__restrict__ ccode;  // contributor codes, bit 31 = active
     const double *__restrict__ Ke;
-    const int32_t *__restrict__ adj_ptr;
-    const int32_t *__restrict__ adj;
-    const int32_t *__restrict__ block_node;
     double *__restrict__ val;
     double eps;
 };
@@ -39,127 +35,364 @@ __device__ __forceinline__ int pair_index(int a, int b) {  // a < b
     return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);
 }
 
-// Diagonal block (a, a): every contributor uses its own diagonal 3x3 block (la == lb), whose
-// 6 stored entries are folded; the 9 outputs mirror them (the element matrices are exactly
-// symmetric, so (i, j) and (j, i) folds are identical).
-__device__ __forceinline__ void fold_diag(const FoldArgs &A, int32_t c, int32_t c1,
-                                          double *__restrict__ out, int rs) {
-    double acc[6];
-    for (; c < c1; ++c)
-        if (A.mask[A.ccode[c] >> 4]) break;
-    if (c == c1) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) acc[k] = 0.0;
+// The 9 operands (i, j) one contributor supplies to a block, read with 16-byte loads from
+// its stored run:
+//   diagonal block (la == lb): the 6-run of (la, la), mirrored;
+//   off-diagonal, la < lb:      the 9-run of (la, lb), row-major;
+//   off-diagonal, la > lb:      the 9-run of (lb, la), transposed.
+// Folding a diagonal block with 9 accumulators gives (i, j) and (j, i) the same sequence of
+// operands, so the mirrored outputs equal those of a 6-accumulator fold.
+__device__ __forceinline__ void load_contrib(const FoldArgs &A, int32_t code, double v[9]) {
+    const int la = (code >> 2) & 3, lb = code & 3;
+    const double *rec = A.Ke + (size_t)code_tet(code) * KE_STRIDE;
+    if (la == lb) {
+        const double2 *r = reinterpret_cast<const double2 *>(rec + 6 * la);
+        const double2 x = __ldg(r), y = __ldg(r + 1), z = __ldg(r + 2);
+        // 6-run order (0,0) (0,1) (0,2) (1,1) (1,2) (2,2)
+        v[0] = x.x; v[1] = x.y; v[2] = y.x;
+        v[3] = x.y; v[4] = y.y; v[5] = z.x;
+        v[6] = y.x; v[7] = z.x; v[8] = z.y;
     } else {
-        int32_t code = A.ccode[c];
-        const double *r = A.Ke + (size_t)(code >> 4) * KE_STRIDE + 6 * ((code >> 2) & 3);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) acc[k] = plus_zero(r[k]);
-        for (++c; c < c1; ++c) {
-            code = A.ccode[c];
-            if (!A.mask[code >> 4]) continue;
-            r = A.Ke + (size_t)(code >> 4) * KE_STRIDE + 6 * ((code >> 2) & 3);
-            double v[6];
-#pragma unroll
-            for (int k = 0; k < 6; ++k) v[k] = r[k];
-#pragma unroll
-            for (int k = 0; k < 6; ++k) acc[k] += v[k];
-        }
-    }
-    if (A.eps != 0.0) {
-        acc[0] += A.eps;
-        acc[3] += A.eps;
-        acc[5] += A.eps;
-    }
-    out[0] = acc[0];          out[1] = acc[1];          out[2] = acc[2];
-    out[rs + 0] = acc[1];     out[rs + 1] = acc[3];     out[rs + 2] = acc[4];
-    out[2 * rs + 0] = acc[2]; out[2 * rs + 1] = acc[4]; out[2 * rs + 2] = acc[5];
-}
-
-// Off-diagonal block: contributor (t, la, lb) supplies K^(t)[3la+i][3lb+j], stored as the
-// 9-run of pair (min, max) read row-major when la < lb and transposed otherwise.
-__device__ __forceinline__ const double *off_run(const FoldArgs &A, int32_t code, int &si, int &sj) {
-    int la = (code >> 2) & 3, lb = code & 3;
-    int lo = la < lb ? la : lb, hi = la < lb ? lb : la;
-    si = la < lb ? 3 : 1;
-    sj = la < lb ? 1 : 3;
-    return A.Ke + (size_t)(code >> 4) * KE_STRIDE + 24 + 9 * pair_index(lo, hi);
-}
-
-__device__ __forceinline__ void fold_off(const FoldArgs &A, int32_t c, int32_t c1,
-                                         double *__restrict__ out, int rs) {
-    double acc[9];
-    for (; c < c1; ++c)
-        if (A.mask[A.ccode[c] >> 4]) break;
-    if (c == c1) {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) acc[k] = 0.0;
-    } else {
-        int si, sj;
-        const double *r = off_run(A, A.ccode[c], si, sj);
+        const int lo = la < lb ? la : lb, hi = la < lb ? lb : la;
+        const double2 *r = reinterpret_cast<const double2 *>(rec + 24 + 10 * pair_index(lo, hi));
+        const double2 p0 = __ldg(r), p1 = __ldg(r + 1), p2 = __ldg(r + 2), p3 = __ldg(r + 3),
+                      p4 = __ldg(r + 4);
+        const double w[9] = {p0.x, p0.y, p1.x, p1.y, p2.x, p2.y, p3.x, p3.y, p4.x};
+        const bool tr = la > lb;
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int j = 0; j < 3; ++j) acc[3 * i + j] = plus_zero(r[si * i + sj * j]);
-        for (++c; c < c1; ++c) {
-            int32_t code = A.ccode[c];
-            if (!A.mask[code >> 4]) continue;
-            r = off_run(A, code, si, sj);
-            double v[9];
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int j = 0; j < 3; ++j) v[3 * i + j] = r[si * i + sj * j];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) acc[k] += v[k];
-        }
+            for (int j = 0; j < 3; ++j) v[3 * i + j] = tr ? w[3 * j + i] : w[3 * i + j];
+    }
+}
+
+// first position >= c in [c, ce) whose contributor is active (code bit 31 set)
+__device__ __forceinline__ int32_t next_active(const FoldArgs &A, int32_t c, int32_t ce) {
+    while (c < ce && __ldg(A.ccode + c) >= 0) ++c;
+    return c;
+}
+
+struct BlockOut {
+    double *out;
+    int rs;
+    bool diag;
+};
+
+__device__ __forceinline__ void write_block(const FoldArgs &A, const BlockOut &o, double acc[9]) {
+    if (o.diag && A.eps != 0.0) {
+        acc[0] += A.eps;
+        acc[4] += A.eps;
+        acc[8] += A.eps;
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) out[i * rs + j] = acc[3 * i + j];
+        for (int j = 0; j < 3; ++j) o.out[i * o.rs + j] = acc[3 * i + j];
 }
 
-__device__ __forceinline__ void fold_block(const FoldArgs &A, int32_t g) {
-    const int32_t a = A.block_node[g], b = A.adj[g];
-    const int32_t s = A.adj_ptr[a], d = A.adj_ptr[a + 1] - s;
-    double *out = A.val + (9 * (int64_t)s + 3 * (int64_t)(g - s));
-    const int rs = 3 * d;
-    if (a == b)
-        fold_diag(A, A.cptr[g], A.cptr[g + 1], out, rs);
-    else
-        fold_off(A, A.cptr[g], A.cptr[g + 1], out, rs);
+// Lockstep fold.  On GB300 a warp-wide FP64 instruction costs the same however many lanes
+// are active, and FP64 issue is the scarcest resource, so every FP64 add instruction should
+// carry 32 useful lanes.  Each warp works in two phases over its share of the blocks:
+//
+//  stage: blocks are taken in order; the active contributor codes of each block are
+//         compacted, in list order, into the warp's shared buffer.  Blocks with no active
+//         contributor are written (+0.0) and blocks with one are written (+0.0 + c) right
+//         away, with no FP64 operation.  Integer and load work only.
+//  fold:  lanes claim staged blocks in order as they become free.  A claim loads the
+//         operands of the block's first contribution into v and of its second into the
+//         accumulators; the next iteration forms (+0.0 + c1) + c2, and every later iteration
+//         adds one more contribution while the loads of the following one are in flight.
+//         Every iteration of a busy lane is one useful 9-wide FP64 add.
+//
+// Items are handed out in chunks of 32: warp w owns chunks w, w + W, w + 2W, ... (W warps in
+// the grid).  MODE 0: item = block id (whole pattern) -- a chunk is 32 consecutive blocks
+// whose codes are contiguous, staged with coalesced windows and ballots; MODE 1: item
+// indexes a list of block ids whose length is read from device memory (streaming), staged
+// one block per lane.
+constexpr int FOLD_WARPS = 4;       // warps per CTA
+constexpr int STAGE_BLOCKS = 192;   // staged blocks per warp
+constexpr int STAGE_CODES = 1280;   // staged active codes per warp (>= contributors of any block)
+constexpr int STAGE_WIN = 8;        // 32-code windows of one staging round held in registers
+constexpr int LONG_BLOCK = 8;       // staged blocks with this many contributors are claimed first
+
+__device__ __forceinline__ int warp_inclusive_scan(int x, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
 }
 
-__global__ void __launch_bounds__(256) k_rebuild(FoldArgs A, int64_t nblocks) {
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nblocks;
-         g += (int64_t)gridDim.x * blockDim.x)
-        fold_block(A, (int32_t)g);
+// bits of positions [0, n) of a 32-bit window (n clamped to [0, 32])
+__device__ __forceinline__ unsigned below(int n) {
+    return n <= 0 ? 0u : (n >= 32 ? 0xffffffffu : ((1u << n) - 1u));
+}
+
+// A block with at most one active contributor: written directly (+0.0, or +0.0 + c).
+__device__ __forceinline__ void write_small_block(const FoldArgs &A, const int4 bm, int cnt,
+                                                  int32_t code) {
+    double acc[9];
+    if (cnt == 0) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) acc[q] = 0.0;
+    } else {
+        load_contrib(A, code, acc);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) acc[q] = plus_zero(acc[q]);
+    }
+    write_block(A, BlockOut{A.val + bm.x, bm.y >> 1, (bm.y & 1) != 0}, acc);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(FOLD_WARPS * 32)
+k_fold(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *__restrict__ count,
+       int64_t nitems_static) {
+    __shared__ int4 sblk_all[FOLD_WARPS][STAGE_BLOCKS];
+    __shared__ int32_t scode_all[FOLD_WARPS][STAGE_CODES];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int4 *sblk = sblk_all[wid];
+    int32_t *scode = scode_all[wid];
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nitems = MODE == 0 ? nitems_static : (int64_t)*count;
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    int64_t p_base = 0;  // warp-uniform position in this warp's item sequence
+    bool more = true;
+    while (more) {
+        // ------------------------------------------------------------ stage
+        int nlong = 0, nshort = 0, nc = 0;
+        while (nlong + nshort + 32 <= STAGE_BLOCKS) {
+            if (MODE == 0) {
+                // the rest of the current chunk: consecutive blocks, contiguous codes
+                const int off = (int)(p_base & 31);
+                const int64_t chunk_first = ((p_base >> 5) * nwarps + warp) * 32;
+                const int64_t g = chunk_first + off + lane;
+                const bool valid = lane < 32 - off && g < nitems;
+                const unsigned validm = __ballot_sync(FULL, valid);
+                if (!validm) {
+                    more = false;
+                    break;
+                }
+                const int nv = __popc(validm);  // valid lanes form a prefix
+                int4 bm = make_int4(0, 0, 0, 0);
+                if (valid) bm = __ldg(A.bmeta + g);
+                const int32_t r0 = __shfl_sync(FULL, bm.z, 0);
+                const int32_t r1 = __shfl_sync(FULL, bm.w, nv - 1);
+                const int nwin = (r1 - r0 + 31) >> 5;
+                // all windows' code loads issued before any is used
+                int32_t cw[STAGE_WIN];
+#pragma unroll
+                for (int w = 0; w < STAGE_WIN; ++w) {
+                    const int32_t c = r0 + 32 * w + lane;
+                    cw[w] = (w < nwin && c < r1) ? __ldg(A.ccode + c) : 0;
+                }
+                // pass 1: active codes before each block start (lo) and in the whole range
+                int lo = 0, total = 0;
+#pragma unroll
+                for (int w = 0; w < STAGE_WIN; ++w) {
+                    if (w < nwin) {
+                        const unsigned m = __ballot_sync(FULL, cw[w] < 0);
+                        lo += __popc(m & below(bm.z - (r0 + 32 * w)));
+                        total += __popc(m);
+                    }
+                }
+                for (int w = STAGE_WIN; w < nwin; ++w) {
+                    const int32_t c = r0 + 32 * w + lane;
+                    const unsigned m = __ballot_sync(FULL, c < r1 && __ldg(A.ccode + c) < 0);
+                    lo += __popc(m & below(bm.z - (r0 + 32 * w)));
+                    total += __popc(m);
+                }
+                int hi = __shfl_down_sync(FULL, lo, 1);
+                if (lane == nv - 1) hi = total;
+                const int cnt = valid ? hi - lo : 0;
+                // blocks that fit: lo + cnt within the free code space (a prefix of lanes)
+                const bool fits = valid && nc + hi <= STAGE_CODES;
+                const unsigned fitm = __ballot_sync(FULL, fits);
+                const int nfit = __popc(fitm);
+                if (nfit > 0) {
+                    // pass 2: compact the active codes of the fitting blocks, in list order
+                    const int32_t f1 = __shfl_sync(FULL, bm.w, nfit - 1);
+                    int run = nc;
+#pragma unroll
+                    for (int w = 0; w < STAGE_WIN; ++w) {
+                        if (w < nwin) {
+                            const int32_t c = r0 + 32 * w + lane;
+                            const bool act = c < f1 && cw[w] < 0;
+                            const unsigned m = __ballot_sync(FULL, act);
+                            if (act) scode[run + __popc(m & lt_mask)] = cw[w];
+                            run += __popc(m);
+                        }
+                    }
+                    for (int w = STAGE_WIN; w < nwin; ++w) {
+                        const int32_t c = r0 + 32 * w + lane;
+                        int32_t code = 0;
+                        const bool act = c < f1 && (code = __ldg(A.ccode + c)) < 0;
+                        const unsigned m = __ballot_sync(FULL, act);
+                        if (act) scode[run + __popc(m & lt_mask)] = code;
+                        run += __popc(m);
+                    }
+                    __syncwarp();
+                    // long blocks fill the staging list from the front, short ones from the
+                    // back: claims take long blocks first (longest-processing-time order)
+                    const unsigned longm = __ballot_sync(FULL, fits && cnt >= LONG_BLOCK);
+                    const unsigned shortm = __ballot_sync(FULL, fits && cnt >= 2 && cnt < LONG_BLOCK);
+                    if (fits) {
+                        if (cnt < 2)
+                            write_small_block(A, bm, cnt, cnt ? scode[nc + lo] : 0);
+                        else if (cnt >= LONG_BLOCK)
+                            sblk[nlong + __popc(longm & lt_mask)] = make_int4(bm.x, bm.y, nc + lo, cnt);
+                        else
+                            sblk[STAGE_BLOCKS - 1 - nshort - __popc(shortm & lt_mask)] =
+                                make_int4(bm.x, bm.y, nc + lo, cnt);
+                    }
+                    nlong += __popc(longm);
+                    nshort += __popc(shortm);
+                    nc += __shfl_sync(FULL, hi, nfit - 1);
+                    p_base += nfit;
+                }
+                if (nfit < nv) break;  // code space full: fold, then continue this chunk
+            } else {
+                const int64_t p = p_base + lane;
+                const int64_t item = ((p >> 5) * nwarps + warp) * 32 + (p & 31);
+                const bool valid = item < nitems;
+                int4 bm = make_int4(0, 0, 0, 0);
+                int cnt = 0;
+                if (valid) {
+                    bm = __ldg(A.bmeta + __ldg(list + item));
+                    for (int32_t c = bm.z; c < bm.w; ++c) cnt += __ldg(A.ccode + c) < 0;
+                }
+                const int inc = warp_inclusive_scan(cnt, lane);
+                const bool fits = valid && nc + inc <= STAGE_CODES;
+                const unsigned fitm = __ballot_sync(FULL, fits);
+                const unsigned longm = __ballot_sync(FULL, fits && cnt >= LONG_BLOCK);
+                const unsigned shortm = __ballot_sync(FULL, fits && cnt >= 2 && cnt < LONG_BLOCK);
+                if (fits) {
+                    const int at = nc + inc - cnt;
+                    int j = 0;
+                    for (int32_t c = bm.z; c < bm.w; ++c) {
+                        const int32_t code = __ldg(A.ccode + c);
+                        if (code < 0) scode[at + j++] = code;
+                    }
+                    if (cnt < 2)
+                        write_small_block(A, bm, cnt, cnt ? scode[at] : 0);
+                    else if (cnt >= LONG_BLOCK)
+                        sblk[nlong + __popc(longm & lt_mask)] = make_int4(bm.x, bm.y, at, cnt);
+                    else
+                        sblk[STAGE_BLOCKS - 1 - nshort - __popc(shortm & lt_mask)] =
+                            make_int4(bm.x, bm.y, at, cnt);
+                }
+                const int nfit = __popc(fitm);  // fitting lanes form a prefix
+                if (nfit > 0) nc += __shfl_sync(FULL, inc, nfit - 1);
+                nlong += __popc(longm);
+                nshort += __popc(shortm);
+                p_base += nfit;
+                if (nfit < 32) {
+                    more = __any_sync(FULL, valid);
+                    break;
+                }
+            }
+        }
+        __syncwarp();
+        // ------------------------------------------------------------ fold
+        int next_blk = 0;  // warp-uniform: staged blocks claimed so far
+        bool busy = false;
+        int k = 0, kend = 0;
+        BlockOut o{nullptr, 0, false};
+        // acc: accumulators; v: operands of the next contribution to add; w: of the one after
+        // (two contributions in flight per lane).  Right after a claim, acc holds the raw
+        // operands of contribution 2 and v those of contribution 1 (fresh).
+        double acc[9], v[9], w[9];
+        bool fresh = false, have_w = false;
+        // Claims come right after a block is written, so the operand loads of a newly
+        // claimed block are in flight for a whole iteration, like every other prefetch.
+        auto claim_blocks = [&]() {
+            const unsigned claim = __ballot_sync(FULL, !busy);
+            if (!busy) {
+                const int b = next_blk + __popc(claim & lt_mask);
+                if (b < nlong + nshort) {
+                    const int4 sb = sblk[b < nlong ? b : STAGE_BLOCKS - 1 - (b - nlong)];
+                    o = BlockOut{A.val + sb.x, sb.y >> 1, (sb.y & 1) != 0};
+                    k = sb.z;
+                    kend = sb.z + sb.w;
+                    load_contrib(A, scode[k], v);
+                    load_contrib(A, scode[k + 1], acc);
+                    k += 2;
+                    have_w = k < kend;
+                    if (have_w) load_contrib(A, scode[k++], w);
+                    busy = true;
+                    fresh = true;
+                }
+            }
+            next_blk += __popc(claim);
+        };
+        claim_blocks();
+        while (__any_sync(FULL, busy)) {
+            if (busy) {
+                if (fresh) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) v[q] = plus_zero(v[q]);
+                    fresh = false;
+                }
+#pragma unroll
+                for (int q = 0; q < 9; ++q) acc[q] += v[q];
+                if (have_w) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) v[q] = w[q];
+                    have_w = k < kend;
+                    if (have_w) load_contrib(A, scode[k++], w);
+                } else {
+                    write_block(A, o, acc);
+                    busy = false;
+                }
+            }
+            if (__any_sync(FULL, !busy)) claim_blocks();
+        }
+        __syncwarp();
+    }
 }
 
 // Streaming, phase 1: apply the frame's mask changes and claim each touched block for the
 // lowest candidate index (edited tet k, local pair s -> candidate 16 k + s).
 // edited[k] = tet id | (new state << 31).
 __global__ void k_stream_apply(const int32_t *__restrict__ edited, int64_t m,
-                               const int32_t *__restrict__ tblk, uint8_t *__restrict__ mask,
+                               const int32_t *__restrict__ tblk, const int32_t *__restrict__ cslot,
+                               int32_t *__restrict__ ccode, uint8_t *__restrict__ mask,
                                int32_t *__restrict__ owner, unsigned long long *counters) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k == 0) counters[1] = 0ull;
     if (k >= m) return;
     uint32_t w = (uint32_t)edited[k];
     int32_t t = (int32_t)(w & 0x7fffffffu);
-    mask[t] = (uint8_t)(w >> 31);
+    const uint32_t on = w >> 31;
+    mask[t] = (uint8_t)on;
 #pragma unroll
-    for (int s = 0; s < 16; ++s) atomicMin(&owner[tblk[16 * (int64_t)t + s]], (int32_t)(16 * k + s));
+    for (int s = 0; s < 16; ++s) {
+        const int32_t slot = cslot[16 * (int64_t)t + s];
+        ccode[slot] = (int32_t)(((uint32_t)ccode[slot] & ~CODE_ACTIVE) | (on << 31));
+        atomicMin(&owner[tblk[16 * (int64_t)t + s]], (int32_t)(16 * k + s));
+    }
 }
 
-// Streaming, phase 2: the owner of each touched block re-folds it and releases the claim.
-// A non-owner reads either the owner's index or INT32_MAX, never its own index, so the
-// release does not race with the ownership test.
-__global__ void __launch_bounds__(256)
-k_stream_fold(FoldArgs A, const int32_t *__restrict__ edited, int64_t m,
-              const int32_t *__restrict__ tblk, int32_t *__restrict__ owner,
-              unsigned long long *counters) {
+// Activity bits of all contributor codes from the mask (full rebuild with a new mask).
+__global__ void k_mask_bits(int32_t *__restrict__ ccode, int64_t n, const uint8_t *__restrict__ mask) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t code = (uint32_t)ccode[k];
+        const uint32_t on = mask[code_tet((int32_t)code)] ? CODE_ACTIVE : 0u;
+        ccode[k] = (int32_t)((code & ~CODE_ACTIVE) | on);
+    }
+}
+
+// Streaming, phase 2: the owner of each touched block appends it to the fold list and
+// releases the claim.  A non-owner reads either the owner's index or INT32_MAX, never its
+// own index, so the release does not race with the ownership test.  The list order depends
+// on scheduling; the values do not (each block is folded independently).
+__global__ void k_stream_compact(const int32_t *__restrict__ edited, int64_t m,
+                                 const int32_t *__restrict__ tblk, int32_t *__restrict__ owner,
+                                 int32_t *__restrict__ list, unsigned long long *counters) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool mine = false;
     int32_t g = 0;
@@ -168,18 +401,24 @@ k_stream_fold(FoldArgs A, const int32_t *__restrict__ edited, int64_t m,
         g = tblk[16 * (int64_t)t + (i & 15)];
         mine = owner[g] == (int32_t)i;
     }
-    unsigned ball = __ballot_sync(0xffffffffu, mine);
-    if ((threadIdx.x & 31) == 0 && ball) atomicAdd(&counters[1], (unsigned long long)__popc(ball));
+    const unsigned ball = __ballot_sync(0xffffffffu, mine);
+    unsigned long long base = 0;
+    const int lane = threadIdx.x & 31;
+    if (lane == 0 && ball) base = atomicAdd(&counters[1], (unsigned long long)__popc(ball));
+    base = __shfl_sync(0xffffffffu, base, 0);
     if (mine) {
-        fold_block(A, g);
+        list[base + __popc(ball & ((1u << lane) - 1u))] = g;
         owner[g] = INT32_MAX;
     }
 }
 
-FoldArgs fold_args(const Ctx *c) {
-    return FoldArgs{c->cptr, c->ccode, c->mask, c->Ke, c->adj_ptr, c->adj, c->block_node,
-                    c->val, c->eps};
-}
+}  // namespace
+
+int max_block_contributors() { return STAGE_CODES; }
+
+namespace {
+
+FoldArgs fold_args(const Ctx *c) { return FoldArgs{c->bmeta, c->ccode, c->Ke, c->val, c->eps}; }
 
 }  // namespace
 
@@ -198,9 +437,20 @@ int persistent_grid(const Ctx *c, const void *kernel, int threads, int64_t items
 
 int launch_rebuild(Ctx *c, cudaStream_t s) {
     if (c->nblocks == 0) return STA_OK;
-    int threads = 256;
-    int grid = persistent_grid(c, (const void *)k_rebuild, threads, c->nblocks);
-    k_rebuild<<<grid, threads, 0, s>>>(fold_args(c), c->nblocks);
+    const int threads = FOLD_WARPS * 32;
+    int grid = persistent_grid(c, (const void *)k_fold<0>, threads, c->nblocks);
+    k_fold<0><<<grid, threads, 0, s>>>(fold_args(c), nullptr, nullptr, c->nblocks);
+    STA_CUDA_TRY(cudaGetLastError());
+    return STA_OK;
+}
+
+int launch_mask_bits(Ctx *c, cudaStream_t s) {
+    if (c->T == 0) return STA_OK;
+    const int64_t n = 16 * c->T;
+    int64_t grid = (n + 255) / 256;
+    const int64_t cap = (int64_t)c->num_sms * 8;
+    if (grid > cap) grid = cap;
+    k_mask_bits<<<(unsigned)grid, 256, 0, s>>>(c->ccode, n, c->mask);
     STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;
 }
@@ -210,11 +460,16 @@ int launch_stream(Ctx *c, int64_t m, cudaStream_t s) {
         STA_CUDA_TRY(cudaMemsetAsync(c->counters + 1, 0, sizeof(unsigned long long), s));
         return STA_OK;
     }
-    int64_t g1 = (m + 255) / 256, g2 = (16 * m + 255) / 256;
-    k_stream_apply<<<(unsigned)g1, 256, 0, s>>>(c->d_edited, m, c->tblk, c->mask, c->owner,
-                                                c->counters);
-    k_stream_fold<<<(unsigned)g2, 256, 0, s>>>(fold_args(c), c->d_edited, m, c->tblk, c->owner,
-                                               c->counters);
+    const int threads = 256;
+    const int64_t g1 = (m + threads - 1) / threads, g2 = (16 * m + threads - 1) / threads;
+    k_stream_apply<<<(unsigned)g1, threads, 0, s>>>(c->d_edited, m, c->tblk, c->cslot, c->ccode,
+                                                    c->mask, c->owner, c->counters);
+    k_stream_compact<<<(unsigned)g2, threads, 0, s>>>(c->d_edited, m, c->tblk, c->owner,
+                                                      c->touched, c->counters);
+    // the touched count is only known on the device: size the grid for the upper bound
+    const int fthreads = FOLD_WARPS * 32;
+    int grid = persistent_grid(c, (const void *)k_fold<1>, fthreads, 16 * m);
+    k_fold<1><<<grid, fthreads, 0, s>>>(fold_args(c), c->touched, c->counters + 1, 0);
     STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;
 }

@@ -253,6 +253,40 @@ __global__ void k_contrib_fill(const int32_t *tblk, int64_t T, const int64_t *cp
     }
 }
 
+// cslot[16 t + 4 la + lb] = position of the contribution (t, la, lb) in its block's list
+__global__ void k_contrib_slots(const int32_t *ccode, int64_t T, int32_t *cslot) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < 16 * T;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int32_t code = ccode[k];
+        cslot[16 * (int64_t)code_tet(code) + ((code >> 2) & 3) * 4 + (code & 3)] = (int32_t)k;
+    }
+}
+
+// Per-block record used by the folds: first value index, row stride and diagonal flag,
+// contributor range.
+__global__ void k_block_meta(int64_t nblocks, const int32_t *block_node, const int32_t *adj_ptr,
+                             const int32_t *adj, const int64_t *cptr64, int4 *bmeta) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nblocks;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        int32_t a = block_node[g], s = adj_ptr[a], d = adj_ptr[a + 1] - s;
+        int32_t off = 9 * s + 3 * ((int32_t)g - s);
+        bmeta[g] = make_int4(off, (3 * d) << 1 | (adj[g] == a ? 1 : 0), (int32_t)cptr64[g],
+                             (int32_t)cptr64[g + 1]);
+    }
+}
+
+__global__ void k_max_i32(const int32_t *in, int64_t m, int64_t *out) {
+    int32_t mx = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        mx = in[i] > mx ? in[i] : mx;
+    for (int o = 16; o > 0; o >>= 1) {
+        int32_t y = __shfl_down_sync(0xffffffffu, mx, o);
+        mx = y > mx ? y : mx;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long *)out, (unsigned long long)mx);
+}
+
 __global__ void k_to_i32(const int64_t *in, int64_t m, int32_t *out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -326,7 +360,10 @@ int build_pattern(Ctx *c, cudaStream_t s) {
     STA_TRY(dev_alloc(c, &c->scat, 144 * T));
     STA_TRY(dev_alloc(c, &c->cptr, nblocks + 1));
     STA_TRY(dev_alloc(c, &c->ccode, 16 * T));
+    STA_TRY(dev_alloc(c, &c->cslot, 16 * T));
+    STA_TRY(dev_alloc(c, &c->bmeta, nblocks));
     STA_TRY(dev_alloc(c, &c->owner, nblocks));
+    STA_TRY(dev_alloc(c, &c->touched, nblocks));
 
     k_adj_fill<<<grid_for(n + 1), TPB, 0, s>>>(n, nt_ptr, scratch, adj_ptr64, c->adj_ptr,
                                                c->adj, c->block_node);
@@ -339,11 +376,23 @@ int build_pattern(Ctx *c, cudaStream_t s) {
     STA_TRY(sc.get(&cptr64, nblocks + 1));
     STA_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nblocks, s));
     k_contrib_count<<<grid_for(16 * T), TPB, 0, s>>>(c->tblk, T, cnt);
+    STA_CUDA_TRY(cudaMemsetAsync(tiles, 0, sizeof(int64_t), s));
+    k_max_i32<<<grid_for(nblocks > 0 ? nblocks : 1), TPB, 0, s>>>(cnt, nblocks, tiles);
+    int64_t max_contrib = 0;
+    STA_CUDA_TRY(cudaMemcpyAsync(&max_contrib, tiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    STA_CUDA_TRY(cudaStreamSynchronize(s));
+    if (max_contrib > max_block_contributors())
+        return fail(STA_ERANGE, "a node pair is shared by " + std::to_string(max_contrib) +
+                                    " tetrahedra; the fold supports at most " +
+                                    std::to_string(max_block_contributors()));
     STA_TRY(exclusive_scan(c, cnt, nblocks, cptr64, tiles, s));
     STA_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nblocks, s));
     k_contrib_fill<<<grid_for(16 * T), TPB, 0, s>>>(c->tblk, T, cptr64, cnt, c->ccode);
     k_sort_segments<<<grid_for(nblocks), TPB, 0, s>>>(cptr64, nblocks, c->ccode);
     k_to_i32<<<grid_for(nblocks + 1), TPB, 0, s>>>(cptr64, nblocks + 1, c->cptr);
+    k_contrib_slots<<<grid_for(16 * T), TPB, 0, s>>>(c->ccode, T, c->cslot);
+    k_block_meta<<<grid_for(nblocks), TPB, 0, s>>>(nblocks, c->block_node, c->adj_ptr, c->adj,
+                                                   cptr64, c->bmeta);
     k_fill_i32<<<grid_for(nblocks), TPB, 0, s>>>(c->owner, nblocks, INT32_MAX);
     STA_CUDA_TRY(cudaGetLastError());
     STA_CUDA_TRY(cudaStreamSynchronize(s));

@@ -93,6 +93,7 @@ __device__ __forceinline__ bool element_record(double4_32a x0, double4_32a x1, d
                                    : __fma_rn(P[a][i], gc(g[b], i), __fma_rn(Q[a][i], gc(g[b], i), D));
                     o[3 * i + j] = v;
                 }
+            o[9] = 0.0;  // pad to a 16-byte aligned run
         }
     return true;
 }

@@ -34,28 +34,32 @@ int fail(int code, const std::string &msg);
 
 // ------------------------------------------------------------------------------------
 // Element cache record: the 78 unique entries of the symmetric 12x12 element matrix,
-// grouped by 3x3 node-pair block so that one block is one contiguous run:
+// grouped by 3x3 node-pair block so that one block is one contiguous, 16-byte aligned run:
 //   diagonal block (a, a), a = 0..3:  6 entries (i <= j, row-major) at 6a
-//   off-diagonal block (a, b), a < b:   9 entries (i, j row-major)    at 24 + 9 * pair(a, b)
-// with pair(0,1..3) = 0..2, pair(1,2..3) = 3..4, pair(2,3) = 5.
+//   off-diagonal block (a, b), a < b:   9 entries (i, j row-major) + 1 pad at 24 + 10 pair(a, b)
+// with pair(0,1..3) = 0..2, pair(1,2..3) = 3..4, pair(2,3) = 5.  84 doubles (672 B) per
+// tetrahedron; every run starts on a 16-byte boundary so a fold reads it with 16-byte loads.
 // ------------------------------------------------------------------------------------
-constexpr int KE_STRIDE = 78;
+constexpr int KE_STRIDE = 84;
 
 __host__ __device__ inline int ke_diag_off(int a) { return 6 * a; }
 __host__ __device__ inline int ke_pair(int a, int b) {  // a < b
     return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);
 }
-__host__ __device__ inline int ke_off_off(int a, int b) { return 24 + 9 * ke_pair(a, b); }
+__host__ __device__ inline int ke_off_off(int a, int b) { return 24 + 10 * ke_pair(a, b); }
 // index of (i, j), i <= j, inside a diagonal 6-run
 __host__ __device__ inline int ke_tri(int i, int j) {
     return i == 0 ? j : (i == 1 ? 2 + j : 5);
 }
 
 // Contributor code of a node-pair block: tetrahedron id and the local indices of the
-// block's row node (la) and column node (lb) inside that tetrahedron.
+// block's row node (la) and column node (lb) inside that tetrahedron; bit 31 holds the
+// tetrahedron's current activity (kept equal to the mask by every call that changes it).
+constexpr uint32_t CODE_ACTIVE = 0x80000000u;
 __host__ __device__ inline int32_t contrib_code(int32_t t, int la, int lb) {
     return (t << 4) | (la << 2) | lb;
 }
+__host__ __device__ inline int32_t code_tet(int32_t code) { return (code >> 4) & 0x07ffffff; }
 
 // ------------------------------------------------------------------------------------
 // Context
@@ -83,12 +87,15 @@ struct Ctx {
     int32_t *scat = nullptr;       // T x 144: CSR index of local entry (p, q)
     int32_t *cptr = nullptr;       // nblocks + 1: contributor list of each block
     int32_t *ccode = nullptr;      // 16 T: contributor codes, ascending tetrahedron id
+    int32_t *cslot = nullptr;      // T x 16: position in ccode of tet t's pair (la, lb)
+    int4 *bmeta = nullptr;         // nblocks: {value offset, 3 deg << 1 | diagonal, c0, c1}
 
     // state
     double *Ke = nullptr;       // T x 78 element cache
     uint8_t *mask = nullptr;    // T
     double *val = nullptr;      // nnz
     int32_t *owner = nullptr;   // nblocks: streaming dedupe slot, INT32_MAX when free
+    int32_t *touched = nullptr; // nblocks: list of blocks touched by the current frame
     unsigned long long *counters = nullptr;  // [0] bad elements, [1] touched blocks
 
     // streaming staging
@@ -126,5 +133,7 @@ int launch_elements(Ctx *c, bool active_only, cudaStream_t s);   // sta_element.
 int launch_expand_elements(Ctx *c, const int32_t *ids, int64_t n, double *out, cudaStream_t s);
 int launch_rebuild(Ctx *c, cudaStream_t s);                      // sta_assemble.cu
 int launch_stream(Ctx *c, int64_t n_edited, cudaStream_t s);
+int launch_mask_bits(Ctx *c, cudaStream_t s);                    // codes <- mask
+int max_block_contributors();  // largest contributor list a fold can stage
 
 }  // namespace sta
