@@ -181,6 +181,30 @@ int sta_set_params(sta_ctx *ctx, const double *nodes, const double *young,
 int sta_element_matrices(sta_ctx *ctx, const int32_t *tet_ids, int64_t n, double *out,
                          void *stream);
 
+/*
+ * sta_apply_edits_noalloc -- the same streaming update as sta_apply_edits, for callers that
+ * must not allocate (no counterpart in the paper).  sta_apply_edits may grow a pinned host
+ * buffer and a device buffer on its first call or when a frame edits more tetrahedra than
+ * before; a frame loop that must never stall on cudaMalloc, a process whose GPU memory is
+ * held by a framework's caching allocator, or work about to be captured into a CUDA graph
+ * cannot allow that.  This variant calls no allocator: its per-call scratch (edited-tet list,
+ * touched-block list, counters) is one fixed device array of about
+ * 68 x STA_NOALLOC_MAX_EDITED bytes (2.2 MB) that every GPU loading the library holds until
+ * the process exits.  Arguments, validation, results and errors are those of
+ * sta_apply_edits, plus:
+ *  - at most STA_NOALLOC_MAX_EDITED edited tetrahedra per call (a swap counts two); more
+ *    is rejected with STA_ERANGE before any device work;
+ *  - the context's device must be current; the first call on each device looks up the
+ *    array's device address (cudaGetSymbolAddress), so make that first call before any
+ *    stream capture;
+ *  - all calls, on every context and stream of a device, share the one array: calls that
+ *    overlap on the GPU race and must be serialised by the caller;
+ *  - the edit list is copied from pageable host memory, so the call returns only after that
+ *    copy has been staged.
+ */
+#define STA_NOALLOC_MAX_EDITED 32768
+int sta_apply_edits_noalloc(sta_ctx *ctx, const sta_edit *edits, int64_t n_edits, void *stream);
+
 /* Human-readable message of the last error on the calling thread. */
 const char *sta_last_error(void);
 const char *sta_status_string(int status);

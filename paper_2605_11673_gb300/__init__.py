@@ -27,8 +27,9 @@ EXPORTED = (
     "sta_default_options", "sta_create", "sta_destroy", "sta_full_rebuild", "sta_apply_edits",
     "sta_last_touched", "sta_refold", "sta_csr", "sta_scatter_map", "sta_sizes", "sta_mask",
     "sta_recompute_elements", "sta_set_params", "sta_element_matrices", "sta_last_error",
-    "sta_status_string",
+    "sta_status_string", "sta_apply_edits_noalloc",
 )
+STA_NOALLOC_MAX_EDITED = 32768
 
 
 class StaError(RuntimeError):
@@ -66,6 +67,7 @@ def load_library(path: Path | str | None = None):
     L.sta_destroy.argtypes = [_p]
     L.sta_full_rebuild.argtypes = [_p, _p, _int, _p]
     L.sta_apply_edits.argtypes = [_p, _p, _i64, _p]
+    L.sta_apply_edits_noalloc.argtypes = [_p, _p, _i64, _p]
     L.sta_last_touched.argtypes = [_p, _P(_i64), _p]
     L.sta_refold.argtypes = [_p, _p]
     L.sta_csr.argtypes = [_p, _P(_p), _P(_p), _P(_p), _P(_i64), _P(_i64)]
@@ -167,6 +169,13 @@ def sta_apply_edits(h: int, edits, stream=None) -> None:
     e = _host(edits, np.int32).reshape(-1, 3)
     _check(load_library().sta_apply_edits(h, e.ctypes.data if e.shape[0] else None, e.shape[0],
                                           _stream_handle(stream)))
+
+
+def sta_apply_edits_noalloc(h: int, edits, stream=None) -> None:
+    """Allocation-free variant of sta_apply_edits (fixed scratch; see include/sta.h)."""
+    e = _host(edits, np.int32).reshape(-1, 3)
+    _check(load_library().sta_apply_edits_noalloc(h, e.ctypes.data if e.shape[0] else None,
+                                                  e.shape[0], _stream_handle(stream)))
 
 
 def sta_refold(h: int, stream=None) -> None:

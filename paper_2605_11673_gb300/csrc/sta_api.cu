@@ -22,12 +22,6 @@ int fail(int code, const std::string &msg) {
 
 using namespace sta;
 
-struct sta_ctx {
-    Ctx c;
-    cudaEvent_t h2d_done = nullptr;
-    bool h2d_pending = false;
-    uint8_t *h_mask = nullptr;  // pinned staging for host masks, T bytes
-};
 
 static int wait_staging(sta_ctx *x) {
     if (x->h2d_pending) {

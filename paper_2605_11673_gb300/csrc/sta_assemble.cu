@@ -474,4 +474,29 @@ int launch_stream(Ctx *c, int64_t m, cudaStream_t s) {
     return STA_OK;
 }
 
+// Streaming update with caller-chosen scratch: the same three kernels as launch_stream, with
+// the edited-tet list, the touched-block list and the counters at the given addresses (used
+// by the allocation-free entry point; the touched count is copied to the context's counter
+// afterwards so that sta_last_touched reports it).
+int launch_stream_scratch(Ctx *c, int64_t m, const int32_t *d_edited, int32_t *touched,
+                          unsigned long long *counters, cudaStream_t s) {
+    if (m == 0) {
+        STA_CUDA_TRY(cudaMemsetAsync(c->counters + 1, 0, sizeof(unsigned long long), s));
+        return STA_OK;
+    }
+    const int threads = 256;
+    const int64_t g1 = (m + threads - 1) / threads, g2 = (16 * m + threads - 1) / threads;
+    k_stream_apply<<<(unsigned)g1, threads, 0, s>>>(d_edited, m, c->tblk, c->cslot, c->ccode,
+                                                    c->mask, c->owner, counters);
+    k_stream_compact<<<(unsigned)g2, threads, 0, s>>>(d_edited, m, c->tblk, c->owner, touched,
+                                                      counters);
+    const int fthreads = FOLD_WARPS * 32;
+    int grid = persistent_grid(c, (const void *)k_fold<1>, fthreads, 16 * m);
+    k_fold<1><<<grid, fthreads, 0, s>>>(fold_args(c), touched, counters + 1, 0);
+    STA_CUDA_TRY(cudaGetLastError());
+    STA_CUDA_TRY(cudaMemcpyAsync(c->counters + 1, counters + 1, sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToDevice, s));
+    return STA_OK;
+}
+
 }  // namespace sta

@@ -134,6 +134,16 @@ int launch_expand_elements(Ctx *c, const int32_t *ids, int64_t n, double *out, c
 int launch_rebuild(Ctx *c, cudaStream_t s);                      // sta_assemble.cu
 int launch_stream(Ctx *c, int64_t n_edited, cudaStream_t s);
 int launch_mask_bits(Ctx *c, cudaStream_t s);                    // codes <- mask
+int launch_stream_scratch(Ctx *c, int64_t m, const int32_t *d_edited, int32_t *touched,
+                          unsigned long long *counters, cudaStream_t s);
 int max_block_contributors();  // largest contributor list a fold can stage
 
 }  // namespace sta
+
+// The opaque handle of the C-ABI.
+struct sta_ctx {
+    sta::Ctx c;
+    cudaEvent_t h2d_done = nullptr;
+    bool h2d_pending = false;
+    uint8_t *h_mask = nullptr;  // pinned staging for host masks, T bytes
+};
