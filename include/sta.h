@@ -182,6 +182,25 @@ int sta_element_matrices(sta_ctx *ctx, const int32_t *tet_ids, int64_t n, double
                          void *stream);
 
 /*
+ * sta_adjoint -- reverse-mode derivative of the assembly (Eq. 8) with respect to the element
+ * parameters, for the current active mask.  Given grad_val = dL/dA per CSR entry (device,
+ * nnz doubles; entries of the same pattern as sta_csr), computes on the device
+ *   dE  (n_tets doubles)  dL/dE_tau,   dnu (n_tets doubles)  dL/dnu_tau   (0 for inactive),
+ *   dX  (n_nodes x 3 doubles)  dL/dx_v, summed over the active tetrahedra incident to v in
+ *       ascending id (deterministic).
+ * Element matrices are recomputed from positions and materials (not read from the cache).
+ * The first call allocates a per-element scratch of 96 bytes per tetrahedron held by the
+ * context.  All pointers are device memory.
+ */
+int sta_adjoint(sta_ctx *ctx, const double *grad_val, double *dE, double *dnu, double *dX,
+                void *stream);
+
+/* y = A x over the context's pattern (device vectors of n_rows doubles), with the values `val`
+ * (device, nnz doubles) or, when val is NULL, the context's current values; each row is summed
+ * in ascending column order.  For consumers such as the conjugate-gradient solve. */
+int sta_spmv(sta_ctx *ctx, const double *val, const double *x, double *y, void *stream);
+
+/*
  * sta_apply_edits_noalloc -- the same streaming update as sta_apply_edits, for callers that
  * must not allocate (no counterpart in the paper).  sta_apply_edits may grow a pinned host
  * buffer and a device buffer on its first call or when a frame edits more tetrahedra than

@@ -27,7 +27,7 @@ EXPORTED = (
     "sta_default_options", "sta_create", "sta_destroy", "sta_full_rebuild", "sta_apply_edits",
     "sta_last_touched", "sta_refold", "sta_csr", "sta_scatter_map", "sta_sizes", "sta_mask",
     "sta_recompute_elements", "sta_set_params", "sta_element_matrices", "sta_last_error",
-    "sta_status_string", "sta_apply_edits_noalloc",
+    "sta_status_string", "sta_apply_edits_noalloc", "sta_adjoint", "sta_spmv",
 )
 STA_NOALLOC_MAX_EDITED = 32768
 
@@ -77,6 +77,8 @@ def load_library(path: Path | str | None = None):
     L.sta_recompute_elements.argtypes = [_p, _int, _p]
     L.sta_set_params.argtypes = [_p, _p, _p, _p, _int, _p]
     L.sta_element_matrices.argtypes = [_p, _p, _i64, _p, _p]
+    L.sta_adjoint.argtypes = [_p, _p, _p, _p, _p, _p]
+    L.sta_spmv.argtypes = [_p, _p, _p, _p, _p]
     L.sta_last_error.restype = C.c_char_p
     L.sta_status_string.argtypes = [_int]
     L.sta_status_string.restype = C.c_char_p
@@ -254,6 +256,29 @@ def sta_element_matrices(h: int, tet_ids, stream=None):
     _check(load_library().sta_element_matrices(h, ids.data_ptr(), ids.numel(), out.data_ptr(),
                                                _stream_handle(stream)))
     return out
+
+
+def sta_adjoint(h: int, grad_val, stream=None):
+    """(dE, dnu, dX) CUDA tensors for dL/dval given as a CUDA float64 tensor of nnz values."""
+    import torch
+    s = sta_sizes(h)
+    g = grad_val.contiguous()
+    assert g.is_cuda and g.dtype == torch.float64 and g.numel() == s["nnz"]
+    dE = torch.empty(s["n_tets"], dtype=torch.float64, device=g.device)
+    dnu = torch.empty_like(dE)
+    dX = torch.empty((s["n_nodes"], 3), dtype=torch.float64, device=g.device)
+    _check(load_library().sta_adjoint(h, g.data_ptr(), dE.data_ptr(), dnu.data_ptr(),
+                                      dX.data_ptr(), _stream_handle(stream)))
+    return dE, dnu, dX
+
+
+def sta_spmv(h: int, x, val=None, stream=None):
+    """y = A x (CUDA float64 tensors) over the pattern, with `val` or the current values."""
+    x = x.contiguous()
+    y = x.new_empty(x.shape)
+    vp = val.contiguous().data_ptr() if val is not None else None
+    _check(load_library().sta_spmv(h, vp, x.data_ptr(), y.data_ptr(), _stream_handle(stream)))
+    return y
 
 
 # ----------------------------------------------------------------------------------------

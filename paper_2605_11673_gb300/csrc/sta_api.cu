@@ -362,6 +362,21 @@ int sta_set_params(sta_ctx *x, const double *nodes, const double *young, const d
     return STA_OK;
 }
 
+int sta_adjoint(sta_ctx *x, const double *grad_val, double *dE, double *dnu, double *dX,
+                void *stream) {
+    if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    const Ctx *c = &x->c;
+    if ((c->nnz > 0 && !grad_val) || (c->T > 0 && (!dE || !dnu)) || (c->n > 0 && !dX))
+        return fail(STA_EINVAL, "NULL argument");
+    return launch_adjoint(&x->c, grad_val, dE, dnu, dX, (cudaStream_t)stream);
+}
+
+int sta_spmv(sta_ctx *x, const double *val, const double *xv, double *y, void *stream) {
+    if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    if (x->c.nrows > 0 && (!xv || !y)) return fail(STA_EINVAL, "NULL argument");
+    return launch_spmv(&x->c, val ? val : x->c.val, xv, y, (cudaStream_t)stream);
+}
+
 int sta_element_matrices(sta_ctx *x, const int32_t *tet_ids, int64_t n, double *out, void *stream) {
     if (!x || n < 0 || (n > 0 && (!tet_ids || !out))) return fail(STA_EINVAL, "bad argument");
     return launch_expand_elements(&x->c, tet_ids, n, out, (cudaStream_t)stream);

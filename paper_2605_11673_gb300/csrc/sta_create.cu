@@ -365,6 +365,11 @@ int build_pattern(Ctx *c, cudaStream_t s) {
     STA_TRY(dev_alloc(c, &c->owner, nblocks));
     STA_TRY(dev_alloc(c, &c->touched, nblocks));
 
+    STA_TRY(dev_alloc(c, &c->nt_ptr, n + 1));
+    STA_TRY(dev_alloc(c, &c->nt_list, 4 * T));
+    k_to_i32<<<grid_for(n + 1), TPB, 0, s>>>(nt_ptr, n + 1, c->nt_ptr);
+    STA_CUDA_TRY(cudaMemcpyAsync(c->nt_list, nt_list, sizeof(int32_t) * 4 * T,
+                                 cudaMemcpyDeviceToDevice, s));
     k_adj_fill<<<grid_for(n + 1), TPB, 0, s>>>(n, nt_ptr, scratch, adj_ptr64, c->adj_ptr,
                                                c->adj, c->block_node);
     k_row_ptr<<<grid_for(3 * n + 1), TPB, 0, s>>>(n, c->adj_ptr, c->row_ptr);

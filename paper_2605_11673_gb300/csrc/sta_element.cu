@@ -136,6 +136,141 @@ k_elements(const double4_32a *__restrict__ X, const int4 *__restrict__ tets,
     }
 }
 
+
+// ------------------------------------------------------------------------------------------
+// Adjoint (a5): dL/dE, dL/dnu and per-element dL/dx for an upstream gradient dL/dA given per
+// CSR entry.  With G = dL/dK^(tau) gathered through the node-pair blocks of the tetrahedron and
+// K = V (lam A + mu B), A[ai][bj] = g_a[i] g_b[j], B[ai][bj] = g_a[j] g_b[i] + d_ij g_a.g_b:
+//   SA = sum_ab g_a^T G_ab g_b,   SB = sum_ab (g_b^T G_ab g_a + tr(G_ab) g_a.g_b)
+//   dL/dE  = V (lam_E SA + mu_E SB),  dL/dnu = V (lam_nu SA + mu_nu SB)
+//   dL/dx_c = V [ (lam SA + mu SB) g_c - sum_a (h_a . g_c) g_a ],  h_a = d(lam SA + mu SB)/dg_a
+// using dV/dx_c = V g_c and dg_a = -(g_a . dx_c) g_c (barycentric gradients of a P1
+// tetrahedron).  Element matrices are recomputed here, not stored.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128)
+k_adjoint(const double4_32a *__restrict__ X, const int4 *__restrict__ tets,
+          const double2 *__restrict__ mat, const uint8_t *__restrict__ mask,
+          const int32_t *__restrict__ tblk, const int4 *__restrict__ bmeta,
+          const double *__restrict__ gval, int64_t T, double *__restrict__ dE,
+          double *__restrict__ dnu, double *__restrict__ dXe) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (!mask[t]) {
+            dE[t] = 0.0;
+            dnu[t] = 0.0;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) dXe[12 * t + k] = 0.0;
+            continue;
+        }
+        const int4 q = tets[t];
+        const double4_32a x0 = X[q.x], x1 = X[q.y], x2 = X[q.z], x3 = X[q.w];
+        V3 d1 = sub(x1, x0), d2 = sub(x2, x0), d3 = sub(x3, x0);
+        V3 c1 = cross_fma(d2, d3), c2 = cross_fma(d3, d1), c3 = cross_fma(d1, d2);
+        const double det = __fma_rn(d1.z, c1.z, __fma_rn(d1.y, c1.y, d1.x * c1.x));
+        const double r = 1.0 / det;
+        double g[4][3] = {{0, 0, 0}, {c1.x * r, c1.y * r, c1.z * r},
+                          {c2.x * r, c2.y * r, c2.z * r}, {c3.x * r, c3.y * r, c3.z * r}};
+#pragma unroll
+        for (int m = 0; m < 3; ++m) g[0][m] = -((g[1][m] + g[2][m]) + g[3][m]);
+        const double V = det / 6.0;
+        const double2 em = mat[t];
+        const double E = em.x, nu = em.y;
+        const double onu = 1.0 + nu, omn = 1.0 - (nu + nu);
+        const double lam = (E * nu) / (onu * omn), mu = E / (onu + onu);
+        double SA = 0.0, SB = 0.0, hA[4][3], hB[4][3];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int m = 0; m < 3; ++m) hA[a][m] = hB[a][m] = 0.0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int4 bm = bmeta[tblk[16 * t + 4 * a + b]];
+                const double *G = gval + bm.x;
+                const int rs = bm.y >> 1;
+                double M[3][3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) M[i][j] = G[i * rs + j];
+                const double tr = M[0][0] + M[1][1] + M[2][2];
+                double Mgb[3], Mtga[3], Mtgb[3], Mga[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    Mgb[i] = M[i][0] * g[b][0] + M[i][1] * g[b][1] + M[i][2] * g[b][2];
+                    Mga[i] = M[i][0] * g[a][0] + M[i][1] * g[a][1] + M[i][2] * g[a][2];
+                    Mtga[i] = M[0][i] * g[a][0] + M[1][i] * g[a][1] + M[2][i] * g[a][2];
+                    Mtgb[i] = M[0][i] * g[b][0] + M[1][i] * g[b][1] + M[2][i] * g[b][2];
+                }
+                const double gab = g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2];
+                SA += g[a][0] * Mgb[0] + g[a][1] * Mgb[1] + g[a][2] * Mgb[2];
+                SB += g[b][0] * Mga[0] + g[b][1] * Mga[1] + g[b][2] * Mga[2] + tr * gab;
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    hA[a][m] += Mgb[m];
+                    hA[b][m] += Mtga[m];
+                    hB[a][m] += Mtgb[m] + tr * g[b][m];
+                    hB[b][m] += Mga[m] + tr * g[a][m];
+                }
+            }
+        const double lamE = nu / (onu * omn), muE = 1.0 / (onu + onu);
+        const double lamN = E * (1.0 + 2.0 * nu * nu) / (onu * onu * omn * omn);
+        const double muN = -E / (2.0 * onu * onu);
+        dE[t] = V * (lamE * SA + muE * SB);
+        dnu[t] = V * (lamN * SA + muN * SB);
+        const double S = lam * SA + mu * SB;
+#pragma unroll
+        for (int cidx = 0; cidx < 4; ++cidx) {
+            double o[3] = {S * g[cidx][0], S * g[cidx][1], S * g[cidx][2]};
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const double hg = (lam * hA[a][0] + mu * hB[a][0]) * g[cidx][0] +
+                                  (lam * hA[a][1] + mu * hB[a][1]) * g[cidx][1] +
+                                  (lam * hA[a][2] + mu * hB[a][2]) * g[cidx][2];
+#pragma unroll
+                for (int m = 0; m < 3; ++m) o[m] -= hg * g[a][m];
+            }
+#pragma unroll
+            for (int m = 0; m < 3; ++m) dXe[12 * t + 3 * cidx + m] = V * o[m];
+        }
+    }
+}
+
+// dL/dX of each node: fold over its incident tetrahedra in ascending id (deterministic).
+__global__ void k_node_grad(const int32_t *__restrict__ nt_ptr, const int32_t *__restrict__ nt_list,
+                            const int4 *__restrict__ tets, const double *__restrict__ dXe,
+                            int64_t n, double *__restrict__ dX) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+        for (int32_t e = nt_ptr[v]; e < nt_ptr[v + 1]; ++e) {
+            const int32_t t = nt_list[e];
+            const int4 q = tets[t];
+            const int k = q.x == v ? 0 : (q.y == v ? 1 : (q.z == v ? 2 : 3));
+            const double *p = dXe + 12 * (int64_t)t + 3 * k;
+            s0 += p[0];
+            s1 += p[1];
+            s2 += p[2];
+        }
+        dX[3 * v] = s0;
+        dX[3 * v + 1] = s1;
+        dX[3 * v + 2] = s2;
+    }
+}
+
+// y = A x over the context's CSR (one thread per row, ascending columns).
+__global__ void k_spmv(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                       const double *__restrict__ val, const double *__restrict__ x, int64_t nrows,
+                       double *__restrict__ y) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int32_t k = row_ptr[r]; k < row_ptr[r + 1]; ++k) s += val[k] * x[col[k]];
+        y[r] = s;
+    }
+}
+
 // Expand cached records of selected tetrahedra to full 12x12 row-major matrices.
 __global__ void k_expand(const double *__restrict__ Ke, int64_t T, const int32_t *ids,
                          int64_t n, double *out) {
@@ -174,6 +309,36 @@ int launch_elements(Ctx *c, bool active_only, cudaStream_t s) {
     k_elements<<<(unsigned)blocks, EL_TPB, smem, s>>>(c->X, c->tets, c->mat, c->mask,
                                                       active_only ? 1 : 0, c->T, c->Ke,
                                                       c->counters);
+    STA_CUDA_TRY(cudaGetLastError());
+    return STA_OK;
+}
+
+int launch_adjoint(Ctx *c, const double *gval, double *dE, double *dnu, double *dX,
+                   cudaStream_t s) {
+    if (!c->dXe) STA_TRY(dev_alloc(c, &c->dXe, 12 * c->T));
+    if (c->T > 0) {
+        int64_t grid = (c->T + 127) / 128;
+        const int64_t cap = (int64_t)c->num_sms * 16;
+        if (grid > cap) grid = cap;
+        k_adjoint<<<(unsigned)grid, 128, 0, s>>>(c->X, c->tets, c->mat, c->mask, c->tblk, c->bmeta,
+                                                gval, c->T, dE, dnu, c->dXe);
+    }
+    if (c->n > 0) {
+        int64_t grid = (c->n + 255) / 256;
+        const int64_t cap = (int64_t)c->num_sms * 16;
+        if (grid > cap) grid = cap;
+        k_node_grad<<<(unsigned)grid, 256, 0, s>>>(c->nt_ptr, c->nt_list, c->tets, c->dXe, c->n, dX);
+    }
+    STA_CUDA_TRY(cudaGetLastError());
+    return STA_OK;
+}
+
+int launch_spmv(Ctx *c, const double *val, const double *x, double *y, cudaStream_t s) {
+    if (c->nrows == 0) return STA_OK;
+    int64_t grid = (c->nrows + 255) / 256;
+    const int64_t cap = (int64_t)c->num_sms * 16;
+    if (grid > cap) grid = cap;
+    k_spmv<<<(unsigned)grid, 256, 0, s>>>(c->row_ptr, c->col, val, x, c->nrows, y);
     STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;
 }

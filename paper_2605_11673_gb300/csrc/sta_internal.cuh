@@ -89,6 +89,9 @@ struct Ctx {
     int32_t *ccode = nullptr;      // 16 T: contributor codes, ascending tetrahedron id
     int32_t *cslot = nullptr;      // T x 16: position in ccode of tet t's pair (la, lb)
     int4 *bmeta = nullptr;         // nblocks: {value offset, 3 deg << 1 | diagonal, c0, c1}
+    int32_t *nt_ptr = nullptr;     // n + 1: node -> incident tetrahedra
+    int32_t *nt_list = nullptr;    // 4 T: incident tetrahedra, ascending id
+    double *dXe = nullptr;         // T x 12: per-element position gradients (adjoint, lazily)
 
     // state
     double *Ke = nullptr;       // T x 78 element cache
@@ -131,6 +134,8 @@ int persistent_grid(const Ctx *c, const void *kernel, int threads, int64_t items
 int build_pattern(Ctx *c, cudaStream_t s);                       // sta_create.cu
 int launch_elements(Ctx *c, bool active_only, cudaStream_t s);   // sta_element.cu
 int launch_expand_elements(Ctx *c, const int32_t *ids, int64_t n, double *out, cudaStream_t s);
+int launch_adjoint(Ctx *c, const double *gval, double *dE, double *dnu, double *dX, cudaStream_t s);
+int launch_spmv(Ctx *c, const double *val, const double *x, double *y, cudaStream_t s);
 int launch_rebuild(Ctx *c, cudaStream_t s);                      // sta_assemble.cu
 int launch_stream(Ctx *c, int64_t n_edited, cudaStream_t s);
 int launch_mask_bits(Ctx *c, cudaStream_t s);                    // codes <- mask
