@@ -63,7 +63,7 @@ typedef struct {
 
 typedef struct {
     double eps;             /* eps of Eq. 4 / Eq. 8, added to diagonal entries; default 0 */
-    int32_t block_threads;  /* threads per CTA of the fold kernels; 0 = built-in default */
+    int32_t block_threads;  /* threads per CTA of the fold kernels: 64, 128 or 256; 0 = 128 */
     int32_t blocks_per_sm;  /* CTAs per SM of the persistent fold grid; 0 = occupancy max */
 } sta_options;
 
@@ -109,6 +109,10 @@ int sta_full_rebuild(sta_ctx *ctx, const uint8_t *mask, int mask_on_device, void
  * after sta_set_params / sta_recompute_elements, or to time a rebuild without a mask copy).
  */
 int sta_refold(sta_ctx *ctx, void *stream);
+
+/* Change the fold launch shape (same meaning as the sta_options fields; results do not
+ * depend on it).  Not allowed while graph mode is on (STA_ESTATE). */
+int sta_set_launch(sta_ctx *ctx, int32_t block_threads, int32_t blocks_per_sm);
 
 /*
  * sta_apply_edits -- one frame of the streaming update (Sec. 3.2; Algorithm 1 receive /
@@ -223,6 +227,48 @@ int sta_spmv(sta_ctx *ctx, const double *val, const double *x, double *y, void *
  */
 #define STA_NOALLOC_MAX_EDITED 32768
 int sta_apply_edits_noalloc(sta_ctx *ctx, const sta_edit *edits, int64_t n_edits, void *stream);
+
+/*
+ * Batched form: k independent superset meshes in one context.  Instance i's arrays (host) are
+ * given by pointer; node ids are local to the instance.  The instances are concatenated with
+ * disjoint id ranges (instance i's tetrahedra get global ids tet_offset_i + local id), so the
+ * assembled matrix is block diagonal and each instance's values are bit-identical to those of
+ * a context created for that instance alone.  sta_full_rebuild takes the concatenated mask
+ * (sum of n_tets bytes, instances in order); sta_refold, sta_recompute_elements and
+ * sta_graph_enable work on the whole batch; one call drives every instance with one launch
+ * sequence (one persistent fold over the blocks of all instances).
+ */
+int sta_batch_create(int32_t k, const int64_t *n_nodes, const double *const *nodes,
+                     const int64_t *n_tets, const int32_t *const *tets,
+                     const double *const *young, const double *const *poisson,
+                     const sta_options *opt, void *stream, sta_ctx **out);
+
+/* Number of instances of a batched context (0 for a plain context). */
+int sta_batch_size(const sta_ctx *ctx, int32_t *k);
+
+/* Instance i's CSR in its own numbering: row_ptr (3 n_i + 1, from 0) and col (local DOFs) are
+ * device index arrays owned by the context; val points at the instance's slice of the batch
+ * values.  tet_offset is the global id of the instance's first tetrahedron. */
+int sta_batch_instance(const sta_ctx *ctx, int32_t i, const int32_t **row_ptr,
+                       const int32_t **col, const double **val, int64_t *n_rows, int64_t *nnz,
+                       int64_t *tet_offset);
+
+/* One streaming frame for every instance: counts[i] edits of instance i (tet ids local to the
+ * instance) follow each other in `edits`.  Same validation and results as sta_apply_edits. */
+int sta_batch_apply_edits(sta_ctx *ctx, const int64_t *counts, const sta_edit *edits,
+                          void *stream);
+
+/*
+ * sta_graph_enable -- capture the per-frame device work of the context into CUDA graphs: the
+ * streaming update (mask and activity update, touched-block dedupe, fold; edit count read
+ * from device memory, grids sized for max_edited), the refold, and the fold of a full
+ * rebuild.  Afterwards sta_apply_edits (frames of at most max_edited edited tetrahedra; a
+ * swap counts two), sta_refold and sta_full_rebuild replay them with one cudaGraphLaunch each;
+ * results are unchanged.  Allocates fixed staging buffers (device and pinned host) and
+ * synchronises `stream`.  sta_graph_disable releases them and returns to plain launches.
+ */
+int sta_graph_enable(sta_ctx *ctx, int64_t max_edited, void *stream);
+int sta_graph_disable(sta_ctx *ctx, void *stream);
 
 /* Human-readable message of the last error on the calling thread. */
 const char *sta_last_error(void);

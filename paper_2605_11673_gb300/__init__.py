@@ -27,7 +27,9 @@ EXPORTED = (
     "sta_default_options", "sta_create", "sta_destroy", "sta_full_rebuild", "sta_apply_edits",
     "sta_last_touched", "sta_refold", "sta_csr", "sta_scatter_map", "sta_sizes", "sta_mask",
     "sta_recompute_elements", "sta_set_params", "sta_element_matrices", "sta_last_error",
-    "sta_status_string", "sta_apply_edits_noalloc", "sta_adjoint", "sta_spmv",
+    "sta_status_string", "sta_apply_edits_noalloc", "sta_adjoint", "sta_spmv", "sta_set_launch",
+    "sta_batch_create", "sta_batch_size", "sta_batch_instance", "sta_batch_apply_edits",
+    "sta_graph_enable", "sta_graph_disable",
 )
 STA_NOALLOC_MAX_EDITED = 32768
 
@@ -79,6 +81,14 @@ def load_library(path: Path | str | None = None):
     L.sta_element_matrices.argtypes = [_p, _p, _i64, _p, _p]
     L.sta_adjoint.argtypes = [_p, _p, _p, _p, _p, _p]
     L.sta_spmv.argtypes = [_p, _p, _p, _p, _p]
+    L.sta_set_launch.argtypes = [_p, C.c_int32, C.c_int32]
+    L.sta_batch_create.argtypes = [C.c_int32, _p, _p, _p, _p, _p, _p, _P(sta_options), _p, _P(_p)]
+    L.sta_batch_size.argtypes = [_p, _P(C.c_int32)]
+    L.sta_batch_instance.argtypes = [_p, C.c_int32, _P(_p), _P(_p), _P(_p), _P(_i64), _P(_i64),
+                                     _P(_i64)]
+    L.sta_batch_apply_edits.argtypes = [_p, _p, _p, _p]
+    L.sta_graph_enable.argtypes = [_p, _i64, _p]
+    L.sta_graph_disable.argtypes = [_p, _p]
     L.sta_last_error.restype = C.c_char_p
     L.sta_status_string.argtypes = [_int]
     L.sta_status_string.restype = C.c_char_p
@@ -281,6 +291,63 @@ def sta_spmv(h: int, x, val=None, stream=None):
     return y
 
 
+def sta_set_launch(h: int, block_threads: int = 0, blocks_per_sm: int = 0) -> None:
+    _check(load_library().sta_set_launch(h, int(block_threads), int(blocks_per_sm)))
+
+
+def sta_graph_enable(h: int, max_edited: int, stream=None) -> None:
+    _check(load_library().sta_graph_enable(h, int(max_edited), _stream_handle(stream)))
+
+
+def sta_graph_disable(h: int, stream=None) -> None:
+    _check(load_library().sta_graph_disable(h, _stream_handle(stream)))
+
+
+def sta_batch_create(instances, opt: sta_options | None = None, stream=None) -> int:
+    """instances: list of (X (n_i, 3), tets (T_i, 4) local ids, E (T_i,), nu (T_i,))."""
+    L = load_library()
+    k = len(instances)
+    keep = []
+    arr = {"X": (C.c_void_p * k)(), "T": (C.c_void_p * k)(), "E": (C.c_void_p * k)(),
+           "NU": (C.c_void_p * k)()}
+    nn = (C.c_int64 * k)()
+    nt = (C.c_int64 * k)()
+    for i, (X, tets, E, nu) in enumerate(instances):
+        X = _host(X, np.float64).reshape(-1, 3)
+        tets = _host(tets, np.int32).reshape(-1, 4)
+        E = _host(E, np.float64).reshape(-1)
+        nu = _host(nu, np.float64).reshape(-1)
+        keep += [X, tets, E, nu]
+        nn[i], nt[i] = X.shape[0], tets.shape[0]
+        arr["X"][i], arr["T"][i] = X.ctypes.data, tets.ctypes.data
+        arr["E"][i], arr["NU"][i] = E.ctypes.data, nu.ctypes.data
+    h = _p()
+    _check(L.sta_batch_create(k, nn, arr["X"], nt, arr["T"], arr["E"], arr["NU"],
+                              C.byref(opt) if opt is not None else None, _stream_handle(stream),
+                              C.byref(h)))
+    return h.value
+
+
+def sta_batch_instance(h: int, i: int, owner=None):
+    """(row_ptr, col, val) DeviceArrays of instance i in its own numbering, and its tet offset."""
+    rp, cl, vl = _p(), _p(), _p()
+    nr, nz, toff = _i64(), _i64(), _i64()
+    _check(load_library().sta_batch_instance(h, int(i), C.byref(rp), C.byref(cl), C.byref(vl),
+                                             C.byref(nr), C.byref(nz), C.byref(toff)))
+    return (DeviceArray(rp.value or 0, (nr.value + 1,), "<i4", owner),
+            DeviceArray(cl.value or 0, (nz.value,), "<i4", owner),
+            DeviceArray(vl.value or 0, (nz.value,), "<f8", owner), int(toff.value))
+
+
+def sta_batch_apply_edits(h: int, edits_per_instance, stream=None) -> None:
+    """edits_per_instance: list of (m_i, 3) int32 arrays with instance-local tet ids."""
+    parts = [_host(e, np.int32).reshape(-1, 3) for e in edits_per_instance]
+    counts = (C.c_int64 * len(parts))(*[p.shape[0] for p in parts])
+    allp = np.ascontiguousarray(np.concatenate(parts, 0)) if parts else np.zeros((0, 3), np.int32)
+    _check(load_library().sta_batch_apply_edits(h, counts, allp.ctypes.data if allp.shape[0] else None,
+                                                 _stream_handle(stream)))
+
+
 # ----------------------------------------------------------------------------------------
 # Convenience wrapper
 # ----------------------------------------------------------------------------------------
@@ -344,3 +411,39 @@ class Assembler:
 
     def sizes(self) -> dict:
         return sta_sizes(self.h)
+
+    def set_launch(self, block_threads: int = 0, blocks_per_sm: int = 0):
+        sta_set_launch(self.h, block_threads, blocks_per_sm)
+
+    def graph_enable(self, max_edited: int, stream=None):
+        sta_graph_enable(self.h, max_edited, stream)
+
+    def graph_disable(self, stream=None):
+        sta_graph_disable(self.h, stream)
+
+
+class BatchAssembler(Assembler):
+    """k independent superset meshes in one context (batched form)."""
+
+    def __init__(self, instances, eps: float = 0.0, block_threads: int = 0,
+                 blocks_per_sm: int = 0, stream=None):
+        o = sta_default_options()
+        o.eps, o.block_threads, o.blocks_per_sm = float(eps), int(block_threads), int(blocks_per_sm)
+        self.h = sta_batch_create(instances, o, stream)
+        s = sta_sizes(self.h)
+        self.n_nodes, self.n_tets, self.nnz = s["n_nodes"], s["n_tets"], s["nnz"]
+        self.n_rows = 3 * self.n_nodes
+        self.k = len(instances)
+
+    def full_rebuild(self, masks, stream=None):
+        """masks: list of per-instance masks, or one concatenated mask."""
+        if isinstance(masks, (list, tuple)):
+            masks = np.concatenate([np.asarray(m, np.uint8) for m in masks])
+        sta_full_rebuild(self.h, masks, stream)
+
+    def apply_edits(self, edits_per_instance, stream=None):
+        sta_batch_apply_edits(self.h, edits_per_instance, stream)
+
+    def instance_csr(self, i: int):
+        rp, col, val, _ = sta_batch_instance(self.h, i, self)
+        return rp.torch(), col.torch(), val.torch()

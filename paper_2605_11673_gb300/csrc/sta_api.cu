@@ -39,6 +39,7 @@ static void free_ctx(sta_ctx *x) {
     if (x->c.d_edited) cudaFree(x->c.d_edited);
     if (x->h_mask) cudaFreeHost(x->h_mask);
     if (x->h2d_done) cudaEventDestroy(x->h2d_done);
+    graph_release(&x->c);
     delete x;
 }
 
@@ -68,6 +69,14 @@ const char *sta_status_string(int status) {
 int sta_create(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
                const double *young, const double *poisson, const sta_options *opt,
                void *stream, sta_ctx **out) {
+    return sta::create_impl(nodes, n_nodes, tets, n_tets, young, poisson, opt, stream, out);
+}
+
+}  // extern "C"
+
+int sta::create_impl(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
+                     const double *young, const double *poisson, const sta_options *opt,
+                     void *stream, sta_ctx **out) {
     if (!out) return fail(STA_EINVAL, "out is NULL");
     *out = nullptr;
     if (n_nodes < 0 || n_tets < 0) return fail(STA_EINVAL, "negative size");
@@ -88,8 +97,9 @@ int sta_create(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_
     sta_options o;
     sta_default_options(&o);
     if (opt) o = *opt;
-    if (o.block_threads != 0 && (o.block_threads < 32 || o.block_threads > 1024 || o.block_threads % 32))
-        return fail(STA_EINVAL, "block_threads must be a multiple of 32 in [32, 1024]");
+    if (o.block_threads != 0 && o.block_threads != 64 && o.block_threads != 128 && o.block_threads != 256)
+        return fail(STA_EINVAL, "block_threads must be 64, 128 or 256");
+    if (o.blocks_per_sm < 0) return fail(STA_EINVAL, "blocks_per_sm must be >= 0");
 
     cudaStream_t s = (cudaStream_t)stream;
     sta_ctx *x = new sta_ctx();
@@ -97,7 +107,7 @@ int sta_create(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_
     c->n = n_nodes;
     c->T = n_tets;
     c->eps = o.eps;
-    c->block_threads = o.block_threads ? o.block_threads : 256;
+    c->block_threads = o.block_threads ? o.block_threads : 128;
     c->blocks_per_sm = o.blocks_per_sm;
     int rc = STA_OK;
     auto bail = [&](int code) {
@@ -109,6 +119,7 @@ int sta_create(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_
         return bail(fail(STA_ECUDA, "no CUDA device"));
     if (cudaEventCreateWithFlags(&x->h2d_done, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(STA_ECUDA, "cudaEventCreate failed"));
+    if ((rc = init_fold_attributes())) return bail(rc);
 
     // inputs: nodes padded to double4_32a, tets as int4, materials as double2
     std::vector<double> X4(4 * (size_t)(n_nodes > 0 ? n_nodes : 1), 0.0);
@@ -155,6 +166,8 @@ int sta_create(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_
     return STA_OK;
 }
 
+extern "C" {
+
 int sta_destroy(sta_ctx *x) {
     if (!x) return STA_OK;
     cudaDeviceSynchronize();
@@ -186,12 +199,31 @@ int sta_full_rebuild(sta_ctx *x, const uint8_t *mask, int mask_on_device, void *
             x->h2d_pending = true;
         }
     }
+    if (c->graph_on) {
+        STA_CUDA_TRY(cudaGraphLaunch(c->g_rebuild, s));
+        return STA_OK;
+    }
     STA_TRY(launch_mask_bits(c, s));
     return launch_rebuild(c, s);
 }
 
+int sta_set_launch(sta_ctx *x, int32_t block_threads, int32_t blocks_per_sm) {
+    if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    if (block_threads != 0 && block_threads != 64 && block_threads != 128 && block_threads != 256)
+        return fail(STA_EINVAL, "block_threads must be 0, 64, 128 or 256");
+    if (blocks_per_sm < 0) return fail(STA_EINVAL, "blocks_per_sm must be >= 0");
+    if (x->c.graph_on) return fail(STA_ESTATE, "disable graph mode before changing the launch shape");
+    x->c.block_threads = block_threads ? block_threads : 128;
+    x->c.blocks_per_sm = blocks_per_sm;
+    return STA_OK;
+}
+
 int sta_refold(sta_ctx *x, void *stream) {
     if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    if (x->c.graph_on) {
+        STA_CUDA_TRY(cudaGraphLaunch(x->c.g_refold, (cudaStream_t)stream));
+        return STA_OK;
+    }
     return launch_rebuild(&x->c, (cudaStream_t)stream);
 }
 
@@ -229,7 +261,16 @@ int sta_apply_edits(sta_ctx *x, const sta_edit *edits, int64_t n_edits, void *st
     }
     if (bad >= 0) return fail(STA_EINVAL, "edit " + std::to_string(bad) + ": " + why);
 
-    if (m > c->edit_cap) {
+    const bool use_graph = c->graph_on && m <= c->gcap;
+    int32_t *stage = nullptr;
+    if (use_graph) {
+        if (c->g_pending) {
+            STA_CUDA_TRY(cudaEventSynchronize(c->g_h2d));
+            c->g_pending = false;
+        }
+        stage = c->h_gedit;
+    }
+    if (!use_graph && m > c->edit_cap) {
         STA_TRY(wait_staging(x));
         int64_t cap = m < 1024 ? 1024 : m + m / 2;
         if (c->h_edited) cudaFreeHost(c->h_edited);
@@ -247,22 +288,38 @@ int sta_apply_edits(sta_ctx *x, const sta_edit *edits, int64_t n_edits, void *st
         c->device_bytes += (int64_t)sizeof(int32_t) * cap;
         c->edit_cap = cap;
     }
-    STA_TRY(wait_staging(x));
+    if (!use_graph) {
+        STA_TRY(wait_staging(x));
+        stage = c->h_edited;
+    }
     int64_t k = 0;
     for (int64_t e = 0; e < n_edits; ++e) {
         const sta_edit &E = edits[e];
         if (E.op == STA_DEACTIVATE) {
-            c->h_edited[k++] = E.tet;
+            stage[k++] = E.tet;
             c->host_mask[E.tet] = 0;
         } else if (E.op == STA_ACTIVATE) {
-            c->h_edited[k++] = (int32_t)((uint32_t)E.tet | 0x80000000u);
+            stage[k++] = (int32_t)((uint32_t)E.tet | 0x80000000u);
             c->host_mask[E.tet] = 1;
         } else {
-            c->h_edited[k++] = E.tet;
-            c->h_edited[k++] = (int32_t)((uint32_t)E.tet2 | 0x80000000u);
+            stage[k++] = E.tet;
+            stage[k++] = (int32_t)((uint32_t)E.tet2 | 0x80000000u);
             c->host_mask[E.tet] = 0;
             c->host_mask[E.tet2] = 1;
         }
+    }
+    c->last_edited = m;
+    if (use_graph) {  // fixed buffers, one captured launch sequence for every frame
+        *c->h_gcount = m;
+        if (m > 0)
+            STA_CUDA_TRY(cudaMemcpyAsync(c->d_gedit, c->h_gedit, sizeof(int32_t) * m,
+                                         cudaMemcpyHostToDevice, s));
+        STA_CUDA_TRY(cudaMemcpyAsync(c->d_gcount, c->h_gcount, sizeof(int64_t),
+                                     cudaMemcpyHostToDevice, s));
+        STA_CUDA_TRY(cudaEventRecord(c->g_h2d, s));
+        c->g_pending = true;
+        STA_CUDA_TRY(cudaGraphLaunch(c->g_stream, s));
+        return STA_OK;
     }
     if (m > 0) {
         STA_CUDA_TRY(cudaMemcpyAsync(c->d_edited, c->h_edited, sizeof(int32_t) * m,
@@ -270,7 +327,6 @@ int sta_apply_edits(sta_ctx *x, const sta_edit *edits, int64_t n_edits, void *st
         STA_CUDA_TRY(cudaEventRecord(x->h2d_done, s));
         x->h2d_pending = true;
     }
-    c->last_edited = m;
     return launch_stream(c, m, s);
 }
 

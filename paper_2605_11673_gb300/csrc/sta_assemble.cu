@@ -109,11 +109,12 @@ __device__ __forceinline__ void write_block(const FoldArgs &A, const BlockOut &o
 // whose codes are contiguous, staged with coalesced windows and ballots; MODE 1: item
 // indexes a list of block ids whose length is read from device memory (streaming), staged
 // one block per lane.
-constexpr int FOLD_WARPS = 4;       // warps per CTA
+constexpr int FOLD_WARPS = 4;       // default warps per CTA (2, 4 or 8 selectable)
 constexpr int STAGE_BLOCKS = 192;   // staged blocks per warp
 constexpr int STAGE_CODES = 1280;   // staged active codes per warp (>= contributors of any block)
 constexpr int STAGE_WIN = 8;        // 32-code windows of one staging round held in registers
 constexpr int LONG_BLOCK = 8;       // staged blocks with this many contributors are claimed first
+constexpr size_t FOLD_WARP_SMEM = sizeof(int4) * STAGE_BLOCKS + sizeof(int32_t) * STAGE_CODES;
 
 __device__ __forceinline__ int warp_inclusive_scan(int x, int lane) {
 #pragma unroll
@@ -144,16 +145,16 @@ __device__ __forceinline__ void write_small_block(const FoldArgs &A, const int4 
     write_block(A, BlockOut{A.val + bm.x, bm.y >> 1, (bm.y & 1) != 0}, acc);
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(FOLD_WARPS * 32)
+template <int MODE, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
 k_fold(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *__restrict__ count,
        int64_t nitems_static) {
-    __shared__ int4 sblk_all[FOLD_WARPS][STAGE_BLOCKS];
-    __shared__ int32_t scode_all[FOLD_WARPS][STAGE_CODES];
+    // per warp: STAGE_BLOCKS int4 block records, then STAGE_CODES int32 codes (dynamic)
+    extern __shared__ int4 fold_smem[];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int4 *sblk = sblk_all[wid];
-    int32_t *scode = scode_all[wid];
+    int4 *sblk = fold_smem + (size_t)wid * (FOLD_WARP_SMEM / sizeof(int4));
+    int32_t *scode = reinterpret_cast<int32_t *>(sblk + STAGE_BLOCKS);
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nitems = MODE == 0 ? nitems_static : (int64_t)*count;
@@ -412,6 +413,55 @@ __global__ void k_stream_compact(const int32_t *__restrict__ edited, int64_t m,
     }
 }
 
+// Device-count variants of the two streaming kernels for CUDA-graph replay: the number of
+// edited tetrahedra is read from device memory, the grid is fixed and strides over it.
+__global__ void k_stream_apply_dc(const int32_t *__restrict__ edited, const int64_t *__restrict__ m_dev,
+                                  const int32_t *__restrict__ tblk, const int32_t *__restrict__ cslot,
+                                  int32_t *__restrict__ ccode, uint8_t *__restrict__ mask,
+                                  int32_t *__restrict__ owner, unsigned long long *counters) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) counters[1] = 0ull;
+    const int64_t m = *m_dev;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = (uint32_t)edited[k];
+        const int32_t t = (int32_t)(w & 0x7fffffffu);
+        const uint32_t on = w >> 31;
+        mask[t] = (uint8_t)on;
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+            const int32_t slot = cslot[16 * (int64_t)t + s];
+            ccode[slot] = (int32_t)(((uint32_t)ccode[slot] & ~CODE_ACTIVE) | (on << 31));
+            atomicMin(&owner[tblk[16 * (int64_t)t + s]], (int32_t)(16 * k + s));
+        }
+    }
+}
+
+__global__ void k_stream_compact_dc(const int32_t *__restrict__ edited, const int64_t *__restrict__ m_dev,
+                                    const int32_t *__restrict__ tblk, int32_t *__restrict__ owner,
+                                    int32_t *__restrict__ list, unsigned long long *counters) {
+    const int64_t n = 16 * *m_dev;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // warp-uniform
+        const int64_t i = i0 + threadIdx.x;
+        bool mine = false;
+        int32_t g = 0;
+        if (i < n) {
+            const int32_t t = (int32_t)((uint32_t)edited[i >> 4] & 0x7fffffffu);
+            g = tblk[16 * (int64_t)t + (i & 15)];
+            mine = owner[g] == (int32_t)i;
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, mine);
+        unsigned long long base = 0;
+        if (lane == 0 && ball) base = atomicAdd(&counters[1], (unsigned long long)__popc(ball));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (mine) {
+            list[base + __popc(ball & ((1u << lane) - 1u))] = g;
+            owner[g] = INT32_MAX;
+        }
+    }
+}
+
 }  // namespace
 
 int max_block_contributors() { return STAGE_CODES; }
@@ -422,10 +472,10 @@ FoldArgs fold_args(const Ctx *c) { return FoldArgs{c->bmeta, c->ccode, c->Ke, c-
 
 }  // namespace
 
-int persistent_grid(const Ctx *c, const void *kernel, int threads, int64_t items) {
+int persistent_grid(const Ctx *c, const void *kernel, int threads, int64_t items, size_t smem) {
     int per_sm = c->blocks_per_sm;
     if (per_sm <= 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
     }
@@ -435,13 +485,42 @@ int persistent_grid(const Ctx *c, const void *kernel, int threads, int64_t items
     return (int)(g < 1 ? 1 : g);
 }
 
-int launch_rebuild(Ctx *c, cudaStream_t s) {
-    if (c->nblocks == 0) return STA_OK;
-    const int threads = FOLD_WARPS * 32;
-    int grid = persistent_grid(c, (const void *)k_fold<0>, threads, c->nblocks);
-    k_fold<0><<<grid, threads, 0, s>>>(fold_args(c), nullptr, nullptr, c->nblocks);
+// Launch the fold with the context's CTA shape (block_threads 64, 128 or 256).
+template <int MODE>
+int launch_fold(Ctx *c, const int32_t *list, const unsigned long long *count, int64_t nitems,
+                int64_t max_items, cudaStream_t s) {
+    const int threads = c->block_threads == 64 || c->block_threads == 256 ? c->block_threads : 128;
+    const void *kern = threads == 64    ? (const void *)k_fold<MODE, 2>
+                       : threads == 256 ? (const void *)k_fold<MODE, 8>
+                                        : (const void *)k_fold<MODE, 4>;
+    const size_t smem = FOLD_WARP_SMEM * (threads / 32);
+    const int grid = persistent_grid(c, kern, threads, max_items, smem);
+    if (threads == 64)
+        k_fold<MODE, 2><<<grid, threads, smem, s>>>(fold_args(c), list, count, nitems);
+    else if (threads == 256)
+        k_fold<MODE, 8><<<grid, threads, smem, s>>>(fold_args(c), list, count, nitems);
+    else
+        k_fold<MODE, 4><<<grid, threads, smem, s>>>(fold_args(c), list, count, nitems);
     STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;
+}
+
+// Dynamic shared memory limits of the fold instantiations (set once per context creation,
+// outside any stream capture).
+int init_fold_attributes() {
+    const void *k[6] = {(const void *)k_fold<0, 2>, (const void *)k_fold<0, 4>,
+                        (const void *)k_fold<0, 8>, (const void *)k_fold<1, 2>,
+                        (const void *)k_fold<1, 4>, (const void *)k_fold<1, 8>};
+    const int w[6] = {2, 4, 8, 2, 4, 8};
+    for (int i = 0; i < 6; ++i)
+        STA_CUDA_TRY(cudaFuncSetAttribute(k[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)(FOLD_WARP_SMEM * w[i])));
+    return STA_OK;
+}
+
+int launch_rebuild(Ctx *c, cudaStream_t s) {
+    if (c->nblocks == 0) return STA_OK;
+    return launch_fold<0>(c, nullptr, nullptr, c->nblocks, c->nblocks, s);
 }
 
 int launch_mask_bits(Ctx *c, cudaStream_t s) {
@@ -467,11 +546,23 @@ int launch_stream(Ctx *c, int64_t m, cudaStream_t s) {
     k_stream_compact<<<(unsigned)g2, threads, 0, s>>>(c->d_edited, m, c->tblk, c->owner,
                                                       c->touched, c->counters);
     // the touched count is only known on the device: size the grid for the upper bound
-    const int fthreads = FOLD_WARPS * 32;
-    int grid = persistent_grid(c, (const void *)k_fold<1>, fthreads, 16 * m);
-    k_fold<1><<<grid, fthreads, 0, s>>>(fold_args(c), c->touched, c->counters + 1, 0);
-    STA_CUDA_TRY(cudaGetLastError());
-    return STA_OK;
+    return launch_fold<1>(c, c->touched, c->counters + 1, 0, 16 * m, s);
+}
+
+// Streaming update for graph capture: edited list and its length in device memory, fixed grids
+// sized for `cap` edited tetrahedra.
+int launch_stream_devcount(Ctx *c, const int32_t *d_edited, const int64_t *d_m, int64_t cap,
+                           cudaStream_t s) {
+    const int threads = 256;
+    int64_t g1 = (cap + threads - 1) / threads, g2 = (16 * cap + threads - 1) / threads;
+    const int64_t c1 = (int64_t)c->num_sms * 8, c2 = (int64_t)c->num_sms * 16;
+    g1 = g1 < 1 ? 1 : (g1 > c1 ? c1 : g1);
+    g2 = g2 < 1 ? 1 : (g2 > c2 ? c2 : g2);
+    k_stream_apply_dc<<<(unsigned)g1, threads, 0, s>>>(d_edited, d_m, c->tblk, c->cslot, c->ccode,
+                                                       c->mask, c->owner, c->counters);
+    k_stream_compact_dc<<<(unsigned)g2, threads, 0, s>>>(d_edited, d_m, c->tblk, c->owner,
+                                                         c->touched, c->counters);
+    return launch_fold<1>(c, c->touched, c->counters + 1, 0, 16 * (cap > 0 ? cap : 1), s);
 }
 
 // Streaming update with caller-chosen scratch: the same three kernels as launch_stream, with
@@ -490,10 +581,7 @@ int launch_stream_scratch(Ctx *c, int64_t m, const int32_t *d_edited, int32_t *t
                                                     c->mask, c->owner, counters);
     k_stream_compact<<<(unsigned)g2, threads, 0, s>>>(d_edited, m, c->tblk, c->owner, touched,
                                                       counters);
-    const int fthreads = FOLD_WARPS * 32;
-    int grid = persistent_grid(c, (const void *)k_fold<1>, fthreads, 16 * m);
-    k_fold<1><<<grid, fthreads, 0, s>>>(fold_args(c), touched, counters + 1, 0);
-    STA_CUDA_TRY(cudaGetLastError());
+    STA_TRY(launch_fold<1>(c, touched, counters + 1, 0, 16 * m, s));
     STA_CUDA_TRY(cudaMemcpyAsync(c->counters + 1, counters + 1, sizeof(unsigned long long),
                                  cudaMemcpyDeviceToDevice, s));
     return STA_OK;

@@ -107,6 +107,21 @@ struct Ctx {
     int64_t edit_cap = 0;
     int64_t last_edited = 0;
 
+    // CUDA-graph mode (sta_graph_enable): captured frame sequences and fixed staging
+    bool graph_on = false;
+    cudaGraphExec_t g_stream = nullptr, g_refold = nullptr, g_rebuild = nullptr;
+    int64_t gcap = 0;
+    int32_t *d_gedit = nullptr, *h_gedit = nullptr;  // device / pinned, gcap entries
+    int64_t *d_gcount = nullptr, *h_gcount = nullptr;
+    cudaEvent_t g_h2d = nullptr;
+    bool g_pending = false;
+
+    // batched form (sta_batch_create): instance offsets and per-instance CSR index arrays
+    int32_t n_inst = 0;
+    std::vector<int64_t> node_off, tet_off, nnz_off;
+    int32_t *local_rp = nullptr;   // sum_i (3 n_i + 1): instance i at 3 node_off[i] + i
+    int32_t *local_col = nullptr;  // nnz: column minus the instance's first DOF
+
     std::vector<uint8_t> host_mask;
     std::vector<uint8_t> seen;  // per-tet scratch for edit validation (all zero at rest)
     int64_t device_bytes = 0;
@@ -126,7 +141,8 @@ template <typename T> int dev_alloc(Ctx *c, T **p, int64_t count) {
 }
 
 // Persistent grid for an item count: min(ceil(items / threads), SMs * CTAs per SM).
-int persistent_grid(const Ctx *c, const void *kernel, int threads, int64_t items);
+int persistent_grid(const Ctx *c, const void *kernel, int threads, int64_t items,
+                    size_t smem = 0);
 
 // ------------------------------------------------------------------------------------
 // Kernel launchers (each returns STA_OK or STA_ECUDA on a launch error)
@@ -139,9 +155,17 @@ int launch_spmv(Ctx *c, const double *val, const double *x, double *y, cudaStrea
 int launch_rebuild(Ctx *c, cudaStream_t s);                      // sta_assemble.cu
 int launch_stream(Ctx *c, int64_t n_edited, cudaStream_t s);
 int launch_mask_bits(Ctx *c, cudaStream_t s);                    // codes <- mask
+int init_fold_attributes();
 int launch_stream_scratch(Ctx *c, int64_t m, const int32_t *d_edited, int32_t *touched,
                           unsigned long long *counters, cudaStream_t s);
+int launch_stream_devcount(Ctx *c, const int32_t *d_edited, const int64_t *d_m, int64_t cap,
+                           cudaStream_t s);
 int max_block_contributors();  // largest contributor list a fold can stage
+
+int create_impl(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
+                const double *young, const double *poisson, const sta_options *opt, void *stream,
+                sta_ctx **out);
+void graph_release(Ctx *c);  // sta_graph.cu
 
 }  // namespace sta
 

@@ -1,0 +1,18 @@
+"""Host logic of the autotuner: selection and cache round trip (no GPU)."""
+from paper_2605_11673_gb300 import autotune as A
+
+
+def test_pick_best_and_ties():
+    t = {(128, 0): 1.0, (64, 2): 0.5, (256, 1): 0.5}
+    assert A.pick_best(t) == (64, 2)  # first in SHAPES order among equal times
+    assert A.pick_best({}) is None
+
+
+def test_cache_roundtrip(tmp_path):
+    p = tmp_path / "c.json"
+    assert A.load_cache(p) == {}
+    k = A.key_for("GPU", {"n_tets": 1, "n_blocks": 2, "nnz": 18})
+    A.save_cache({k: {"shape": [64, 3]}}, p)
+    assert A.load_cache(p)[k]["shape"] == [64, 3]
+    p.write_text("not json")
+    assert A.load_cache(p) == {}
