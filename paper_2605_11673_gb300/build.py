@@ -45,15 +45,21 @@ def _stale() -> bool:
     return any(p.stat().st_mtime > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> Path:
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, out: Path | None = None,
+          defines: tuple = (), src: Path | None = None) -> Path:
+    """Compile every translation unit (of `src`, default csrc/) and link libsta.so (into `out`,
+    default _build/)."""
+    lib = Path(out) / "libsta.so" if out else LIB
+    if out is None and not force and not _stale():
         return LIB
-    OUT.mkdir(exist_ok=True)
+    odir = lib.parent
+    odir.mkdir(parents=True, exist_ok=True)
     cc = nvcc()
+    extra = [f"-D{d}" for d in defines]
 
     def compile_one(src: Path) -> Path:
-        obj = OUT / (src.stem + ".o")
-        cmd = [cc, *ARCH, *NVFLAGS, "-c", str(src), "-o", str(obj)]
+        obj = odir / (src.stem + ".o")
+        cmd = [cc, *ARCH, *NVFLAGS, *extra, "-c", str(src), "-o", str(obj)]
         if verbose:
             cmd.append("-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -64,14 +70,14 @@ def build(force: bool = False, verbose: bool = False) -> Path:
         return obj
 
     with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
-        objs = list(ex.map(compile_one, sources()))
-    tmp = LIB.with_suffix(f".so.{os.getpid()}.tmp")
+        objs = list(ex.map(compile_one, sorted(Path(src).glob("*.cu")) if src else sources()))
+    tmp = lib.with_suffix(f".so.{os.getpid()}.tmp")
     r = subprocess.run([cc, *ARCH, "-shared", "-o", str(tmp), *map(str, objs)],
                        capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

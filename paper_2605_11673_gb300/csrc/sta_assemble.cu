@@ -12,7 +12,15 @@
 // launch configuration.
 #include <climits>
 
+#include "softfloat.cuh"
 #include "sta_internal.cuh"
+
+// Number of the 9 accumulators of a fold step whose additions run on the integer pipes
+// (int_add, bit-identical to the FP64 add); the rest use the FP64 pipe.  Build-time tuning;
+// measured slower on the fold (its loop is latency- rather than FP64-issue-bound), so 0.
+#ifndef STA_INT_ADDS
+#define STA_INT_ADDS 0
+#endif
 
 namespace sta {
 namespace {
@@ -338,7 +346,8 @@ k_fold(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *_
                     fresh = false;
                 }
 #pragma unroll
-                for (int q = 0; q < 9; ++q) acc[q] += v[q];
+                for (int q = 0; q < 9; ++q)
+                    acc[q] = q < STA_INT_ADDS ? int_add(acc[q], v[q]) : acc[q] + v[q];
                 if (have_w) {
 #pragma unroll
                     for (int q = 0; q < 9; ++q) v[q] = w[q];

@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/sta.h"
+#include "sta.h"
 
 namespace sta {
 
