@@ -364,6 +364,225 @@ k_fold(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *_
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Fold of a list of blocks (streaming).  A frame touches few blocks (thousands to tens of
+// thousands), so here latency rules, not FP64 issue: each warp takes up to 32 listed blocks
+// per round (one per lane), counts their active contributors with batched code loads,
+// compacts the active codes into its shared memory and copies their operand runs there with
+// asynchronous 16-byte copies (cp.async, all in flight together), then folds the blocks from
+// shared memory, lanes claiming the staged blocks longest first.  Same fold order and
+// operations as k_fold, so the values are the same bits.
+// ------------------------------------------------------------------------------------------
+constexpr int LIST_WARPS = 4;
+constexpr int LIST_BLOCKS = 64;     // staged blocks per warp
+constexpr int LIST_CONTRIB = 256;   // staged operand runs per warp
+constexpr int LIST_RUN = 10;        // doubles per staged run (80 bytes, 16-byte aligned)
+constexpr size_t LIST_WARP_SMEM = sizeof(int4) * LIST_BLOCKS + sizeof(int32_t) * LIST_CONTRIB +
+                                  sizeof(double) * LIST_RUN * LIST_CONTRIB;
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// copy a contribution's operand run (48 or 80 bytes) into shared memory
+__device__ __forceinline__ void stage_run(const FoldArgs &A, int32_t code, double *dst) {
+    const int la = (code >> 2) & 3, lb = code & 3;
+    const double *rec = A.Ke + (size_t)code_tet(code) * KE_STRIDE;
+    if (la == lb) {
+        const double *src = rec + 6 * la;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) cp_async16(dst + 2 * q, src + 2 * q);
+    } else {
+        const int lo = la < lb ? la : lb, hi = la < lb ? lb : la;
+        const double *src = rec + 24 + 10 * pair_index(lo, hi);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) cp_async16(dst + 2 * q, src + 2 * q);
+    }
+}
+
+// the 9 operands of a staged run (same three layouts as load_contrib)
+__device__ __forceinline__ void smem_operands(const double *r, int32_t code, double v[9]) {
+    const int la = (code >> 2) & 3, lb = code & 3;
+    const double2 *p = reinterpret_cast<const double2 *>(r);
+    const double2 p0 = p[0], p1 = p[1], p2 = p[2];
+    if (la == lb) {
+        v[0] = p0.x; v[1] = p0.y; v[2] = p1.x;
+        v[3] = p0.y; v[4] = p1.y; v[5] = p2.x;
+        v[6] = p1.x; v[7] = p2.x; v[8] = p2.y;
+    } else {
+        const double2 p3 = p[3], p4 = p[4];
+        const double w[9] = {p0.x, p0.y, p1.x, p1.y, p2.x, p2.y, p3.x, p3.y, p4.x};
+        const bool tr = la > lb;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) v[3 * i + j] = tr ? w[3 * j + i] : w[3 * i + j];
+    }
+}
+
+// One lane folds a whole block from global memory (blocks larger than the shared buffers).
+__device__ void fold_direct(const FoldArgs &A, const int4 bm) {
+    double acc[9], v[9];
+    int32_t c = next_active(A, bm.z, bm.w);
+    if (c == bm.w) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) acc[q] = 0.0;
+    } else {
+        load_contrib(A, __ldg(A.ccode + c), acc);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) acc[q] = plus_zero(acc[q]);
+        for (c = next_active(A, c + 1, bm.w); c < bm.w; c = next_active(A, c + 1, bm.w)) {
+            load_contrib(A, __ldg(A.ccode + c), v);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) acc[q] += v[q];
+        }
+    }
+    write_block(A, BlockOut{A.val + bm.x, bm.y >> 1, (bm.y & 1) != 0}, acc);
+}
+
+__global__ void __launch_bounds__(LIST_WARPS * 32)
+k_fold_list(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *__restrict__ count) {
+    extern __shared__ int4 list_smem[];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int4 *sblk = list_smem + (size_t)wid * (LIST_WARP_SMEM / sizeof(int4));
+    int32_t *scode = reinterpret_cast<int32_t *>(sblk + LIST_BLOCKS);
+    double *sop = reinterpret_cast<double *>(scode + LIST_CONTRIB);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nitems = (int64_t)*count;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    int64_t p_base = 0;
+    bool more = true;
+    while (more) {
+        // ------------------------------------------------------------ stage
+        int nlong = 0, nshort = 0, nc = 0;
+        while (true) {
+            const int nb = nlong + nshort;
+            const int64_t p = p_base + lane;
+            const int64_t item = ((p >> 5) * nwarps + warp) * 32 + (p & 31);
+            const bool valid = item < nitems;
+            int4 bm = make_int4(0, 0, 0, 0);
+            if (valid) bm = __ldg(A.bmeta + __ldg(list + item));
+            const unsigned validm = __ballot_sync(FULL, valid);
+            if (!validm) {
+                more = false;
+                break;
+            }
+            const int nv = __popc(validm);
+            int cnt = 0;
+            for (int32_t c0 = bm.z; c0 < bm.w; c0 += 8) {  // 8 code loads in flight
+                int32_t cb[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) cb[u] = c0 + u < bm.w ? __ldg(A.ccode + c0 + u) : 0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) cnt += cb[u] < 0;
+            }
+            const int hi = warp_inclusive_scan(cnt, lane), lo = hi - cnt;
+            const unsigned nzm = __ballot_sync(FULL, valid && cnt > 0);
+            const int blk_upto = nb + __popc(nzm & (lt_mask | (1u << lane)));
+            const bool fits = valid && nc + hi <= LIST_CONTRIB && blk_upto <= LIST_BLOCKS;
+            const unsigned fitm = __ballot_sync(FULL, fits);
+            const int nfit = __popc(fitm);
+            if (nfit == 0) {
+                if (nc == 0 && nb == 0) {  // one block larger than the buffers
+                    if (lane == 0) fold_direct(A, bm);
+                    p_base += 1;
+                    continue;
+                }
+                break;
+            }
+            if (fits) {
+                int j = nc + lo;
+                for (int32_t c = bm.z; c < bm.w; ++c) {
+                    const int32_t code = __ldg(A.ccode + c);
+                    if (code < 0) {
+                        scode[j] = code;
+                        stage_run(A, code, sop + LIST_RUN * j);
+                        ++j;
+                    }
+                }
+            }
+            const unsigned longm = __ballot_sync(FULL, fits && cnt >= LONG_BLOCK);
+            const unsigned shortm = __ballot_sync(FULL, fits && cnt > 0 && cnt < LONG_BLOCK);
+            if (fits) {
+                if (cnt == 0) {
+                    double acc[9];
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) acc[q] = 0.0;
+                    write_block(A, BlockOut{A.val + bm.x, bm.y >> 1, (bm.y & 1) != 0}, acc);
+                } else if (cnt >= LONG_BLOCK) {
+                    sblk[nlong + __popc(longm & lt_mask)] = make_int4(bm.x, bm.y, nc + lo, cnt);
+                } else {
+                    sblk[LIST_BLOCKS - 1 - nshort - __popc(shortm & lt_mask)] =
+                        make_int4(bm.x, bm.y, nc + lo, cnt);
+                }
+            }
+            nlong += __popc(longm);
+            nshort += __popc(shortm);
+            nc += __shfl_sync(FULL, hi, nfit - 1);
+            p_base += nfit;
+            if (nfit < nv) break;
+        }
+        cp_async_wait_all();
+        __syncwarp();
+        // ------------------------------------------------------------ fold
+        const int nstaged = nlong + nshort;
+        int next_blk = 0;
+        bool busy = false, parked = false;
+        int k = 0, kend = 0;
+        BlockOut o{nullptr, 0, false};
+        double acc[9], v[9];
+        auto claim_blocks = [&]() {
+            while (true) {
+                const unsigned need = __ballot_sync(FULL, !busy && !parked);
+                if (!need) break;
+                const int b = next_blk + __popc(need & lt_mask);
+                next_blk += __popc(need);
+                if (!busy && !parked) {
+                    if (b >= nstaged) {
+                        parked = true;
+                    } else {
+                        const int4 sb = sblk[b < nlong ? b : LIST_BLOCKS - 1 - (b - nlong)];
+                        o = BlockOut{A.val + sb.x, sb.y >> 1, (sb.y & 1) != 0};
+                        k = sb.z;
+                        kend = sb.z + sb.w;
+                        smem_operands(sop + LIST_RUN * k, scode[k], v);
+#pragma unroll
+                        for (int q = 0; q < 9; ++q) acc[q] = plus_zero(v[q]);
+                        ++k;
+                        if (k == kend) {
+                            write_block(A, o, acc);
+                        } else {
+                            smem_operands(sop + LIST_RUN * k, scode[k], v);
+                            busy = true;
+                        }
+                    }
+                }
+            }
+        };
+        claim_blocks();
+        while (__any_sync(FULL, busy)) {
+            if (busy) {
+#pragma unroll
+                for (int q = 0; q < 9; ++q) acc[q] += v[q];
+                ++k;
+                if (k < kend) {
+                    smem_operands(sop + LIST_RUN * k, scode[k], v);
+                } else {
+                    write_block(A, o, acc);
+                    busy = false;
+                }
+            }
+            if (__any_sync(FULL, !busy && !parked)) claim_blocks();
+        }
+        __syncwarp();
+    }
+}
+
 // Streaming, phase 1: apply the frame's mask changes and claim each touched block for the
 // lowest candidate index (edited tet k, local pair s -> candidate 16 k + s).
 // edited[k] = tet id | (new state << 31).
@@ -371,19 +590,18 @@ __global__ void k_stream_apply(const int32_t *__restrict__ edited, int64_t m,
                                const int32_t *__restrict__ tblk, const int32_t *__restrict__ cslot,
                                int32_t *__restrict__ ccode, uint8_t *__restrict__ mask,
                                int32_t *__restrict__ owner, unsigned long long *counters) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k == 0) counters[1] = 0ull;
-    if (k >= m) return;
-    uint32_t w = (uint32_t)edited[k];
-    int32_t t = (int32_t)(w & 0x7fffffffu);
+    // one thread per (edited tet k, local pair s)
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) counters[1] = 0ull;
+    if (i >= 16 * m) return;
+    const uint32_t w = (uint32_t)edited[i >> 4];
+    const int32_t t = (int32_t)(w & 0x7fffffffu);
     const uint32_t on = w >> 31;
-    mask[t] = (uint8_t)on;
-#pragma unroll
-    for (int s = 0; s < 16; ++s) {
-        const int32_t slot = cslot[16 * (int64_t)t + s];
-        ccode[slot] = (int32_t)(((uint32_t)ccode[slot] & ~CODE_ACTIVE) | (on << 31));
-        atomicMin(&owner[tblk[16 * (int64_t)t + s]], (int32_t)(16 * k + s));
-    }
+    const int s = (int)(i & 15);
+    if (s == 0) mask[t] = (uint8_t)on;
+    const int32_t slot = cslot[16 * (int64_t)t + s];
+    ccode[slot] = (int32_t)(((uint32_t)ccode[slot] & ~CODE_ACTIVE) | (on << 31));
+    atomicMin(&owner[tblk[16 * (int64_t)t + s]], (int32_t)i);
 }
 
 // Activity bits of all contributor codes from the mask (full rebuild with a new mask).
@@ -429,19 +647,17 @@ __global__ void k_stream_apply_dc(const int32_t *__restrict__ edited, const int6
                                   int32_t *__restrict__ ccode, uint8_t *__restrict__ mask,
                                   int32_t *__restrict__ owner, unsigned long long *counters) {
     if (blockIdx.x == 0 && threadIdx.x == 0) counters[1] = 0ull;
-    const int64_t m = *m_dev;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t w = (uint32_t)edited[k];
+    const int64_t n = 16 * *m_dev;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = (uint32_t)edited[i >> 4];
         const int32_t t = (int32_t)(w & 0x7fffffffu);
         const uint32_t on = w >> 31;
-        mask[t] = (uint8_t)on;
-#pragma unroll
-        for (int s = 0; s < 16; ++s) {
-            const int32_t slot = cslot[16 * (int64_t)t + s];
-            ccode[slot] = (int32_t)(((uint32_t)ccode[slot] & ~CODE_ACTIVE) | (on << 31));
-            atomicMin(&owner[tblk[16 * (int64_t)t + s]], (int32_t)(16 * k + s));
-        }
+        const int s = (int)(i & 15);
+        if (s == 0) mask[t] = (uint8_t)on;
+        const int32_t slot = cslot[16 * (int64_t)t + s];
+        ccode[slot] = (int32_t)(((uint32_t)ccode[slot] & ~CODE_ACTIVE) | (on << 31));
+        atomicMin(&owner[tblk[16 * (int64_t)t + s]], (int32_t)i);
     }
 }
 
@@ -524,6 +740,20 @@ int init_fold_attributes() {
     for (int i = 0; i < 6; ++i)
         STA_CUDA_TRY(cudaFuncSetAttribute(k[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)(FOLD_WARP_SMEM * w[i])));
+    STA_CUDA_TRY(cudaFuncSetAttribute((const void *)k_fold_list,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(LIST_WARP_SMEM * LIST_WARPS)));
+    return STA_OK;
+}
+
+int launch_fold_list(Ctx *c, const int32_t *list, const unsigned long long *count,
+                     int64_t max_items, cudaStream_t s) {
+    const int threads = LIST_WARPS * 32;
+    const size_t smem = LIST_WARP_SMEM * LIST_WARPS;
+    // ~one listed block per lane of the grid, at most the resident CTAs
+    const int grid = persistent_grid(c, (const void *)k_fold_list, threads, max_items, smem);
+    k_fold_list<<<grid, threads, smem, s>>>(fold_args(c), list, count);
+    STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;
 }
 
@@ -549,13 +779,13 @@ int launch_stream(Ctx *c, int64_t m, cudaStream_t s) {
         return STA_OK;
     }
     const int threads = 256;
-    const int64_t g1 = (m + threads - 1) / threads, g2 = (16 * m + threads - 1) / threads;
-    k_stream_apply<<<(unsigned)g1, threads, 0, s>>>(c->d_edited, m, c->tblk, c->cslot, c->ccode,
+    const int64_t g2 = (16 * m + threads - 1) / threads;
+    k_stream_apply<<<(unsigned)g2, threads, 0, s>>>(c->d_edited, m, c->tblk, c->cslot, c->ccode,
                                                     c->mask, c->owner, c->counters);
     k_stream_compact<<<(unsigned)g2, threads, 0, s>>>(c->d_edited, m, c->tblk, c->owner,
                                                       c->touched, c->counters);
     // the touched count is only known on the device: size the grid for the upper bound
-    return launch_fold<1>(c, c->touched, c->counters + 1, 0, 16 * m, s);
+    return launch_fold_list(c, c->touched, c->counters + 1, 16 * m, s);
 }
 
 // Streaming update for graph capture: edited list and its length in device memory, fixed grids
@@ -563,15 +793,15 @@ int launch_stream(Ctx *c, int64_t m, cudaStream_t s) {
 int launch_stream_devcount(Ctx *c, const int32_t *d_edited, const int64_t *d_m, int64_t cap,
                            cudaStream_t s) {
     const int threads = 256;
-    int64_t g1 = (cap + threads - 1) / threads, g2 = (16 * cap + threads - 1) / threads;
-    const int64_t c1 = (int64_t)c->num_sms * 8, c2 = (int64_t)c->num_sms * 16;
+    int64_t g1 = (16 * cap + threads - 1) / threads, g2 = (16 * cap + threads - 1) / threads;
+    const int64_t c1 = (int64_t)c->num_sms * 16, c2 = (int64_t)c->num_sms * 16;
     g1 = g1 < 1 ? 1 : (g1 > c1 ? c1 : g1);
     g2 = g2 < 1 ? 1 : (g2 > c2 ? c2 : g2);
     k_stream_apply_dc<<<(unsigned)g1, threads, 0, s>>>(d_edited, d_m, c->tblk, c->cslot, c->ccode,
                                                        c->mask, c->owner, c->counters);
     k_stream_compact_dc<<<(unsigned)g2, threads, 0, s>>>(d_edited, d_m, c->tblk, c->owner,
                                                          c->touched, c->counters);
-    return launch_fold<1>(c, c->touched, c->counters + 1, 0, 16 * (cap > 0 ? cap : 1), s);
+    return launch_fold_list(c, c->touched, c->counters + 1, 16 * (cap > 0 ? cap : 1), s);
 }
 
 // Streaming update with caller-chosen scratch: the same three kernels as launch_stream, with
@@ -585,12 +815,12 @@ int launch_stream_scratch(Ctx *c, int64_t m, const int32_t *d_edited, int32_t *t
         return STA_OK;
     }
     const int threads = 256;
-    const int64_t g1 = (m + threads - 1) / threads, g2 = (16 * m + threads - 1) / threads;
-    k_stream_apply<<<(unsigned)g1, threads, 0, s>>>(d_edited, m, c->tblk, c->cslot, c->ccode,
+    const int64_t g2 = (16 * m + threads - 1) / threads;
+    k_stream_apply<<<(unsigned)g2, threads, 0, s>>>(d_edited, m, c->tblk, c->cslot, c->ccode,
                                                     c->mask, c->owner, counters);
     k_stream_compact<<<(unsigned)g2, threads, 0, s>>>(d_edited, m, c->tblk, c->owner, touched,
                                                       counters);
-    STA_TRY(launch_fold<1>(c, touched, counters + 1, 0, 16 * m, s));
+    STA_TRY(launch_fold_list(c, touched, counters + 1, 16 * m, s));
     STA_CUDA_TRY(cudaMemcpyAsync(c->counters + 1, counters + 1, sizeof(unsigned long long),
                                  cudaMemcpyDeviceToDevice, s));
     return STA_OK;
