@@ -36,11 +36,20 @@ def build(force: bool = False) -> Path:
     return _LIB
 
 
-def lib():
+def use_library(path=None):
+    """Bind the wrapper to another build of sta_oracle.c (None: the default build).  Used by the
+    mutation tests, which compile deliberately broken copies and check that the pins fail."""
+    global _lib
+    _lib = None
+    return lib(path)
+
+
+def lib(path=None):
     global _lib
     if _lib is None:
-        build()
-        L = C.CDLL(str(_LIB))
+        if path is None:
+            build()
+        L = C.CDLL(str(path or _LIB))
         L.orc_element.argtypes = [_p, _f64, _f64, _p]
         L.orc_element.restype = C.c_int
         L.orc_element_btdb.argtypes = [_p, _f64, _f64, _p]

@@ -1,0 +1,81 @@
+"""Mistakes planted in copies of the oracle (and of the integer-pipe add) must fail a pin.
+
+Each mutation is a plausible slip -- a transposed operand, a dropped term, a wrong sign or
+index, an ignored mask -- compiled on the CPU from a modified copy of the source; the oracle
+wrapper is re-bound to it and the relevant pins of test_oracle_pins run and must fail."""
+import shutil
+import subprocess
+from pathlib import Path
+
+import pytest
+
+import oracle
+import tests.test_oracle_pins as pins
+
+ROOT = Path(__file__).resolve().parent.parent
+SRC = ROOT / "oracle" / "sta_oracle.c"
+
+MUTATIONS = {
+    "transposed_operand": ("v = fma(P[a][i], g[b][j], Q[a][j] * g[b][i]);",
+                           "v = fma(P[a][i], g[b][j], Q[a][i] * g[b][j]);",
+                           [pins.test_element_reference_tet_closed_form,
+                            pins.test_element_matches_literal_btdb]),
+    "dropped_dot_term": ("v = fma(P[a][i], g[b][i], fma(Q[a][i], g[b][i], D[a][b]));",
+                         "v = fma(P[a][i], g[b][i], Q[a][i] * g[b][i]);",
+                         [pins.test_element_reference_tet_closed_form,
+                          pins.test_element_symmetric_exactly_and_rigid_modes]),
+    "g0_sign": ("for (int m = 0; m < 3; ++m) g[0][m] = -((g[1][m] + g[2][m]) + g[3][m]);",
+                "for (int m = 0; m < 3; ++m) g[0][m] = ((g[1][m] + g[2][m]) + g[3][m]);",
+                [pins.test_element_symmetric_exactly_and_rigid_modes]),
+    "lame_lambda": ("double lam = (E * nu) / (onu * (1.0 - (nu + nu)));",
+                    "double lam = (E * nu) / (onu * (1.0 - nu));",
+                    [pins.test_element_reference_tet_closed_form,
+                     pins.test_element_matches_literal_btdb]),
+    "rebuild_ignores_mask": ("        if (!mask[t]) continue;\n        for (int pq = 0; pq < 144; ++pq) val[p->scat",
+                             "        for (int pq = 0; pq < 144; ++pq) val[p->scat",
+                             [pins.test_pattern_and_rebuild_vs_dense_bruteforce]),
+    "recompute_wrong_local_index": ("            acc += Ke[144 * t + 12 * (3 * la + i) + 3 * lb + j];\n        }\n        if (r == c) acc += eps;\n        val[k] = acc;",
+                                    "            acc += Ke[144 * t + 12 * (3 * lb + i) + 3 * la + j];\n        }\n        if (r == c) acc += eps;\n        val[k] = acc;",
+                                    [pins.test_local_recompute_equals_rebuild_every_frame]),
+    "dnu_sign": ("- sb * E / (2.0 * onu * onu));", "+ sb * E / (2.0 * onu * onu));",
+                 [pins.test_element_param_grad_vs_fd_and_linearity]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_oracle_mistake_fails_a_pin(name, tmp_path):
+    old, new, checks = MUTATIONS[name]
+    src = SRC.read_text()
+    assert src.count(old) == 1, name
+    mut = tmp_path / "mutant.c"
+    mut.write_text(src.replace(old, new))
+    so = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(so),
+                           str(mut), "-lm"])
+    try:
+        oracle.use_library(so)
+        failed = 0
+        for check in checks:
+            try:
+                if "tmp_path" in check.__code__.co_varnames[:check.__code__.co_argcount]:
+                    check(oracle, tmp_path)
+                else:
+                    check(oracle)
+            except AssertionError:
+                failed += 1
+        assert failed > 0, f"mutation {name} passed every pin"
+    finally:
+        oracle.use_library(None)
+
+
+@pytest.mark.skipif(shutil.which("g++") is None, reason="needs g++")
+def test_planted_rounding_mistake_in_int_add_is_caught(tmp_path):
+    hdr = (ROOT / "paper_2605_11673_gb300" / "csrc" / "softfloat.cuh").read_text()
+    old = "if (rem > 0x200 || (rem == 0x200 && (sig & 1))) ++sig;"
+    assert hdr.count(old) == 1
+    (tmp_path / "softfloat.cuh").write_text(hdr.replace(old, "if (rem >= 0x200) ++sig;"))
+    exe = tmp_path / "check"
+    subprocess.check_call(["g++", "-O2", "-ffp-contract=off", "-std=c++17", f"-I{tmp_path}",
+                           str(ROOT / "tests" / "native" / "int_add_check.cpp"), "-o", str(exe)])
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0 and int(r.stdout.split()[-1]) > 0
