@@ -334,9 +334,9 @@ int sta_last_touched(sta_ctx *x, int64_t *touched_nnz, void *stream) {
     if (!x || !touched_nnz) return fail(STA_EINVAL, "NULL argument");
     unsigned long long v = 0;
     cudaStream_t s = (cudaStream_t)stream;
-    STA_CUDA_TRY(cudaMemcpyAsync(&v, x->c.counters + 1, sizeof v, cudaMemcpyDeviceToHost, s));
+    STA_CUDA_TRY(cudaMemcpyAsync(&v, x->c.counters + 3, sizeof v, cudaMemcpyDeviceToHost, s));
     STA_CUDA_TRY(cudaStreamSynchronize(s));
-    *touched_nnz = 9 * (int64_t)v;
+    *touched_nnz = (int64_t)v;
     return STA_OK;
 }
 

@@ -26,7 +26,8 @@ namespace sta {
 namespace {
 
 struct FoldArgs {
-    const int4 *__restrict__ bmeta;     // per block: value offset, row stride/diag, c0, c1
+    const int4 *__restrict__ bmeta;     // per unit: value offset of (a,b), rs_a << 1 | diag, c0, c1
+    const int2 *__restrict__ bmirror;   // per unit: value offset of (b,a), rs_b
     const int32_t *__restrict__ ccode;  // contributor codes, bit 31 = active
     const double *__restrict__ Ke;
     double *__restrict__ val;
@@ -43,23 +44,23 @@ __device__ __forceinline__ int pair_index(int a, int b) {  // a < b
     return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);
 }
 
-// The 9 operands (i, j) one contributor supplies to a block, read with 16-byte loads from
-// its stored run:
-//   diagonal block (la == lb): the 6-run of (la, la), mirrored;
-//   off-diagonal, la < lb:      the 9-run of (la, lb), row-major;
-//   off-diagonal, la > lb:      the 9-run of (lb, la), transposed.
-// Folding a diagonal block with 9 accumulators gives (i, j) and (j, i) the same sequence of
-// operands, so the mirrored outputs equal those of a 6-accumulator fold.
+// The operands one contributor supplies to a fold unit (node pair a <= b; la, lb the local
+// indices of a and b in the contributing tetrahedron), read with 16-byte loads:
+//   diagonal unit (la == lb): the 6-run of (la, la): v[0..5] = (0,0) (0,1) (0,2) (1,1) (1,2)
+//                              (2,2); the mirrored entries (j, i) fold the same operands;
+//   off-diagonal, la < lb:     the 9-run of (la, lb), row-major: v[3i+j] = K[3la+i][3lb+j];
+//   off-diagonal, la > lb:     the 9-run of (lb, la), transposed.
+// The mirror block (b, a) folds exactly the same operand sequence (K is stored exactly
+// symmetric), so one fold per unit gives both blocks' values bit for bit.
 __device__ __forceinline__ void load_contrib(const FoldArgs &A, int32_t code, double v[9]) {
     const int la = (code >> 2) & 3, lb = code & 3;
     const double *rec = A.Ke + (size_t)code_tet(code) * KE_STRIDE;
     if (la == lb) {
         const double2 *r = reinterpret_cast<const double2 *>(rec + 6 * la);
         const double2 x = __ldg(r), y = __ldg(r + 1), z = __ldg(r + 2);
-        // 6-run order (0,0) (0,1) (0,2) (1,1) (1,2) (2,2)
         v[0] = x.x; v[1] = x.y; v[2] = y.x;
-        v[3] = x.y; v[4] = y.y; v[5] = z.x;
-        v[6] = y.x; v[7] = z.x; v[8] = z.y;
+        v[3] = y.y; v[4] = z.x; v[5] = z.y;
+        v[6] = 0.0; v[7] = 0.0; v[8] = 0.0;
     } else {
         const int lo = la < lb ? la : lb, hi = la < lb ? lb : la;
         const double2 *r = reinterpret_cast<const double2 *>(rec + 24 + 10 * pair_index(lo, hi));
@@ -81,21 +82,40 @@ __device__ __forceinline__ int32_t next_active(const FoldArgs &A, int32_t c, int
 }
 
 struct BlockOut {
-    double *out;
-    int rs;
+    double *out;   // block (a, b)
+    double *out2;  // its mirror (b, a)
+    int rs, rs2;
     bool diag;
 };
 
+__device__ __forceinline__ BlockOut unit_out(const FoldArgs &A, int4 bm, int2 mir) {
+    return BlockOut{A.val + bm.x, A.val + mir.x, bm.y >> 1, mir.y, (bm.y & 1) != 0};
+}
+
+// Writes a unit's folds: a diagonal unit's 6 folds to the 9 entries of its block (mirrored,
+// eps added to the diagonal entries last); an off-diagonal unit's 9 folds to (a, b) and,
+// transposed, to (b, a).
 __device__ __forceinline__ void write_block(const FoldArgs &A, const BlockOut &o, double acc[9]) {
-    if (o.diag && A.eps != 0.0) {
-        acc[0] += A.eps;
-        acc[4] += A.eps;
-        acc[8] += A.eps;
+    if (o.diag) {
+        if (A.eps != 0.0) {
+            acc[0] += A.eps;
+            acc[3] += A.eps;
+            acc[5] += A.eps;
+        }
+        const int tri[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) o.out[i * o.rs + j] = acc[tri[i][j]];
+    } else {
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                o.out[i * o.rs + j] = acc[3 * i + j];
+                o.out2[j * o.rs2 + i] = acc[3 * i + j];
+            }
     }
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) o.out[i * o.rs + j] = acc[3 * i + j];
 }
 
 // Lockstep fold.  On GB300 a warp-wide FP64 instruction costs the same however many lanes
@@ -122,7 +142,8 @@ constexpr int STAGE_BLOCKS = 192;   // staged blocks per warp
 constexpr int STAGE_CODES = 1280;   // staged active codes per warp (>= contributors of any block)
 constexpr int STAGE_WIN = 8;        // 32-code windows of one staging round held in registers
 constexpr int LONG_BLOCK = 8;       // staged blocks with this many contributors are claimed first
-constexpr size_t FOLD_WARP_SMEM = sizeof(int4) * STAGE_BLOCKS + sizeof(int32_t) * STAGE_CODES;
+constexpr size_t FOLD_WARP_SMEM = sizeof(int4) * STAGE_BLOCKS + sizeof(int2) * STAGE_BLOCKS +
+                                  sizeof(int32_t) * STAGE_CODES;
 
 __device__ __forceinline__ int warp_inclusive_scan(int x, int lane) {
 #pragma unroll
@@ -139,8 +160,8 @@ __device__ __forceinline__ unsigned below(int n) {
 }
 
 // A block with at most one active contributor: written directly (+0.0, or +0.0 + c).
-__device__ __forceinline__ void write_small_block(const FoldArgs &A, const int4 bm, int cnt,
-                                                  int32_t code) {
+__device__ __forceinline__ void write_small_block(const FoldArgs &A, const int4 bm, int2 mir,
+                                                  int cnt, int32_t code) {
     double acc[9];
     if (cnt == 0) {
 #pragma unroll
@@ -150,7 +171,7 @@ __device__ __forceinline__ void write_small_block(const FoldArgs &A, const int4 
 #pragma unroll
         for (int q = 0; q < 9; ++q) acc[q] = plus_zero(acc[q]);
     }
-    write_block(A, BlockOut{A.val + bm.x, bm.y >> 1, (bm.y & 1) != 0}, acc);
+    write_block(A, unit_out(A, bm, mir), acc);
 }
 
 template <int MODE, int WARPS>
@@ -162,7 +183,8 @@ k_fold(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *_
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int4 *sblk = fold_smem + (size_t)wid * (FOLD_WARP_SMEM / sizeof(int4));
-    int32_t *scode = reinterpret_cast<int32_t *>(sblk + STAGE_BLOCKS);
+    int2 *smir = reinterpret_cast<int2 *>(sblk + STAGE_BLOCKS);
+    int32_t *scode = reinterpret_cast<int32_t *>(smir + STAGE_BLOCKS);
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nitems = MODE == 0 ? nitems_static : (int64_t)*count;
@@ -187,7 +209,11 @@ k_fold(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *_
                 }
                 const int nv = __popc(validm);  // valid lanes form a prefix
                 int4 bm = make_int4(0, 0, 0, 0);
-                if (valid) bm = __ldg(A.bmeta + g);
+                int2 mir = make_int2(0, 0);
+                if (valid) {
+                    bm = __ldg(A.bmeta + g);
+                    mir = __ldg(A.bmirror + g);
+                }
                 const int32_t r0 = __shfl_sync(FULL, bm.z, 0);
                 const int32_t r1 = __shfl_sync(FULL, bm.w, nv - 1);
                 const int nwin = (r1 - r0 + 31) >> 5;
@@ -249,13 +275,15 @@ k_fold(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *_
                     const unsigned longm = __ballot_sync(FULL, fits && cnt >= LONG_BLOCK);
                     const unsigned shortm = __ballot_sync(FULL, fits && cnt >= 2 && cnt < LONG_BLOCK);
                     if (fits) {
-                        if (cnt < 2)
-                            write_small_block(A, bm, cnt, cnt ? scode[nc + lo] : 0);
-                        else if (cnt >= LONG_BLOCK)
-                            sblk[nlong + __popc(longm & lt_mask)] = make_int4(bm.x, bm.y, nc + lo, cnt);
-                        else
-                            sblk[STAGE_BLOCKS - 1 - nshort - __popc(shortm & lt_mask)] =
-                                make_int4(bm.x, bm.y, nc + lo, cnt);
+                        if (cnt < 2) {
+                            write_small_block(A, bm, mir, cnt, cnt ? scode[nc + lo] : 0);
+                        } else {
+                            const int at = cnt >= LONG_BLOCK
+                                               ? nlong + __popc(longm & lt_mask)
+                                               : STAGE_BLOCKS - 1 - nshort - __popc(shortm & lt_mask);
+                            sblk[at] = make_int4(bm.x, bm.y, nc + lo, cnt);
+                            smir[at] = mir;
+                        }
                     }
                     nlong += __popc(longm);
                     nshort += __popc(shortm);
@@ -268,9 +296,12 @@ k_fold(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *_
                 const int64_t item = ((p >> 5) * nwarps + warp) * 32 + (p & 31);
                 const bool valid = item < nitems;
                 int4 bm = make_int4(0, 0, 0, 0);
+                int2 mir = make_int2(0, 0);
                 int cnt = 0;
                 if (valid) {
-                    bm = __ldg(A.bmeta + __ldg(list + item));
+                    const int32_t u = __ldg(list + item);
+                    bm = __ldg(A.bmeta + u);
+                    mir = __ldg(A.bmirror + u);
                     for (int32_t c = bm.z; c < bm.w; ++c) cnt += __ldg(A.ccode + c) < 0;
                 }
                 const int inc = warp_inclusive_scan(cnt, lane);
@@ -285,13 +316,15 @@ k_fold(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *_
                         const int32_t code = __ldg(A.ccode + c);
                         if (code < 0) scode[at + j++] = code;
                     }
-                    if (cnt < 2)
-                        write_small_block(A, bm, cnt, cnt ? scode[at] : 0);
-                    else if (cnt >= LONG_BLOCK)
-                        sblk[nlong + __popc(longm & lt_mask)] = make_int4(bm.x, bm.y, at, cnt);
-                    else
-                        sblk[STAGE_BLOCKS - 1 - nshort - __popc(shortm & lt_mask)] =
-                            make_int4(bm.x, bm.y, at, cnt);
+                    if (cnt < 2) {
+                        write_small_block(A, bm, mir, cnt, cnt ? scode[at] : 0);
+                    } else {
+                        const int idx = cnt >= LONG_BLOCK
+                                            ? nlong + __popc(longm & lt_mask)
+                                            : STAGE_BLOCKS - 1 - nshort - __popc(shortm & lt_mask);
+                        sblk[idx] = make_int4(bm.x, bm.y, at, cnt);
+                        smir[idx] = mir;
+                    }
                 }
                 const int nfit = __popc(fitm);  // fitting lanes form a prefix
                 if (nfit > 0) nc += __shfl_sync(FULL, inc, nfit - 1);
@@ -309,7 +342,7 @@ k_fold(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *_
         int next_blk = 0;  // warp-uniform: staged blocks claimed so far
         bool busy = false;
         int k = 0, kend = 0;
-        BlockOut o{nullptr, 0, false};
+        BlockOut o{nullptr, nullptr, 0, 0, false};
         // acc: accumulators; v: operands of the next contribution to add; w: of the one after
         // (two contributions in flight per lane).  Right after a claim, acc holds the raw
         // operands of contribution 2 and v those of contribution 1 (fresh).
@@ -322,8 +355,9 @@ k_fold(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *_
             if (!busy) {
                 const int b = next_blk + __popc(claim & lt_mask);
                 if (b < nlong + nshort) {
-                    const int4 sb = sblk[b < nlong ? b : STAGE_BLOCKS - 1 - (b - nlong)];
-                    o = BlockOut{A.val + sb.x, sb.y >> 1, (sb.y & 1) != 0};
+                    const int at = b < nlong ? b : STAGE_BLOCKS - 1 - (b - nlong);
+                    const int4 sb = sblk[at];
+                    o = unit_out(A, sb, smir[at]);
                     k = sb.z;
                     kend = sb.z + sb.w;
                     load_contrib(A, scode[k], v);
@@ -346,8 +380,13 @@ k_fold(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *_
                     fresh = false;
                 }
 #pragma unroll
-                for (int q = 0; q < 9; ++q)
+                for (int q = 0; q < 6; ++q)
                     acc[q] = q < STA_INT_ADDS ? int_add(acc[q], v[q]) : acc[q] + v[q];
+                if (!o.diag) {  // a diagonal unit folds 6 entries
+#pragma unroll
+                    for (int q = 6; q < 9; ++q)
+                        acc[q] = q < STA_INT_ADDS ? int_add(acc[q], v[q]) : acc[q] + v[q];
+                }
                 if (have_w) {
 #pragma unroll
                     for (int q = 0; q < 9; ++q) v[q] = w[q];
@@ -377,7 +416,8 @@ constexpr int LIST_WARPS = 4;
 constexpr int LIST_BLOCKS = 64;     // staged blocks per warp
 constexpr int LIST_CONTRIB = 256;   // staged operand runs per warp
 constexpr int LIST_RUN = 10;        // doubles per staged run (80 bytes, 16-byte aligned)
-constexpr size_t LIST_WARP_SMEM = sizeof(int4) * LIST_BLOCKS + sizeof(int32_t) * LIST_CONTRIB +
+constexpr size_t LIST_WARP_SMEM = sizeof(int4) * LIST_BLOCKS + sizeof(int2) * LIST_BLOCKS +
+                                  sizeof(int32_t) * LIST_CONTRIB +
                                   sizeof(double) * LIST_RUN * LIST_CONTRIB;
 
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
@@ -410,8 +450,8 @@ __device__ __forceinline__ void smem_operands(const double *r, int32_t code, dou
     const double2 p0 = p[0], p1 = p[1], p2 = p[2];
     if (la == lb) {
         v[0] = p0.x; v[1] = p0.y; v[2] = p1.x;
-        v[3] = p0.y; v[4] = p1.y; v[5] = p2.x;
-        v[6] = p1.x; v[7] = p2.x; v[8] = p2.y;
+        v[3] = p1.y; v[4] = p2.x; v[5] = p2.y;
+        v[6] = 0.0; v[7] = 0.0; v[8] = 0.0;
     } else {
         const double2 p3 = p[3], p4 = p[4];
         const double w[9] = {p0.x, p0.y, p1.x, p1.y, p2.x, p2.y, p3.x, p3.y, p4.x};
@@ -423,8 +463,8 @@ __device__ __forceinline__ void smem_operands(const double *r, int32_t code, dou
     }
 }
 
-// One lane folds a whole block from global memory (blocks larger than the shared buffers).
-__device__ void fold_direct(const FoldArgs &A, const int4 bm) {
+// One lane folds a whole unit from global memory (units larger than the shared buffers).
+__device__ void fold_direct(const FoldArgs &A, const int4 bm, const int2 mir) {
     double acc[9], v[9];
     int32_t c = next_active(A, bm.z, bm.w);
     if (c == bm.w) {
@@ -437,10 +477,10 @@ __device__ void fold_direct(const FoldArgs &A, const int4 bm) {
         for (c = next_active(A, c + 1, bm.w); c < bm.w; c = next_active(A, c + 1, bm.w)) {
             load_contrib(A, __ldg(A.ccode + c), v);
 #pragma unroll
-            for (int q = 0; q < 9; ++q) acc[q] += v[q];
+            for (int q = 0; q < 9; ++q) acc[q] += v[q];  // (diagonal: entries 6..8 unused)
         }
     }
-    write_block(A, BlockOut{A.val + bm.x, bm.y >> 1, (bm.y & 1) != 0}, acc);
+    write_block(A, unit_out(A, bm, mir), acc);
 }
 
 __global__ void __launch_bounds__(LIST_WARPS * 32)
@@ -449,7 +489,8 @@ k_fold_list(FoldArgs A, const int32_t *__restrict__ list, const unsigned long lo
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int4 *sblk = list_smem + (size_t)wid * (LIST_WARP_SMEM / sizeof(int4));
-    int32_t *scode = reinterpret_cast<int32_t *>(sblk + LIST_BLOCKS);
+    int2 *smir = reinterpret_cast<int2 *>(sblk + LIST_BLOCKS);
+    int32_t *scode = reinterpret_cast<int32_t *>(smir + LIST_BLOCKS);
     double *sop = reinterpret_cast<double *>(scode + LIST_CONTRIB);
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -466,7 +507,12 @@ k_fold_list(FoldArgs A, const int32_t *__restrict__ list, const unsigned long lo
             const int64_t item = ((p >> 5) * nwarps + warp) * 32 + (p & 31);
             const bool valid = item < nitems;
             int4 bm = make_int4(0, 0, 0, 0);
-            if (valid) bm = __ldg(A.bmeta + __ldg(list + item));
+            int2 mir = make_int2(0, 0);
+            if (valid) {
+                const int32_t u = __ldg(list + item);
+                bm = __ldg(A.bmeta + u);
+                mir = __ldg(A.bmirror + u);
+            }
             const unsigned validm = __ballot_sync(FULL, valid);
             if (!validm) {
                 more = false;
@@ -489,7 +535,7 @@ k_fold_list(FoldArgs A, const int32_t *__restrict__ list, const unsigned long lo
             const int nfit = __popc(fitm);
             if (nfit == 0) {
                 if (nc == 0 && nb == 0) {  // one block larger than the buffers
-                    if (lane == 0) fold_direct(A, bm);
+                    if (lane == 0) fold_direct(A, bm, mir);
                     p_base += 1;
                     continue;
                 }
@@ -513,12 +559,12 @@ k_fold_list(FoldArgs A, const int32_t *__restrict__ list, const unsigned long lo
                     double acc[9];
 #pragma unroll
                     for (int q = 0; q < 9; ++q) acc[q] = 0.0;
-                    write_block(A, BlockOut{A.val + bm.x, bm.y >> 1, (bm.y & 1) != 0}, acc);
-                } else if (cnt >= LONG_BLOCK) {
-                    sblk[nlong + __popc(longm & lt_mask)] = make_int4(bm.x, bm.y, nc + lo, cnt);
+                    write_block(A, unit_out(A, bm, mir), acc);
                 } else {
-                    sblk[LIST_BLOCKS - 1 - nshort - __popc(shortm & lt_mask)] =
-                        make_int4(bm.x, bm.y, nc + lo, cnt);
+                    const int at = cnt >= LONG_BLOCK ? nlong + __popc(longm & lt_mask)
+                                                     : LIST_BLOCKS - 1 - nshort - __popc(shortm & lt_mask);
+                    sblk[at] = make_int4(bm.x, bm.y, nc + lo, cnt);
+                    smir[at] = mir;
                 }
             }
             nlong += __popc(longm);
@@ -534,7 +580,7 @@ k_fold_list(FoldArgs A, const int32_t *__restrict__ list, const unsigned long lo
         int next_blk = 0;
         bool busy = false, parked = false;
         int k = 0, kend = 0;
-        BlockOut o{nullptr, 0, false};
+        BlockOut o{nullptr, nullptr, 0, 0, false};
         double acc[9], v[9];
         auto claim_blocks = [&]() {
             while (true) {
@@ -546,8 +592,9 @@ k_fold_list(FoldArgs A, const int32_t *__restrict__ list, const unsigned long lo
                     if (b >= nstaged) {
                         parked = true;
                     } else {
-                        const int4 sb = sblk[b < nlong ? b : LIST_BLOCKS - 1 - (b - nlong)];
-                        o = BlockOut{A.val + sb.x, sb.y >> 1, (sb.y & 1) != 0};
+                        const int at = b < nlong ? b : LIST_BLOCKS - 1 - (b - nlong);
+                        const int4 sb = sblk[at];
+                        o = unit_out(A, sb, smir[at]);
                         k = sb.z;
                         kend = sb.z + sb.w;
                         smem_operands(sop + LIST_RUN * k, scode[k], v);
@@ -568,7 +615,11 @@ k_fold_list(FoldArgs A, const int32_t *__restrict__ list, const unsigned long lo
         while (__any_sync(FULL, busy)) {
             if (busy) {
 #pragma unroll
-                for (int q = 0; q < 9; ++q) acc[q] += v[q];
+                for (int q = 0; q < 6; ++q) acc[q] += v[q];
+                if (!o.diag) {
+#pragma unroll
+                    for (int q = 6; q < 9; ++q) acc[q] += v[q];
+                }
                 ++k;
                 if (k < kend) {
                     smem_operands(sop + LIST_RUN * k, scode[k], v);
@@ -583,25 +634,130 @@ k_fold_list(FoldArgs A, const int32_t *__restrict__ list, const unsigned long lo
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Entry-parallel fold of a list of units (streaming).  A frame's touched list is short and its
+// longest folds (diagonal units, ~24 contributions) set the latency, so here each lane folds ONE
+// matrix entry: a warp takes 3 listed units, lanes 9g .. 9g+8 fold the 9 entries (i, j) of
+// unit g (6 of them for a diagonal unit), and one FP64 instruction per step advances all 27
+// folds.  The unit's active codes are compacted (in list order) into shared memory first; each
+// step then loads one operand per lane (4 steps of loads in flight).  Operands, order and
+// operations are those of k_fold, so the values are the same bits.
+// ------------------------------------------------------------------------------------------
+constexpr int ENT_UNITS = 3;    // units per warp round (27 lanes)
+constexpr int ENT_CAP = 96;     // active contributions staged per unit; larger units fold directly
+constexpr int ENT_WARPS = 4;
+
+template <int MODE>  // 0: units 0 .. nitems_static-1; 1: the listed units (count on the device)
+__global__ void __launch_bounds__(ENT_WARPS * 32)
+k_fold_entries(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *__restrict__ count,
+               int64_t nitems_static) {
+    __shared__ int32_t scode_all[ENT_WARPS][ENT_UNITS][ENT_CAP];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int g = lane / 9, q = lane % 9;  // g == 3: lanes 27..31 idle
+    const int qi = q / 3, qj = q % 3;
+    int32_t *scode = scode_all[wid][g < ENT_UNITS ? g : 0];
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nitems = MODE == 0 ? nitems_static : (int64_t)*count;
+    for (int64_t base = warp * ENT_UNITS; base < nitems; base += nwarps * ENT_UNITS) {  // warp-uniform
+        const int64_t item = base + g;
+        const bool valid = g < ENT_UNITS && item < nitems;
+        int4 bm = make_int4(0, 0, 0, 0);
+        int2 mir = make_int2(0, 0);
+        if (valid) {
+            const int32_t u = MODE == 0 ? (int32_t)item : __ldg(list + item);
+            bm = __ldg(A.bmeta + u);
+            mir = __ldg(A.bmirror + u);
+        }
+        // compact the unit's active codes, 9 lanes striding over its contributor list
+        int nact = 0;
+        const int span = valid ? bm.w - bm.z : 0;
+        const int max_span = __reduce_max_sync(FULL, span);
+        for (int c0 = 0; c0 < max_span; c0 += 9) {
+            const int c = c0 + q;
+            const int32_t code = (valid && c < span) ? __ldg(A.ccode + bm.z + c) : 0;
+            const unsigned m = __ballot_sync(FULL, code < 0);
+            const unsigned gm = (m >> (9 * g)) & 0x1ffu;
+            const int pos = nact + __popc(gm & ((1u << q) - 1u));
+            if (code < 0 && pos < ENT_CAP) scode[pos] = code;
+            nact += __popc(gm);
+        }
+        __syncwarp();
+        const bool big = valid && nact > ENT_CAP;
+        if (big && q == 0) fold_direct(A, bm, mir);  // rare: more active contributions than staged
+        const int n = valid && !big ? nact : 0;
+        const bool diag = (bm.y & 1) != 0;
+        const bool mine = n > 0 && (!diag || q < 6);  // a diagonal unit folds 6 entries
+        double acc = 0.0;
+        const int maxn = __reduce_max_sync(FULL, n);
+        for (int j0 = 0; j0 < maxn; j0 += 4) {
+            double v[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                v[t] = 0.0;
+                const int j = j0 + t;
+                if (mine && j < n) {
+                    const int32_t code = scode[j];
+                    const int la = (code >> 2) & 3, lb = code & 3;
+                    const double *rec = A.Ke + (size_t)code_tet(code) * KE_STRIDE;
+                    if (la == lb) {
+                        v[t] = __ldg(rec + 6 * la + q);
+                    } else {
+                        const int lo = la < lb ? la : lb, hi = la < lb ? lb : la;
+                        v[t] = __ldg(rec + 24 + 10 * pair_index(lo, hi) + (la < lb ? q : 3 * qj + qi));
+                    }
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int j = j0 + t;
+                if (mine && j < n) acc = j == 0 ? plus_zero(v[t]) : acc + v[t];
+            }
+        }
+        if (valid && !big) {
+            if (diag) {
+                if (q < 6) {
+                    // 6-run entry q = (i, j), i <= j
+                    const int i = q < 3 ? 0 : (q < 5 ? 1 : 2), j = q < 3 ? q : (q < 5 ? q - 2 : 2);
+                    double a = acc;
+                    if (i == j && A.eps != 0.0) a += A.eps;
+                    double *out = A.val + bm.x;
+                    const int rs = bm.y >> 1;
+                    out[i * rs + j] = a;
+                    if (i != j) out[j * rs + i] = a;
+                }
+            } else {
+                A.val[bm.x + qi * (bm.y >> 1) + qj] = acc;
+                A.val[mir.x + qj * mir.y + qi] = acc;
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // Streaming, phase 1: apply the frame's mask changes and claim each touched block for the
 // lowest candidate index (edited tet k, local pair s -> candidate 16 k + s).
 // edited[k] = tet id | (new state << 31).
 __global__ void k_stream_apply(const int32_t *__restrict__ edited, int64_t m,
-                               const int32_t *__restrict__ tblk, const int32_t *__restrict__ cslot,
+                               const int32_t *__restrict__ tunit, const int32_t *__restrict__ cslot,
                                int32_t *__restrict__ ccode, uint8_t *__restrict__ mask,
                                int32_t *__restrict__ owner, unsigned long long *counters) {
-    // one thread per (edited tet k, local pair s)
+    // one thread per (edited tet k, unit slot s): candidate 10 k + s
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) counters[1] = 0ull;
-    if (i >= 16 * m) return;
-    const uint32_t w = (uint32_t)edited[i >> 4];
+    if (i == 0) {
+        counters[1] = 0ull;
+        counters[3] = 0ull;
+    }
+    if (i >= 10 * m) return;
+    const uint32_t w = (uint32_t)edited[i / 10];
     const int32_t t = (int32_t)(w & 0x7fffffffu);
     const uint32_t on = w >> 31;
-    const int s = (int)(i & 15);
+    const int s = (int)(i % 10);
     if (s == 0) mask[t] = (uint8_t)on;
-    const int32_t slot = cslot[16 * (int64_t)t + s];
+    const int32_t slot = cslot[10 * (int64_t)t + s];
     ccode[slot] = (int32_t)(((uint32_t)ccode[slot] & ~CODE_ACTIVE) | (on << 31));
-    atomicMin(&owner[tblk[16 * (int64_t)t + s]], (int32_t)i);
+    atomicMin(&owner[tunit[10 * (int64_t)t + s]], (int32_t)i);
 }
 
 // Activity bits of all contributor codes from the mask (full rebuild with a new mask).
@@ -618,21 +774,28 @@ __global__ void k_mask_bits(int32_t *__restrict__ ccode, int64_t n, const uint8_
 // releases the claim.  A non-owner reads either the owner's index or INT32_MAX, never its
 // own index, so the release does not race with the ownership test.  The list order depends
 // on scheduling; the values do not (each block is folded independently).
-__global__ void k_stream_compact(const int32_t *__restrict__ edited, int64_t m,
-                                 const int32_t *__restrict__ tblk, int32_t *__restrict__ owner,
-                                 int32_t *__restrict__ list, unsigned long long *counters) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool mine = false;
+__device__ __forceinline__ void compact_one(int64_t i, int64_t n, const int32_t *__restrict__ edited,
+                                            const int32_t *__restrict__ tunit,
+                                            int32_t *__restrict__ owner, int32_t *__restrict__ list,
+                                            unsigned long long *counters) {
+    bool mine = false, diag = false;
     int32_t g = 0;
-    if (i < 16 * m) {
-        int32_t t = (int32_t)((uint32_t)edited[i >> 4] & 0x7fffffffu);
-        g = tblk[16 * (int64_t)t + (i & 15)];
+    if (i < n) {
+        const int32_t t = (int32_t)((uint32_t)edited[i / 10] & 0x7fffffffu);
+        const int s = (int)(i % 10);
+        g = tunit[10 * (int64_t)t + s];
+        diag = s < 4;
         mine = owner[g] == (int32_t)i;
     }
     const unsigned ball = __ballot_sync(0xffffffffu, mine);
+    const unsigned dball = __ballot_sync(0xffffffffu, mine && diag);
     unsigned long long base = 0;
     const int lane = threadIdx.x & 31;
-    if (lane == 0 && ball) base = atomicAdd(&counters[1], (unsigned long long)__popc(ball));
+    if (lane == 0 && ball) {
+        base = atomicAdd(&counters[1], (unsigned long long)__popc(ball));
+        // touched CSR entries: 9 for a diagonal unit, 18 (both blocks) for a pair
+        atomicAdd(&counters[3], (unsigned long long)(18 * __popc(ball) - 9 * __popc(dball)));
+    }
     base = __shfl_sync(0xffffffffu, base, 0);
     if (mine) {
         list[base + __popc(ball & ((1u << lane) - 1u))] = g;
@@ -640,52 +803,46 @@ __global__ void k_stream_compact(const int32_t *__restrict__ edited, int64_t m,
     }
 }
 
+__global__ void k_stream_compact(const int32_t *__restrict__ edited, int64_t m,
+                                 const int32_t *__restrict__ tunit, int32_t *__restrict__ owner,
+                                 int32_t *__restrict__ list, unsigned long long *counters) {
+    compact_one((int64_t)blockIdx.x * blockDim.x + threadIdx.x, 10 * m, edited, tunit, owner, list,
+                counters);
+}
+
 // Device-count variants of the two streaming kernels for CUDA-graph replay: the number of
 // edited tetrahedra is read from device memory, the grid is fixed and strides over it.
 __global__ void k_stream_apply_dc(const int32_t *__restrict__ edited, const int64_t *__restrict__ m_dev,
-                                  const int32_t *__restrict__ tblk, const int32_t *__restrict__ cslot,
+                                  const int32_t *__restrict__ tunit, const int32_t *__restrict__ cslot,
                                   int32_t *__restrict__ ccode, uint8_t *__restrict__ mask,
                                   int32_t *__restrict__ owner, unsigned long long *counters) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) counters[1] = 0ull;
-    const int64_t n = 16 * *m_dev;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        counters[1] = 0ull;
+        counters[3] = 0ull;
+    }
+    const int64_t n = 10 * *m_dev;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t w = (uint32_t)edited[i >> 4];
+        const uint32_t w = (uint32_t)edited[i / 10];
         const int32_t t = (int32_t)(w & 0x7fffffffu);
         const uint32_t on = w >> 31;
-        const int s = (int)(i & 15);
+        const int s = (int)(i % 10);
         if (s == 0) mask[t] = (uint8_t)on;
-        const int32_t slot = cslot[16 * (int64_t)t + s];
+        const int32_t slot = cslot[10 * (int64_t)t + s];
         ccode[slot] = (int32_t)(((uint32_t)ccode[slot] & ~CODE_ACTIVE) | (on << 31));
-        atomicMin(&owner[tblk[16 * (int64_t)t + s]], (int32_t)i);
+        atomicMin(&owner[tunit[10 * (int64_t)t + s]], (int32_t)i);
     }
 }
 
 __global__ void k_stream_compact_dc(const int32_t *__restrict__ edited, const int64_t *__restrict__ m_dev,
-                                    const int32_t *__restrict__ tblk, int32_t *__restrict__ owner,
+                                    const int32_t *__restrict__ tunit, int32_t *__restrict__ owner,
                                     int32_t *__restrict__ list, unsigned long long *counters) {
-    const int64_t n = 16 * *m_dev;
-    const int lane = threadIdx.x & 31;
+    const int64_t n = 10 * *m_dev;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // warp-uniform
-        const int64_t i = i0 + threadIdx.x;
-        bool mine = false;
-        int32_t g = 0;
-        if (i < n) {
-            const int32_t t = (int32_t)((uint32_t)edited[i >> 4] & 0x7fffffffu);
-            g = tblk[16 * (int64_t)t + (i & 15)];
-            mine = owner[g] == (int32_t)i;
-        }
-        const unsigned ball = __ballot_sync(0xffffffffu, mine);
-        unsigned long long base = 0;
-        if (lane == 0 && ball) base = atomicAdd(&counters[1], (unsigned long long)__popc(ball));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (mine) {
-            list[base + __popc(ball & ((1u << lane) - 1u))] = g;
-            owner[g] = INT32_MAX;
-        }
-    }
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride)  // warp-uniform
+        compact_one(i0 + threadIdx.x, n, edited, tunit, owner, list, counters);
 }
+
 
 }  // namespace
 
@@ -693,7 +850,9 @@ int max_block_contributors() { return STAGE_CODES; }
 
 namespace {
 
-FoldArgs fold_args(const Ctx *c) { return FoldArgs{c->bmeta, c->ccode, c->Ke, c->val, c->eps}; }
+FoldArgs fold_args(const Ctx *c) {
+    return FoldArgs{c->bmeta, c->bmirror, c->ccode, c->Ke, c->val, c->eps};
+}
 
 }  // namespace
 
@@ -748,23 +907,35 @@ int init_fold_attributes() {
 
 int launch_fold_list(Ctx *c, const int32_t *list, const unsigned long long *count,
                      int64_t max_items, cudaStream_t s) {
-    const int threads = LIST_WARPS * 32;
-    const size_t smem = LIST_WARP_SMEM * LIST_WARPS;
-    // ~one listed block per lane of the grid, at most the resident CTAs
-    const int grid = persistent_grid(c, (const void *)k_fold_list, threads, max_items, smem);
-    k_fold_list<<<grid, threads, smem, s>>>(fold_args(c), list, count);
+    const int threads = ENT_WARPS * 32;
+    // one unit per 9 lanes (3 per warp) for the largest possible list, at most the resident CTAs
+    const int grid = persistent_grid(c, (const void *)k_fold_entries<1>, threads,
+                                     (max_items + ENT_UNITS - 1) / ENT_UNITS * 32);
+    k_fold_entries<1><<<grid, threads, 0, s>>>(fold_args(c), list, count, 0);
     STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;
 }
 
+#ifndef STA_REBUILD_ENTRIES
+#define STA_REBUILD_ENTRIES 0
+#endif
+
 int launch_rebuild(Ctx *c, cudaStream_t s) {
-    if (c->nblocks == 0) return STA_OK;
-    return launch_fold<0>(c, nullptr, nullptr, c->nblocks, c->nblocks, s);
+    if (c->nunits == 0) return STA_OK;
+    if (STA_REBUILD_ENTRIES) {
+        const int threads = ENT_WARPS * 32;
+        const int grid = persistent_grid(c, (const void *)k_fold_entries<0>, threads,
+                                         (c->nunits + ENT_UNITS - 1) / ENT_UNITS * 32);
+        k_fold_entries<0><<<grid, threads, 0, s>>>(fold_args(c), nullptr, nullptr, c->nunits);
+        STA_CUDA_TRY(cudaGetLastError());
+        return STA_OK;
+    }
+    return launch_fold<0>(c, nullptr, nullptr, c->nunits, c->nunits, s);
 }
 
 int launch_mask_bits(Ctx *c, cudaStream_t s) {
     if (c->T == 0) return STA_OK;
-    const int64_t n = 16 * c->T;
+    const int64_t n = 10 * c->T;
     int64_t grid = (n + 255) / 256;
     const int64_t cap = (int64_t)c->num_sms * 8;
     if (grid > cap) grid = cap;
@@ -775,17 +946,17 @@ int launch_mask_bits(Ctx *c, cudaStream_t s) {
 
 int launch_stream(Ctx *c, int64_t m, cudaStream_t s) {
     if (m == 0) {
-        STA_CUDA_TRY(cudaMemsetAsync(c->counters + 1, 0, sizeof(unsigned long long), s));
+        STA_CUDA_TRY(cudaMemsetAsync(c->counters + 1, 0, 3 * sizeof(unsigned long long), s));
         return STA_OK;
     }
     const int threads = 256;
-    const int64_t g2 = (16 * m + threads - 1) / threads;
-    k_stream_apply<<<(unsigned)g2, threads, 0, s>>>(c->d_edited, m, c->tblk, c->cslot, c->ccode,
+    const int64_t g2 = (10 * m + threads - 1) / threads;
+    k_stream_apply<<<(unsigned)g2, threads, 0, s>>>(c->d_edited, m, c->tunit, c->cslot, c->ccode,
                                                     c->mask, c->owner, c->counters);
-    k_stream_compact<<<(unsigned)g2, threads, 0, s>>>(c->d_edited, m, c->tblk, c->owner,
+    k_stream_compact<<<(unsigned)g2, threads, 0, s>>>(c->d_edited, m, c->tunit, c->owner,
                                                       c->touched, c->counters);
     // the touched count is only known on the device: size the grid for the upper bound
-    return launch_fold_list(c, c->touched, c->counters + 1, 16 * m, s);
+    return launch_fold_list(c, c->touched, c->counters + 1, 10 * m, s);
 }
 
 // Streaming update for graph capture: edited list and its length in device memory, fixed grids
@@ -793,15 +964,15 @@ int launch_stream(Ctx *c, int64_t m, cudaStream_t s) {
 int launch_stream_devcount(Ctx *c, const int32_t *d_edited, const int64_t *d_m, int64_t cap,
                            cudaStream_t s) {
     const int threads = 256;
-    int64_t g1 = (16 * cap + threads - 1) / threads, g2 = (16 * cap + threads - 1) / threads;
+    int64_t g1 = (10 * cap + threads - 1) / threads, g2 = (10 * cap + threads - 1) / threads;
     const int64_t c1 = (int64_t)c->num_sms * 16, c2 = (int64_t)c->num_sms * 16;
     g1 = g1 < 1 ? 1 : (g1 > c1 ? c1 : g1);
     g2 = g2 < 1 ? 1 : (g2 > c2 ? c2 : g2);
-    k_stream_apply_dc<<<(unsigned)g1, threads, 0, s>>>(d_edited, d_m, c->tblk, c->cslot, c->ccode,
+    k_stream_apply_dc<<<(unsigned)g1, threads, 0, s>>>(d_edited, d_m, c->tunit, c->cslot, c->ccode,
                                                        c->mask, c->owner, c->counters);
-    k_stream_compact_dc<<<(unsigned)g2, threads, 0, s>>>(d_edited, d_m, c->tblk, c->owner,
+    k_stream_compact_dc<<<(unsigned)g2, threads, 0, s>>>(d_edited, d_m, c->tunit, c->owner,
                                                          c->touched, c->counters);
-    return launch_fold_list(c, c->touched, c->counters + 1, 16 * (cap > 0 ? cap : 1), s);
+    return launch_fold_list(c, c->touched, c->counters + 1, 10 * (cap > 0 ? cap : 1), s);
 }
 
 // Streaming update with caller-chosen scratch: the same three kernels as launch_stream, with
@@ -811,17 +982,20 @@ int launch_stream_devcount(Ctx *c, const int32_t *d_edited, const int64_t *d_m, 
 int launch_stream_scratch(Ctx *c, int64_t m, const int32_t *d_edited, int32_t *touched,
                           unsigned long long *counters, cudaStream_t s) {
     if (m == 0) {
-        STA_CUDA_TRY(cudaMemsetAsync(c->counters + 1, 0, sizeof(unsigned long long), s));
+        STA_CUDA_TRY(cudaMemsetAsync(c->counters + 1, 0, 3 * sizeof(unsigned long long), s));
         return STA_OK;
     }
     const int threads = 256;
-    const int64_t g2 = (16 * m + threads - 1) / threads;
-    k_stream_apply<<<(unsigned)g2, threads, 0, s>>>(d_edited, m, c->tblk, c->cslot, c->ccode,
+    const int64_t g2 = (10 * m + threads - 1) / threads;
+    k_stream_apply<<<(unsigned)g2, threads, 0, s>>>(d_edited, m, c->tunit, c->cslot, c->ccode,
                                                     c->mask, c->owner, counters);
-    k_stream_compact<<<(unsigned)g2, threads, 0, s>>>(d_edited, m, c->tblk, c->owner, touched,
+    k_stream_compact<<<(unsigned)g2, threads, 0, s>>>(d_edited, m, c->tunit, c->owner, touched,
                                                       counters);
-    STA_TRY(launch_fold_list(c, touched, counters + 1, 16 * m, s));
+    STA_TRY(launch_fold_list(c, touched, counters + 1, 10 * m, s));
+    // touched units and touched entries, for sta_last_touched
     STA_CUDA_TRY(cudaMemcpyAsync(c->counters + 1, counters + 1, sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToDevice, s));
+    STA_CUDA_TRY(cudaMemcpyAsync(c->counters + 3, counters + 3, sizeof(unsigned long long),
                                  cudaMemcpyDeviceToDevice, s));
     return STA_OK;
 }

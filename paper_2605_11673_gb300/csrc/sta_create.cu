@@ -8,7 +8,8 @@
 //   scalar CSR                                        row_ptr / col
 //   tet -> block of each local node pair              tblk   (T x 16)
 //   tet -> CSR index of each local entry              scat   (T x 144)
-//   block -> contributors in ascending tet id         cptr / ccode
+//   fold units (node pairs a <= b) with their contributors in ascending tet id, and each
+//   tetrahedron's 10 unit slots                      bmeta / bmirror / ccode / cslot / tunit
 // Lists filled with atomics are sorted afterwards, so every array is deterministic.
 #include <climits>
 
@@ -234,44 +235,103 @@ __global__ void k_tet_maps(const int4 *tets, int64_t T, const int32_t *adj_ptr,
     }
 }
 
-// ---------------------------------------------------------------- contributor lists
+// ---------------------------------------------------------------- fold units
+// A unit is an unordered node pair {a <= b} of the pattern: the block (a, b) of an "upper"
+// block g (adj[g] >= block_node[g]); the lower block (b, a) is its mirror.
 
-__global__ void k_contrib_count(const int32_t *tblk, int64_t T, int32_t *cnt) {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < 16 * T;
-         k += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&cnt[tblk[k]], 1);
-}
-
-__global__ void k_contrib_fill(const int32_t *tblk, int64_t T, const int64_t *cptr64,
-                               int32_t *fill, int32_t *ccode) {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < 16 * T;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        int32_t g = tblk[k];
-        int32_t slot = atomicAdd(&fill[g], 1);
-        int32_t t = (int32_t)(k >> 4), la = (int32_t)((k >> 2) & 3), lb = (int32_t)(k & 3);
-        ccode[cptr64[g] + slot] = contrib_code(t, la, lb);
-    }
-}
-
-// cslot[16 t + 4 la + lb] = position of the contribution (t, la, lb) in its block's list
-__global__ void k_contrib_slots(const int32_t *ccode, int64_t T, int32_t *cslot) {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < 16 * T;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        int32_t code = ccode[k];
-        cslot[16 * (int64_t)code_tet(code) + ((code >> 2) & 3) * 4 + (code & 3)] = (int32_t)k;
-    }
-}
-
-// Per-block record used by the folds: first value index, row stride and diagonal flag,
-// contributor range.
-__global__ void k_block_meta(int64_t nblocks, const int32_t *block_node, const int32_t *adj_ptr,
-                             const int32_t *adj, const int64_t *cptr64, int4 *bmeta) {
+__global__ void k_block_off(int64_t nblocks, const int32_t *block_node, const int32_t *adj_ptr,
+                            int2 *boff, int32_t *upper) {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nblocks;
          g += (int64_t)gridDim.x * blockDim.x) {
-        int32_t a = block_node[g], s = adj_ptr[a], d = adj_ptr[a + 1] - s;
-        int32_t off = 9 * s + 3 * ((int32_t)g - s);
-        bmeta[g] = make_int4(off, (3 * d) << 1 | (adj[g] == a ? 1 : 0), (int32_t)cptr64[g],
-                             (int32_t)cptr64[g + 1]);
+        const int32_t a = block_node[g], s = adj_ptr[a], d = adj_ptr[a + 1] - s;
+        boff[g] = make_int2(9 * s + 3 * ((int32_t)g - s), 3 * d);
+        upper[g] = 0;  // set by k_upper_flags
+    }
+}
+
+__global__ void k_upper_flags(int64_t nblocks, const int32_t *block_node, const int32_t *adj,
+                              int32_t *upper) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nblocks;
+         g += (int64_t)gridDim.x * blockDim.x)
+        upper[g] = adj[g] >= block_node[g] ? 1 : 0;
+}
+
+__device__ __forceinline__ int32_t find_block(const int32_t *adj_ptr, const int32_t *adj,
+                                              int32_t a, int32_t b) {
+    int32_t lo = adj_ptr[a], hi = adj_ptr[a + 1];  // first position with adj >= b
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (adj[mid] < b) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// unit of every block (upper: its own prefix index; lower: its mirror's)
+__global__ void k_unit_of_block(int64_t nblocks, const int32_t *block_node, const int32_t *adj,
+                                const int32_t *adj_ptr, const int64_t *uid, int32_t *ublk) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nblocks;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = block_node[g], b = adj[g];
+        const int64_t gu = b >= a ? g : find_block(adj_ptr, adj, b, a);
+        ublk[g] = (int32_t)uid[gu];
+    }
+}
+
+// tunit[10 t + s] = unit of slot s of tetrahedron t; counts per unit
+__global__ void k_unit_count(const int32_t *tblk, const int32_t *ublk, int64_t T, int32_t *tunit,
+                             int32_t *cnt) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < 10 * T;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = k / 10;
+        const int s = (int)(k % 10);
+        const int32_t u = ublk[tblk[16 * t + 4 * slot_la(s) + slot_lb(s)]];
+        tunit[k] = u;
+        atomicAdd(&cnt[u], 1);
+    }
+}
+
+// codes in each unit's list: (t, la, lb) with la the local index of the unit's lower node
+__global__ void k_unit_fill(const int4 *tets, const int32_t *tunit, int64_t T, const int64_t *uptr,
+                            int32_t *fill, int32_t *ccode) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < 10 * T;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = k / 10;
+        const int s = (int)(k % 10);
+        const int4 q = tets[t];
+        const int v[4] = {q.x, q.y, q.z, q.w};
+        int la = slot_la(s), lb = slot_lb(s);
+        if (v[la] > v[lb]) {
+            const int x = la;
+            la = lb;
+            lb = x;
+        }
+        const int32_t u = tunit[k];
+        const int32_t slot = atomicAdd(&fill[u], 1);
+        ccode[uptr[u] + slot] = contrib_code((int32_t)t, la, lb);
+    }
+}
+
+// cslot[10 t + s] = position of tetrahedron t's slot-s contribution in its unit's list
+__global__ void k_unit_slots(const int32_t *ccode, int64_t T, int32_t *cslot) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < 10 * T;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t code = ccode[k];
+        cslot[10 * (int64_t)code_tet(code) + slot_of((code >> 2) & 3, code & 3)] = (int32_t)k;
+    }
+}
+
+// unit records: value offset and row stride of (a, b) and of its mirror (b, a), contributors
+__global__ void k_unit_meta(int64_t nblocks, const int32_t *block_node, const int32_t *adj,
+                            const int32_t *adj_ptr, const int2 *boff, const int64_t *uid,
+                            const int32_t *upper, const int64_t *uptr, int4 *umeta, int2 *umirror) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nblocks;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        if (!upper[g]) continue;
+        const int32_t a = block_node[g], b = adj[g];
+        const int64_t u = uid[g];
+        const int2 o = boff[g], m = boff[find_block(adj_ptr, adj, b, a)];
+        umeta[u] = make_int4(o.x, o.y << 1 | (a == b ? 1 : 0), (int32_t)uptr[u], (int32_t)uptr[u + 1]);
+        umirror[u] = m;
     }
 }
 
@@ -358,12 +418,7 @@ int build_pattern(Ctx *c, cudaStream_t s) {
     STA_TRY(dev_alloc(c, &c->col, c->nnz));
     STA_TRY(dev_alloc(c, &c->tblk, 16 * T));
     STA_TRY(dev_alloc(c, &c->scat, 144 * T));
-    STA_TRY(dev_alloc(c, &c->cptr, nblocks + 1));
-    STA_TRY(dev_alloc(c, &c->ccode, 16 * T));
-    STA_TRY(dev_alloc(c, &c->cslot, 16 * T));
-    STA_TRY(dev_alloc(c, &c->bmeta, nblocks));
-    STA_TRY(dev_alloc(c, &c->owner, nblocks));
-    STA_TRY(dev_alloc(c, &c->touched, nblocks));
+    STA_TRY(dev_alloc(c, &c->boff, nblocks));
 
     STA_TRY(dev_alloc(c, &c->nt_ptr, n + 1));
     STA_TRY(dev_alloc(c, &c->nt_list, 4 * T));
@@ -376,13 +431,35 @@ int build_pattern(Ctx *c, cudaStream_t s) {
     k_col<<<grid_for(nblocks), TPB, 0, s>>>(nblocks, c->block_node, c->adj_ptr, c->adj, c->col);
     k_tet_maps<<<grid_for(T), TPB, 0, s>>>(c->tets, T, c->adj_ptr, c->adj, c->tblk, c->scat);
 
-    // contributor lists, ascending tetrahedron id (codes carry the id in their high bits)
-    int64_t *cptr64 = nullptr;
-    STA_TRY(sc.get(&cptr64, nblocks + 1));
-    STA_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nblocks, s));
-    k_contrib_count<<<grid_for(16 * T), TPB, 0, s>>>(c->tblk, T, cnt);
+    // fold units and their contributor lists, ascending tetrahedron id (the codes carry the id
+    // in their high bits)
+    int32_t *upper = nullptr, *ublk = nullptr;
+    int64_t *uid = nullptr;
+    STA_TRY(sc.get(&upper, nblocks));
+    STA_TRY(sc.get(&ublk, nblocks));
+    STA_TRY(sc.get(&uid, nblocks + 1));
+    k_block_off<<<grid_for(nblocks), TPB, 0, s>>>(nblocks, c->block_node, c->adj_ptr, c->boff, upper);
+    k_upper_flags<<<grid_for(nblocks), TPB, 0, s>>>(nblocks, c->block_node, c->adj, upper);
+    STA_TRY(exclusive_scan(c, upper, nblocks, uid, tiles, s));
+    int64_t nunits = 0;
+    STA_CUDA_TRY(cudaMemcpyAsync(&nunits, uid + nblocks, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    STA_CUDA_TRY(cudaStreamSynchronize(s));
+    c->nunits = nunits;
+    STA_TRY(dev_alloc(c, &c->bmeta, nunits));
+    STA_TRY(dev_alloc(c, &c->bmirror, nunits));
+    STA_TRY(dev_alloc(c, &c->ccode, 10 * T));
+    STA_TRY(dev_alloc(c, &c->cslot, 10 * T));
+    STA_TRY(dev_alloc(c, &c->tunit, 10 * T));
+    STA_TRY(dev_alloc(c, &c->owner, nunits));
+    STA_TRY(dev_alloc(c, &c->touched, nunits));
+    k_unit_of_block<<<grid_for(nblocks), TPB, 0, s>>>(nblocks, c->block_node, c->adj, c->adj_ptr,
+                                                      uid, ublk);
+    int64_t *uptr = nullptr;
+    STA_TRY(sc.get(&uptr, nunits + 1));
+    STA_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nunits > 0 ? nunits : 1), s));
+    k_unit_count<<<grid_for(10 * T), TPB, 0, s>>>(c->tblk, ublk, T, c->tunit, cnt);
     STA_CUDA_TRY(cudaMemsetAsync(tiles, 0, sizeof(int64_t), s));
-    k_max_i32<<<grid_for(nblocks > 0 ? nblocks : 1), TPB, 0, s>>>(cnt, nblocks, tiles);
+    k_max_i32<<<grid_for(nunits > 0 ? nunits : 1), TPB, 0, s>>>(cnt, nunits, tiles);
     int64_t max_contrib = 0;
     STA_CUDA_TRY(cudaMemcpyAsync(&max_contrib, tiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     STA_CUDA_TRY(cudaStreamSynchronize(s));
@@ -390,15 +467,14 @@ int build_pattern(Ctx *c, cudaStream_t s) {
         return fail(STA_ERANGE, "a node pair is shared by " + std::to_string(max_contrib) +
                                     " tetrahedra; the fold supports at most " +
                                     std::to_string(max_block_contributors()));
-    STA_TRY(exclusive_scan(c, cnt, nblocks, cptr64, tiles, s));
-    STA_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nblocks, s));
-    k_contrib_fill<<<grid_for(16 * T), TPB, 0, s>>>(c->tblk, T, cptr64, cnt, c->ccode);
-    k_sort_segments<<<grid_for(nblocks), TPB, 0, s>>>(cptr64, nblocks, c->ccode);
-    k_to_i32<<<grid_for(nblocks + 1), TPB, 0, s>>>(cptr64, nblocks + 1, c->cptr);
-    k_contrib_slots<<<grid_for(16 * T), TPB, 0, s>>>(c->ccode, T, c->cslot);
-    k_block_meta<<<grid_for(nblocks), TPB, 0, s>>>(nblocks, c->block_node, c->adj_ptr, c->adj,
-                                                   cptr64, c->bmeta);
-    k_fill_i32<<<grid_for(nblocks), TPB, 0, s>>>(c->owner, nblocks, INT32_MAX);
+    STA_TRY(exclusive_scan(c, cnt, nunits, uptr, tiles, s));
+    STA_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nunits > 0 ? nunits : 1), s));
+    k_unit_fill<<<grid_for(10 * T), TPB, 0, s>>>(c->tets, c->tunit, T, uptr, cnt, c->ccode);
+    k_sort_segments<<<grid_for(nunits), TPB, 0, s>>>(uptr, nunits, c->ccode);
+    k_unit_slots<<<grid_for(10 * T), TPB, 0, s>>>(c->ccode, T, c->cslot);
+    k_unit_meta<<<grid_for(nblocks), TPB, 0, s>>>(nblocks, c->block_node, c->adj, c->adj_ptr,
+                                                  c->boff, uid, upper, uptr, c->bmeta, c->bmirror);
+    k_fill_i32<<<grid_for(nunits), TPB, 0, s>>>(c->owner, nunits, INT32_MAX);
     STA_CUDA_TRY(cudaGetLastError());
     STA_CUDA_TRY(cudaStreamSynchronize(s));
     return STA_OK;

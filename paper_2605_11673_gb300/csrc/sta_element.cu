@@ -150,7 +150,7 @@ k_elements(const double4_32a *__restrict__ X, const int4 *__restrict__ tets,
 __global__ void __launch_bounds__(128)
 k_adjoint(const double4_32a *__restrict__ X, const int4 *__restrict__ tets,
           const double2 *__restrict__ mat, const uint8_t *__restrict__ mask,
-          const int32_t *__restrict__ tblk, const int4 *__restrict__ bmeta,
+          const int32_t *__restrict__ tblk, const int2 *__restrict__ boff,
           const double *__restrict__ gval, int64_t T, double *__restrict__ dE,
           double *__restrict__ dnu, double *__restrict__ dXe) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
@@ -186,9 +186,9 @@ k_adjoint(const double4_32a *__restrict__ X, const int4 *__restrict__ tets,
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const int4 bm = bmeta[tblk[16 * t + 4 * a + b]];
-                const double *G = gval + bm.x;
-                const int rs = bm.y >> 1;
+                const int2 bo = boff[tblk[16 * t + 4 * a + b]];
+                const double *G = gval + bo.x;
+                const int rs = bo.y;
                 double M[3][3];
 #pragma unroll
                 for (int i = 0; i < 3; ++i)
@@ -320,7 +320,7 @@ int launch_adjoint(Ctx *c, const double *gval, double *dE, double *dnu, double *
         int64_t grid = (c->T + 127) / 128;
         const int64_t cap = (int64_t)c->num_sms * 16;
         if (grid > cap) grid = cap;
-        k_adjoint<<<(unsigned)grid, 128, 0, s>>>(c->X, c->tets, c->mat, c->mask, c->tblk, c->bmeta,
+        k_adjoint<<<(unsigned)grid, 128, 0, s>>>(c->X, c->tets, c->mat, c->mask, c->tblk, c->boff,
                                                 gval, c->T, dE, dnu, c->dXe);
     }
     if (c->n > 0) {

@@ -52,14 +52,26 @@ __host__ __device__ inline int ke_tri(int i, int j) {
     return i == 0 ? j : (i == 1 ? 2 + j : 5);
 }
 
-// Contributor code of a node-pair block: tetrahedron id and the local indices of the
-// block's row node (la) and column node (lb) inside that tetrahedron; bit 31 holds the
-// tetrahedron's current activity (kept equal to the mask by every call that changes it).
+// Contributor code of a fold unit (node pair a <= b): tetrahedron id and the local indices of
+// the unit's nodes a (la) and b (lb) inside that tetrahedron; bit 31 holds the tetrahedron's
+// current activity (kept equal to the mask by every call that changes it).
 constexpr uint32_t CODE_ACTIVE = 0x80000000u;
 __host__ __device__ inline int32_t contrib_code(int32_t t, int la, int lb) {
     return (t << 4) | (la << 2) | lb;
 }
 __host__ __device__ inline int32_t code_tet(int32_t code) { return (code >> 4) & 0x07ffffff; }
+
+// The 10 unit slots of a tetrahedron: 0..3 diagonal (la, la), 4..9 the pairs (0,1) (0,2) (0,3)
+// (1,2) (1,3) (2,3).
+__host__ __device__ inline int slot_la(int s) { return s < 4 ? s : (s < 7 ? 0 : (s < 9 ? 1 : 2)); }
+__host__ __device__ inline int slot_lb(int s) {
+    return s < 4 ? s : (s == 4 ? 1 : (s == 5 ? 2 : (s == 6 ? 3 : (s == 7 ? 2 : 3))));
+}
+__host__ __device__ inline int slot_of(int la, int lb) {  // unordered local pair -> slot
+    if (la == lb) return la;
+    const int lo = la < lb ? la : lb, hi = la < lb ? lb : la;
+    return 4 + (lo == 0 ? hi - 1 : (lo == 1 ? hi + 1 : 5));
+}
 
 // ------------------------------------------------------------------------------------
 // Context
@@ -85,10 +97,16 @@ struct Ctx {
     int32_t *col = nullptr;        // nnz
     int32_t *tblk = nullptr;       // T x 16: block of local pair (la, lb) = 4 la + lb
     int32_t *scat = nullptr;       // T x 144: CSR index of local entry (p, q)
-    int32_t *cptr = nullptr;       // nblocks + 1: contributor list of each block
-    int32_t *ccode = nullptr;      // 16 T: contributor codes, ascending tetrahedron id
-    int32_t *cslot = nullptr;      // T x 16: position in ccode of tet t's pair (la, lb)
-    int4 *bmeta = nullptr;         // nblocks: {value offset, 3 deg << 1 | diagonal, c0, c1}
+    int2 *boff = nullptr;          // nblocks: {first value index, row stride}
+    // Fold units: unordered node pairs {a <= b}.  Entry (3a+i, 3b+j) and its mirror
+    // (3b+j, 3a+i) fold the same operands in the same order (the element matrices are exactly
+    // symmetric), so one fold per unit writes both blocks.
+    int64_t nunits = 0;
+    int4 *bmeta = nullptr;         // nunits: {value offset of (a,b), rs_a << 1 | diagonal, c0, c1}
+    int2 *bmirror = nullptr;       // nunits: {value offset of (b,a), rs_b}
+    int32_t *ccode = nullptr;      // 10 T: unit contributor codes, ascending tetrahedron id
+    int32_t *cslot = nullptr;      // T x 10: position in ccode of tet t's unit slot
+    int32_t *tunit = nullptr;      // T x 10: unit of tet t's slot (4 diagonal, 6 pairs)
     int32_t *nt_ptr = nullptr;     // n + 1: node -> incident tetrahedra
     int32_t *nt_list = nullptr;    // 4 T: incident tetrahedra, ascending id
     double *dXe = nullptr;         // T x 12: per-element position gradients (adjoint, lazily)
@@ -97,9 +115,10 @@ struct Ctx {
     double *Ke = nullptr;       // T x 78 element cache
     uint8_t *mask = nullptr;    // T
     double *val = nullptr;      // nnz
-    int32_t *owner = nullptr;   // nblocks: streaming dedupe slot, INT32_MAX when free
-    int32_t *touched = nullptr; // nblocks: list of blocks touched by the current frame
-    unsigned long long *counters = nullptr;  // [0] bad elements, [1] touched blocks
+    int32_t *owner = nullptr;   // nunits: streaming dedupe slot, INT32_MAX when free
+    int32_t *touched = nullptr; // nunits: list of units touched by the current frame
+    // [0] bad elements, [1] touched units, [2] first bad element, [3] touched CSR entries
+    unsigned long long *counters = nullptr;
 
     // streaming staging
     int32_t *d_edited = nullptr;  // capacity: edited tetrahedra (id | new state << 31)

@@ -15,7 +15,8 @@ namespace {
 
 constexpr int64_t kMaxEdited = STA_NOALLOC_MAX_EDITED;
 constexpr int64_t kMaxTouched = 16 * kMaxEdited;  // an edited tetrahedron touches 16 blocks
-// layout: counters (4 x u64) | edited tets (kMaxEdited x i32) | touched blocks (16 x that)
+// layout: counters (4 x u64) | edited tets (kMaxEdited x i32) | touched units (16 x that; an
+// edited tetrahedron touches 10)
 constexpr size_t kCountersBytes = 4 * sizeof(unsigned long long);
 constexpr size_t kScratchBytes =
     kCountersBytes + sizeof(int32_t) * (size_t)kMaxEdited + sizeof(int32_t) * (size_t)kMaxTouched;
