@@ -63,8 +63,8 @@ typedef struct {
 
 typedef struct {
     double eps;             /* eps of Eq. 4 / Eq. 8, added to diagonal entries; default 0 */
-    int32_t block_threads;  /* threads per CTA of the fold kernels: 64, 128 or 256; 0 = 128 */
-    int32_t blocks_per_sm;  /* CTAs per SM of the persistent fold grid; 0 = occupancy max */
+    int32_t block_threads;  /* threads per CTA of the rebuild fold: 64, 128 or 256; 0 = 128 */
+    int32_t blocks_per_sm;  /* CTAs per SM of the persistent rebuild grid; 0 = occupancy max */
 } sta_options;
 
 /* Fills defaults (eps 0, launch shape from the built-in table). */
@@ -84,7 +84,8 @@ void sta_default_options(sta_options *opt);
  * active set is empty and all values are +0.0; call sta_full_rebuild with the initial mask
  * (Algorithm 1 "a_0").  Synchronises `stream`.  Errors: STA_EINVAL for a bad id, a repeated
  * node or a tetrahedron with det <= 0 (its index is in sta_last_error()); STA_ERANGE when
- * nnz or 16 * n_tets exceeds int32; STA_ENOMEM; STA_ECUDA.
+ * nnz or 16 * n_tets exceeds int32 or n_tets >= 2^31 / 84 (25,565,281: 31-bit offsets into the
+ * element cache); STA_ENOMEM; STA_ECUDA.
  */
 int sta_create(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
                const double *young, const double *poisson, const sta_options *opt,
@@ -110,8 +111,9 @@ int sta_full_rebuild(sta_ctx *ctx, const uint8_t *mask, int mask_on_device, void
  */
 int sta_refold(sta_ctx *ctx, void *stream);
 
-/* Change the fold launch shape (same meaning as the sta_options fields; results do not
- * depend on it).  Not allowed while graph mode is on (STA_ESTATE). */
+/* Change the rebuild fold's launch shape (same meaning as the sta_options fields; results do
+ * not depend on it; the streaming fold always runs at occupancy maximum).  Not allowed while
+ * graph mode is on (STA_ESTATE). */
 int sta_set_launch(sta_ctx *ctx, int32_t block_threads, int32_t blocks_per_sm);
 
 /*

@@ -83,6 +83,8 @@ int sta::create_impl(const double *nodes, int64_t n_nodes, const int32_t *tets, 
     if ((n_nodes > 0 && !nodes) || (n_tets > 0 && (!tets || !young || !poisson)))
         return fail(STA_EINVAL, "NULL input array");
     if (n_tets >= (1LL << 27)) return fail(STA_ERANGE, "n_tets must be < 2^27");
+    if (n_tets * KE_STRIDE >= (1LL << 31))  // element cache offsets of the folds are 31-bit
+        return fail(STA_ERANGE, "n_tets must be < 2^31 / " + std::to_string(KE_STRIDE));
     if (3 * n_nodes + 1 > INT32_MAX) return fail(STA_ERANGE, "3 * n_nodes + 1 exceeds int32");
     for (int64_t t = 0; t < n_tets; ++t) {
         const int32_t *q = tets + 4 * t;
@@ -119,7 +121,6 @@ int sta::create_impl(const double *nodes, int64_t n_nodes, const int32_t *tets, 
         return bail(fail(STA_ECUDA, "no CUDA device"));
     if (cudaEventCreateWithFlags(&x->h2d_done, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(STA_ECUDA, "cudaEventCreate failed"));
-    if ((rc = init_fold_attributes())) return bail(rc);
 
     // inputs: nodes padded to double4_32a, tets as int4, materials as double2
     std::vector<double> X4(4 * (size_t)(n_nodes > 0 ? n_nodes : 1), 0.0);

@@ -3,24 +3,20 @@
 // Both evaluate, for a node-pair block (a, b) of the superset pattern, the 9 CSR values
 //   A[3a+i][3b+j] = fold_{tau active, ascending id} K^(tau)[3 la + i][3 lb + j]   (+ eps)
 // i.e. Eq. 8 of STA-FEM restricted to one block, with the fold starting at +0.0 and eps
-// added afterwards on the diagonal.  The streaming pass (Sec. 3.2, Algorithm 1; the
-// local_recompute policy of Sec. 3.5) calls the same device function on the blocks touched
-// by the frame's edits only, so its values are bit-identical to the rebuild's.
+// added afterwards on the diagonal.  The work unit is an unordered node pair {a <= b}: the
+// element matrices are stored exactly symmetric, so block (b, a) folds the same operands in
+// the same order as (a, b) and one fold writes both.  The streaming pass (Sec. 3.2,
+// Algorithm 1; the local_recompute policy of Sec. 3.5) folds the units touched by the frame's
+// edits only, with the same operands, order and operations, so its values are bit-identical
+// to the rebuild's.
 //
-// No atomics touch values: each block is folded by exactly one thread, and the summation
-// order is the order of the contributor list (ascending tetrahedron id), independent of the
-// launch configuration.
+// No atomics touch values: each entry is folded by exactly one lane, and the summation order
+// is the order of the unit's contributor list (ascending tetrahedron id), independent of the
+// kernel and the launch configuration.  Every fold starts with (+0.0 + c1) formed without an
+// FP64 operation (plus_zero) and continues with one FP64 add per further contribution.
 #include <climits>
 
-#include "softfloat.cuh"
 #include "sta_internal.cuh"
-
-// Number of the 9 accumulators of a fold step whose additions run on the integer pipes
-// (int_add, bit-identical to the FP64 add); the rest use the FP64 pipe.  Build-time tuning;
-// measured slower on the fold (its loop is latency- rather than FP64-issue-bound), so 0.
-#ifndef STA_INT_ADDS
-#define STA_INT_ADDS 0
-#endif
 
 namespace sta {
 namespace {
@@ -118,351 +114,6 @@ __device__ __forceinline__ void write_block(const FoldArgs &A, const BlockOut &o
     }
 }
 
-// Lockstep fold.  On GB300 a warp-wide FP64 instruction costs the same however many lanes
-// are active, and FP64 issue is the scarcest resource, so every FP64 add instruction should
-// carry 32 useful lanes.  Each warp works in two phases over its share of the blocks:
-//
-//  stage: blocks are taken in order; the active contributor codes of each block are
-//         compacted, in list order, into the warp's shared buffer.  Blocks with no active
-//         contributor are written (+0.0) and blocks with one are written (+0.0 + c) right
-//         away, with no FP64 operation.  Integer and load work only.
-//  fold:  lanes claim staged blocks in order as they become free.  A claim loads the
-//         operands of the block's first contribution into v and of its second into the
-//         accumulators; the next iteration forms (+0.0 + c1) + c2, and every later iteration
-//         adds one more contribution while the loads of the following one are in flight.
-//         Every iteration of a busy lane is one useful 9-wide FP64 add.
-//
-// Items are handed out in chunks of 32: warp w owns chunks w, w + W, w + 2W, ... (W warps in
-// the grid).  MODE 0: item = block id (whole pattern) -- a chunk is 32 consecutive blocks
-// whose codes are contiguous, staged with coalesced windows and ballots; MODE 1: item
-// indexes a list of block ids whose length is read from device memory (streaming), staged
-// one block per lane.
-constexpr int FOLD_WARPS = 4;       // default warps per CTA (2, 4 or 8 selectable)
-constexpr int STAGE_BLOCKS = 192;   // staged blocks per warp
-constexpr int STAGE_CODES = 1280;   // staged active codes per warp (>= contributors of any block)
-constexpr int STAGE_WIN = 8;        // 32-code windows of one staging round held in registers
-constexpr int LONG_BLOCK = 8;       // staged blocks with this many contributors are claimed first
-constexpr size_t FOLD_WARP_SMEM = sizeof(int4) * STAGE_BLOCKS + sizeof(int2) * STAGE_BLOCKS +
-                                  sizeof(int32_t) * STAGE_CODES;
-
-__device__ __forceinline__ int warp_inclusive_scan(int x, int lane) {
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    return x;
-}
-
-// bits of positions [0, n) of a 32-bit window (n clamped to [0, 32])
-__device__ __forceinline__ unsigned below(int n) {
-    return n <= 0 ? 0u : (n >= 32 ? 0xffffffffu : ((1u << n) - 1u));
-}
-
-// A block with at most one active contributor: written directly (+0.0, or +0.0 + c).
-__device__ __forceinline__ void write_small_block(const FoldArgs &A, const int4 bm, int2 mir,
-                                                  int cnt, int32_t code) {
-    double acc[9];
-    if (cnt == 0) {
-#pragma unroll
-        for (int q = 0; q < 9; ++q) acc[q] = 0.0;
-    } else {
-        load_contrib(A, code, acc);
-#pragma unroll
-        for (int q = 0; q < 9; ++q) acc[q] = plus_zero(acc[q]);
-    }
-    write_block(A, unit_out(A, bm, mir), acc);
-}
-
-template <int MODE, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32)
-k_fold(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *__restrict__ count,
-       int64_t nitems_static) {
-    // per warp: STAGE_BLOCKS int4 block records, then STAGE_CODES int32 codes (dynamic)
-    extern __shared__ int4 fold_smem[];
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int4 *sblk = fold_smem + (size_t)wid * (FOLD_WARP_SMEM / sizeof(int4));
-    int2 *smir = reinterpret_cast<int2 *>(sblk + STAGE_BLOCKS);
-    int32_t *scode = reinterpret_cast<int32_t *>(smir + STAGE_BLOCKS);
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t nitems = MODE == 0 ? nitems_static : (int64_t)*count;
-    const unsigned lt_mask = (1u << lane) - 1u;
-
-    int64_t p_base = 0;  // warp-uniform position in this warp's item sequence
-    bool more = true;
-    while (more) {
-        // ------------------------------------------------------------ stage
-        int nlong = 0, nshort = 0, nc = 0;
-        while (nlong + nshort + 32 <= STAGE_BLOCKS) {
-            if (MODE == 0) {
-                // the rest of the current chunk: consecutive blocks, contiguous codes
-                const int off = (int)(p_base & 31);
-                const int64_t chunk_first = ((p_base >> 5) * nwarps + warp) * 32;
-                const int64_t g = chunk_first + off + lane;
-                const bool valid = lane < 32 - off && g < nitems;
-                const unsigned validm = __ballot_sync(FULL, valid);
-                if (!validm) {
-                    more = false;
-                    break;
-                }
-                const int nv = __popc(validm);  // valid lanes form a prefix
-                int4 bm = make_int4(0, 0, 0, 0);
-                int2 mir = make_int2(0, 0);
-                if (valid) {
-                    bm = __ldg(A.bmeta + g);
-                    mir = __ldg(A.bmirror + g);
-                }
-                const int32_t r0 = __shfl_sync(FULL, bm.z, 0);
-                const int32_t r1 = __shfl_sync(FULL, bm.w, nv - 1);
-                const int nwin = (r1 - r0 + 31) >> 5;
-                // all windows' code loads issued before any is used
-                int32_t cw[STAGE_WIN];
-#pragma unroll
-                for (int w = 0; w < STAGE_WIN; ++w) {
-                    const int32_t c = r0 + 32 * w + lane;
-                    cw[w] = (w < nwin && c < r1) ? __ldg(A.ccode + c) : 0;
-                }
-                // pass 1: active codes before each block start (lo) and in the whole range
-                int lo = 0, total = 0;
-#pragma unroll
-                for (int w = 0; w < STAGE_WIN; ++w) {
-                    if (w < nwin) {
-                        const unsigned m = __ballot_sync(FULL, cw[w] < 0);
-                        lo += __popc(m & below(bm.z - (r0 + 32 * w)));
-                        total += __popc(m);
-                    }
-                }
-                for (int w = STAGE_WIN; w < nwin; ++w) {
-                    const int32_t c = r0 + 32 * w + lane;
-                    const unsigned m = __ballot_sync(FULL, c < r1 && __ldg(A.ccode + c) < 0);
-                    lo += __popc(m & below(bm.z - (r0 + 32 * w)));
-                    total += __popc(m);
-                }
-                int hi = __shfl_down_sync(FULL, lo, 1);
-                if (lane == nv - 1) hi = total;
-                const int cnt = valid ? hi - lo : 0;
-                // blocks that fit: lo + cnt within the free code space (a prefix of lanes)
-                const bool fits = valid && nc + hi <= STAGE_CODES;
-                const unsigned fitm = __ballot_sync(FULL, fits);
-                const int nfit = __popc(fitm);
-                if (nfit > 0) {
-                    // pass 2: compact the active codes of the fitting blocks, in list order
-                    const int32_t f1 = __shfl_sync(FULL, bm.w, nfit - 1);
-                    int run = nc;
-#pragma unroll
-                    for (int w = 0; w < STAGE_WIN; ++w) {
-                        if (w < nwin) {
-                            const int32_t c = r0 + 32 * w + lane;
-                            const bool act = c < f1 && cw[w] < 0;
-                            const unsigned m = __ballot_sync(FULL, act);
-                            if (act) scode[run + __popc(m & lt_mask)] = cw[w];
-                            run += __popc(m);
-                        }
-                    }
-                    for (int w = STAGE_WIN; w < nwin; ++w) {
-                        const int32_t c = r0 + 32 * w + lane;
-                        int32_t code = 0;
-                        const bool act = c < f1 && (code = __ldg(A.ccode + c)) < 0;
-                        const unsigned m = __ballot_sync(FULL, act);
-                        if (act) scode[run + __popc(m & lt_mask)] = code;
-                        run += __popc(m);
-                    }
-                    __syncwarp();
-                    // long blocks fill the staging list from the front, short ones from the
-                    // back: claims take long blocks first (longest-processing-time order)
-                    const unsigned longm = __ballot_sync(FULL, fits && cnt >= LONG_BLOCK);
-                    const unsigned shortm = __ballot_sync(FULL, fits && cnt >= 2 && cnt < LONG_BLOCK);
-                    if (fits) {
-                        if (cnt < 2) {
-                            write_small_block(A, bm, mir, cnt, cnt ? scode[nc + lo] : 0);
-                        } else {
-                            const int at = cnt >= LONG_BLOCK
-                                               ? nlong + __popc(longm & lt_mask)
-                                               : STAGE_BLOCKS - 1 - nshort - __popc(shortm & lt_mask);
-                            sblk[at] = make_int4(bm.x, bm.y, nc + lo, cnt);
-                            smir[at] = mir;
-                        }
-                    }
-                    nlong += __popc(longm);
-                    nshort += __popc(shortm);
-                    nc += __shfl_sync(FULL, hi, nfit - 1);
-                    p_base += nfit;
-                }
-                if (nfit < nv) break;  // code space full: fold, then continue this chunk
-            } else {
-                const int64_t p = p_base + lane;
-                const int64_t item = ((p >> 5) * nwarps + warp) * 32 + (p & 31);
-                const bool valid = item < nitems;
-                int4 bm = make_int4(0, 0, 0, 0);
-                int2 mir = make_int2(0, 0);
-                int cnt = 0;
-                if (valid) {
-                    const int32_t u = __ldg(list + item);
-                    bm = __ldg(A.bmeta + u);
-                    mir = __ldg(A.bmirror + u);
-                    for (int32_t c = bm.z; c < bm.w; ++c) cnt += __ldg(A.ccode + c) < 0;
-                }
-                const int inc = warp_inclusive_scan(cnt, lane);
-                const bool fits = valid && nc + inc <= STAGE_CODES;
-                const unsigned fitm = __ballot_sync(FULL, fits);
-                const unsigned longm = __ballot_sync(FULL, fits && cnt >= LONG_BLOCK);
-                const unsigned shortm = __ballot_sync(FULL, fits && cnt >= 2 && cnt < LONG_BLOCK);
-                if (fits) {
-                    const int at = nc + inc - cnt;
-                    int j = 0;
-                    for (int32_t c = bm.z; c < bm.w; ++c) {
-                        const int32_t code = __ldg(A.ccode + c);
-                        if (code < 0) scode[at + j++] = code;
-                    }
-                    if (cnt < 2) {
-                        write_small_block(A, bm, mir, cnt, cnt ? scode[at] : 0);
-                    } else {
-                        const int idx = cnt >= LONG_BLOCK
-                                            ? nlong + __popc(longm & lt_mask)
-                                            : STAGE_BLOCKS - 1 - nshort - __popc(shortm & lt_mask);
-                        sblk[idx] = make_int4(bm.x, bm.y, at, cnt);
-                        smir[idx] = mir;
-                    }
-                }
-                const int nfit = __popc(fitm);  // fitting lanes form a prefix
-                if (nfit > 0) nc += __shfl_sync(FULL, inc, nfit - 1);
-                nlong += __popc(longm);
-                nshort += __popc(shortm);
-                p_base += nfit;
-                if (nfit < 32) {
-                    more = __any_sync(FULL, valid);
-                    break;
-                }
-            }
-        }
-        __syncwarp();
-        // ------------------------------------------------------------ fold
-        int next_blk = 0;  // warp-uniform: staged blocks claimed so far
-        bool busy = false;
-        int k = 0, kend = 0;
-        BlockOut o{nullptr, nullptr, 0, 0, false};
-        // acc: accumulators; v: operands of the next contribution to add; w: of the one after
-        // (two contributions in flight per lane).  Right after a claim, acc holds the raw
-        // operands of contribution 2 and v those of contribution 1 (fresh).
-        double acc[9], v[9], w[9];
-        bool fresh = false, have_w = false;
-        // Claims come right after a block is written, so the operand loads of a newly
-        // claimed block are in flight for a whole iteration, like every other prefetch.
-        auto claim_blocks = [&]() {
-            const unsigned claim = __ballot_sync(FULL, !busy);
-            if (!busy) {
-                const int b = next_blk + __popc(claim & lt_mask);
-                if (b < nlong + nshort) {
-                    const int at = b < nlong ? b : STAGE_BLOCKS - 1 - (b - nlong);
-                    const int4 sb = sblk[at];
-                    o = unit_out(A, sb, smir[at]);
-                    k = sb.z;
-                    kend = sb.z + sb.w;
-                    load_contrib(A, scode[k], v);
-                    load_contrib(A, scode[k + 1], acc);
-                    k += 2;
-                    have_w = k < kend;
-                    if (have_w) load_contrib(A, scode[k++], w);
-                    busy = true;
-                    fresh = true;
-                }
-            }
-            next_blk += __popc(claim);
-        };
-        claim_blocks();
-        while (__any_sync(FULL, busy)) {
-            if (busy) {
-                if (fresh) {
-#pragma unroll
-                    for (int q = 0; q < 9; ++q) v[q] = plus_zero(v[q]);
-                    fresh = false;
-                }
-#pragma unroll
-                for (int q = 0; q < 6; ++q)
-                    acc[q] = q < STA_INT_ADDS ? int_add(acc[q], v[q]) : acc[q] + v[q];
-                if (!o.diag) {  // a diagonal unit folds 6 entries
-#pragma unroll
-                    for (int q = 6; q < 9; ++q)
-                        acc[q] = q < STA_INT_ADDS ? int_add(acc[q], v[q]) : acc[q] + v[q];
-                }
-                if (have_w) {
-#pragma unroll
-                    for (int q = 0; q < 9; ++q) v[q] = w[q];
-                    have_w = k < kend;
-                    if (have_w) load_contrib(A, scode[k++], w);
-                } else {
-                    write_block(A, o, acc);
-                    busy = false;
-                }
-            }
-            if (__any_sync(FULL, !busy)) claim_blocks();
-        }
-        __syncwarp();
-    }
-}
-
-// ------------------------------------------------------------------------------------------
-// Fold of a list of blocks (streaming).  A frame touches few blocks (thousands to tens of
-// thousands), so here latency rules, not FP64 issue: each warp takes up to 32 listed blocks
-// per round (one per lane), counts their active contributors with batched code loads,
-// compacts the active codes into its shared memory and copies their operand runs there with
-// asynchronous 16-byte copies (cp.async, all in flight together), then folds the blocks from
-// shared memory, lanes claiming the staged blocks longest first.  Same fold order and
-// operations as k_fold, so the values are the same bits.
-// ------------------------------------------------------------------------------------------
-constexpr int LIST_WARPS = 4;
-constexpr int LIST_BLOCKS = 64;     // staged blocks per warp
-constexpr int LIST_CONTRIB = 256;   // staged operand runs per warp
-constexpr int LIST_RUN = 10;        // doubles per staged run (80 bytes, 16-byte aligned)
-constexpr size_t LIST_WARP_SMEM = sizeof(int4) * LIST_BLOCKS + sizeof(int2) * LIST_BLOCKS +
-                                  sizeof(int32_t) * LIST_CONTRIB +
-                                  sizeof(double) * LIST_RUN * LIST_CONTRIB;
-
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-// copy a contribution's operand run (48 or 80 bytes) into shared memory
-__device__ __forceinline__ void stage_run(const FoldArgs &A, int32_t code, double *dst) {
-    const int la = (code >> 2) & 3, lb = code & 3;
-    const double *rec = A.Ke + (size_t)code_tet(code) * KE_STRIDE;
-    if (la == lb) {
-        const double *src = rec + 6 * la;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) cp_async16(dst + 2 * q, src + 2 * q);
-    } else {
-        const int lo = la < lb ? la : lb, hi = la < lb ? lb : la;
-        const double *src = rec + 24 + 10 * pair_index(lo, hi);
-#pragma unroll
-        for (int q = 0; q < 5; ++q) cp_async16(dst + 2 * q, src + 2 * q);
-    }
-}
-
-// the 9 operands of a staged run (same three layouts as load_contrib)
-__device__ __forceinline__ void smem_operands(const double *r, int32_t code, double v[9]) {
-    const int la = (code >> 2) & 3, lb = code & 3;
-    const double2 *p = reinterpret_cast<const double2 *>(r);
-    const double2 p0 = p[0], p1 = p[1], p2 = p[2];
-    if (la == lb) {
-        v[0] = p0.x; v[1] = p0.y; v[2] = p1.x;
-        v[3] = p1.y; v[4] = p2.x; v[5] = p2.y;
-        v[6] = 0.0; v[7] = 0.0; v[8] = 0.0;
-    } else {
-        const double2 p3 = p[3], p4 = p[4];
-        const double w[9] = {p0.x, p0.y, p1.x, p1.y, p2.x, p2.y, p3.x, p3.y, p4.x};
-        const bool tr = la > lb;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) v[3 * i + j] = tr ? w[3 * j + i] : w[3 * i + j];
-    }
-}
-
 // One lane folds a whole unit from global memory (units larger than the shared buffers).
 __device__ void fold_direct(const FoldArgs &A, const int4 bm, const int2 mir) {
     double acc[9], v[9];
@@ -483,157 +134,6 @@ __device__ void fold_direct(const FoldArgs &A, const int4 bm, const int2 mir) {
     write_block(A, unit_out(A, bm, mir), acc);
 }
 
-__global__ void __launch_bounds__(LIST_WARPS * 32)
-k_fold_list(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *__restrict__ count) {
-    extern __shared__ int4 list_smem[];
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int4 *sblk = list_smem + (size_t)wid * (LIST_WARP_SMEM / sizeof(int4));
-    int2 *smir = reinterpret_cast<int2 *>(sblk + LIST_BLOCKS);
-    int32_t *scode = reinterpret_cast<int32_t *>(smir + LIST_BLOCKS);
-    double *sop = reinterpret_cast<double *>(scode + LIST_CONTRIB);
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t nitems = (int64_t)*count;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    int64_t p_base = 0;
-    bool more = true;
-    while (more) {
-        // ------------------------------------------------------------ stage
-        int nlong = 0, nshort = 0, nc = 0;
-        while (true) {
-            const int nb = nlong + nshort;
-            const int64_t p = p_base + lane;
-            const int64_t item = ((p >> 5) * nwarps + warp) * 32 + (p & 31);
-            const bool valid = item < nitems;
-            int4 bm = make_int4(0, 0, 0, 0);
-            int2 mir = make_int2(0, 0);
-            if (valid) {
-                const int32_t u = __ldg(list + item);
-                bm = __ldg(A.bmeta + u);
-                mir = __ldg(A.bmirror + u);
-            }
-            const unsigned validm = __ballot_sync(FULL, valid);
-            if (!validm) {
-                more = false;
-                break;
-            }
-            const int nv = __popc(validm);
-            int cnt = 0;
-            for (int32_t c0 = bm.z; c0 < bm.w; c0 += 8) {  // 8 code loads in flight
-                int32_t cb[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) cb[u] = c0 + u < bm.w ? __ldg(A.ccode + c0 + u) : 0;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) cnt += cb[u] < 0;
-            }
-            const int hi = warp_inclusive_scan(cnt, lane), lo = hi - cnt;
-            const unsigned nzm = __ballot_sync(FULL, valid && cnt > 0);
-            const int blk_upto = nb + __popc(nzm & (lt_mask | (1u << lane)));
-            const bool fits = valid && nc + hi <= LIST_CONTRIB && blk_upto <= LIST_BLOCKS;
-            const unsigned fitm = __ballot_sync(FULL, fits);
-            const int nfit = __popc(fitm);
-            if (nfit == 0) {
-                if (nc == 0 && nb == 0) {  // one block larger than the buffers
-                    if (lane == 0) fold_direct(A, bm, mir);
-                    p_base += 1;
-                    continue;
-                }
-                break;
-            }
-            if (fits) {
-                int j = nc + lo;
-                for (int32_t c = bm.z; c < bm.w; ++c) {
-                    const int32_t code = __ldg(A.ccode + c);
-                    if (code < 0) {
-                        scode[j] = code;
-                        stage_run(A, code, sop + LIST_RUN * j);
-                        ++j;
-                    }
-                }
-            }
-            const unsigned longm = __ballot_sync(FULL, fits && cnt >= LONG_BLOCK);
-            const unsigned shortm = __ballot_sync(FULL, fits && cnt > 0 && cnt < LONG_BLOCK);
-            if (fits) {
-                if (cnt == 0) {
-                    double acc[9];
-#pragma unroll
-                    for (int q = 0; q < 9; ++q) acc[q] = 0.0;
-                    write_block(A, unit_out(A, bm, mir), acc);
-                } else {
-                    const int at = cnt >= LONG_BLOCK ? nlong + __popc(longm & lt_mask)
-                                                     : LIST_BLOCKS - 1 - nshort - __popc(shortm & lt_mask);
-                    sblk[at] = make_int4(bm.x, bm.y, nc + lo, cnt);
-                    smir[at] = mir;
-                }
-            }
-            nlong += __popc(longm);
-            nshort += __popc(shortm);
-            nc += __shfl_sync(FULL, hi, nfit - 1);
-            p_base += nfit;
-            if (nfit < nv) break;
-        }
-        cp_async_wait_all();
-        __syncwarp();
-        // ------------------------------------------------------------ fold
-        const int nstaged = nlong + nshort;
-        int next_blk = 0;
-        bool busy = false, parked = false;
-        int k = 0, kend = 0;
-        BlockOut o{nullptr, nullptr, 0, 0, false};
-        double acc[9], v[9];
-        auto claim_blocks = [&]() {
-            while (true) {
-                const unsigned need = __ballot_sync(FULL, !busy && !parked);
-                if (!need) break;
-                const int b = next_blk + __popc(need & lt_mask);
-                next_blk += __popc(need);
-                if (!busy && !parked) {
-                    if (b >= nstaged) {
-                        parked = true;
-                    } else {
-                        const int at = b < nlong ? b : LIST_BLOCKS - 1 - (b - nlong);
-                        const int4 sb = sblk[at];
-                        o = unit_out(A, sb, smir[at]);
-                        k = sb.z;
-                        kend = sb.z + sb.w;
-                        smem_operands(sop + LIST_RUN * k, scode[k], v);
-#pragma unroll
-                        for (int q = 0; q < 9; ++q) acc[q] = plus_zero(v[q]);
-                        ++k;
-                        if (k == kend) {
-                            write_block(A, o, acc);
-                        } else {
-                            smem_operands(sop + LIST_RUN * k, scode[k], v);
-                            busy = true;
-                        }
-                    }
-                }
-            }
-        };
-        claim_blocks();
-        while (__any_sync(FULL, busy)) {
-            if (busy) {
-#pragma unroll
-                for (int q = 0; q < 6; ++q) acc[q] += v[q];
-                if (!o.diag) {
-#pragma unroll
-                    for (int q = 6; q < 9; ++q) acc[q] += v[q];
-                }
-                ++k;
-                if (k < kend) {
-                    smem_operands(sop + LIST_RUN * k, scode[k], v);
-                } else {
-                    write_block(A, o, acc);
-                    busy = false;
-                }
-            }
-            if (__any_sync(FULL, !busy && !parked)) claim_blocks();
-        }
-        __syncwarp();
-    }
-}
-
 // ------------------------------------------------------------------------------------------
 // Entry-parallel fold of a list of units (streaming).  A frame's touched list is short and its
 // longest folds (diagonal units, ~24 contributions) set the latency, so here each lane folds ONE
@@ -641,36 +141,47 @@ k_fold_list(FoldArgs A, const int32_t *__restrict__ list, const unsigned long lo
 // unit g (6 of them for a diagonal unit), and one FP64 instruction per step advances all 27
 // folds.  The unit's active codes are compacted (in list order) into shared memory first; each
 // step then loads one operand per lane (4 steps of loads in flight).  Operands, order and
-// operations are those of k_fold, so the values are the same bits.
+// operations are those of k_fold_flat, so the values are the same bits.
 // ------------------------------------------------------------------------------------------
 constexpr int ENT_UNITS = 3;    // units per warp round (27 lanes)
 constexpr int ENT_CAP = 96;     // active contributions staged per unit; larger units fold directly
 constexpr int ENT_WARPS = 4;
 
-template <int MODE>  // 0: units 0 .. nitems_static-1; 1: the listed units (count on the device)
+// Operand base of contributor `code` for the entry-parallel folds, encoded as
+// (record offset << 1) | transposed: a diagonal unit reads entry q of the 6-run of (la, la); an
+// off-diagonal unit entry q = 3i + j of the 9-run of (lo, hi), or -- contributor with la > lb --
+// its transposed entry 3j + i.  T * KE_STRIDE < 2^31 is checked at create.
+__device__ __forceinline__ uint32_t operand_base(int32_t code) {
+    const int la = (code >> 2) & 3, lb = code & 3;
+    const uint32_t rec = (uint32_t)code_tet(code) * KE_STRIDE;
+    if (la == lb) return (rec + 6 * la) << 1;
+    const int lo = la < lb ? la : lb, hi = la < lb ? lb : la;
+    return ((rec + 24 + 10 * pair_index(lo, hi)) << 1) | (la > lb ? 1u : 0u);
+}
+
 __global__ void __launch_bounds__(ENT_WARPS * 32)
-k_fold_entries(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *__restrict__ count,
-               int64_t nitems_static) {
-    __shared__ int32_t scode_all[ENT_WARPS][ENT_UNITS][ENT_CAP];
+k_fold_entries(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *__restrict__ count) {
+    __shared__ uint32_t sop_all[ENT_WARPS][ENT_UNITS][ENT_CAP];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int g = lane / 9, q = lane % 9;  // g == 3: lanes 27..31 idle
     const int qi = q / 3, qj = q % 3;
-    int32_t *scode = scode_all[wid][g < ENT_UNITS ? g : 0];
+    uint32_t *sop = sop_all[wid][g < ENT_UNITS ? g : 0];
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t nitems = MODE == 0 ? nitems_static : (int64_t)*count;
+    const int64_t nitems = (int64_t)*count;
+    const bool has_eps = A.eps != 0.0;
     for (int64_t base = warp * ENT_UNITS; base < nitems; base += nwarps * ENT_UNITS) {  // warp-uniform
         const int64_t item = base + g;
         const bool valid = g < ENT_UNITS && item < nitems;
         int4 bm = make_int4(0, 0, 0, 0);
         int2 mir = make_int2(0, 0);
         if (valid) {
-            const int32_t u = MODE == 0 ? (int32_t)item : __ldg(list + item);
+            const int32_t u = __ldg(list + item);
             bm = __ldg(A.bmeta + u);
             mir = __ldg(A.bmirror + u);
         }
-        // compact the unit's active codes, 9 lanes striding over its contributor list
+        // compact the unit's active contributors (as operand bases), 9 lanes striding over its list
         int nact = 0;
         const int span = valid ? bm.w - bm.z : 0;
         const int max_span = __reduce_max_sync(FULL, span);
@@ -680,59 +191,245 @@ k_fold_entries(FoldArgs A, const int32_t *__restrict__ list, const unsigned long
             const unsigned m = __ballot_sync(FULL, code < 0);
             const unsigned gm = (m >> (9 * g)) & 0x1ffu;
             const int pos = nact + __popc(gm & ((1u << q) - 1u));
-            if (code < 0 && pos < ENT_CAP) scode[pos] = code;
+            if (code < 0 && pos < ENT_CAP) sop[pos] = operand_base(code);
             nact += __popc(gm);
         }
         __syncwarp();
         const bool big = valid && nact > ENT_CAP;
         if (big && q == 0) fold_direct(A, bm, mir);  // rare: more active contributions than staged
-        const int n = valid && !big ? nact : 0;
         const bool diag = (bm.y & 1) != 0;
-        const bool mine = n > 0 && (!diag || q < 6);  // a diagonal unit folds 6 entries
+        const bool mine = valid && !big && (!diag || q < 6);  // a diagonal unit folds 6 entries
+        const int n = mine ? nact : 0;
+        const int qt = diag ? q : 3 * qj + qi;  // entry of a transposed run
         double acc = 0.0;
         const int maxn = __reduce_max_sync(FULL, n);
-        for (int j0 = 0; j0 < maxn; j0 += 4) {
-            double v[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                v[t] = 0.0;
-                const int j = j0 + t;
-                if (mine && j < n) {
-                    const int32_t code = scode[j];
-                    const int la = (code >> 2) & 3, lb = code & 3;
-                    const double *rec = A.Ke + (size_t)code_tet(code) * KE_STRIDE;
-                    if (la == lb) {
-                        v[t] = __ldg(rec + 6 * la + q);
-                    } else {
-                        const int lo = la < lb ? la : lb, hi = la < lb ? lb : la;
-                        v[t] = __ldg(rec + 24 + 10 * pair_index(lo, hi) + (la < lb ? q : 3 * qj + qi));
-                    }
-                }
+#define STA_LD(j) ((j) < n ? __ldg(A.Ke + (sop[(j)] >> 1) + ((sop[(j)] & 1u) ? qt : q)) : 0.0)
+        if (maxn > 0) {  // warp-uniform guards, as in k_fold_flat
+            acc = plus_zero(STA_LD(0));  // the first contribution: +0.0 + v, no FP64 add
+            double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+            if (maxn > 1) v0 = STA_LD(1);
+            if (maxn > 2) v1 = STA_LD(2);
+            if (maxn > 3) v2 = STA_LD(3);
+            if (maxn > 4) v3 = STA_LD(4);
+            int j = 1;
+            for (; j + 4 <= maxn; j += 4) {  // next 4 operands in flight
+                double x0 = 0.0, x1 = 0.0, x2 = 0.0, x3 = 0.0;
+                if (j + 4 < maxn) x0 = STA_LD(j + 4);
+                if (j + 5 < maxn) x1 = STA_LD(j + 5);
+                if (j + 6 < maxn) x2 = STA_LD(j + 6);
+                if (j + 7 < maxn) x3 = STA_LD(j + 7);
+                if (j < n) acc += v0;
+                if (j + 1 < n) acc += v1;
+                if (j + 2 < n) acc += v2;
+                if (j + 3 < n) acc += v3;
+                v0 = x0;
+                v1 = x1;
+                v2 = x2;
+                v3 = x3;
             }
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int j = j0 + t;
-                if (mine && j < n) acc = j == 0 ? plus_zero(v[t]) : acc + v[t];
-            }
+            if (j < maxn && j < n) acc += v0;
+            if (j + 1 < maxn && j + 1 < n) acc += v1;
+            if (j + 2 < maxn && j + 2 < n) acc += v2;
         }
-        if (valid && !big) {
+#undef STA_LD
+        if (mine) {
             if (diag) {
-                if (q < 6) {
-                    // 6-run entry q = (i, j), i <= j
-                    const int i = q < 3 ? 0 : (q < 5 ? 1 : 2), j = q < 3 ? q : (q < 5 ? q - 2 : 2);
-                    double a = acc;
-                    if (i == j && A.eps != 0.0) a += A.eps;
-                    double *out = A.val + bm.x;
-                    const int rs = bm.y >> 1;
-                    out[i * rs + j] = a;
-                    if (i != j) out[j * rs + i] = a;
-                }
+                // 6-run entry q = (i, j), i <= j
+                const int i = q < 3 ? 0 : (q < 5 ? 1 : 2), j = q < 3 ? q : (q < 5 ? q - 2 : 2);
+                double a = acc;
+                if (i == j && has_eps) a += A.eps;
+                double *out = A.val + bm.x;
+                const int rs = bm.y >> 1;
+                out[i * rs + j] = a;
+                if (i != j) out[j * rs + i] = a;
             } else {
                 A.val[bm.x + qi * (bm.y >> 1) + qj] = acc;
                 A.val[mir.x + qj * mir.y + qi] = acc;
             }
         }
         __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Flat entry-parallel rebuild.  Every fold entry of the pattern gets a lane: 6 per diagonal
+// unit, 9 per off-diagonal unit.  A warp tile is 32 consecutive entries of units of one kind
+// (tile records built at create: first unit, entry offset, kind, entry count); its units (up to
+// 7) have contiguous contributor codes.  The warp compacts the active codes of that range into
+// shared memory with ballots (list order kept, so each unit's active codes form one segment),
+// each lane locates its unit's segment from the same ballots, and every FP64 add instruction
+// then advances up to 32 folds.  Units are ordered so that a tile's lists have equal length.
+//
+// Each tile needs three dependent loads before its first add (tile record -> unit record ->
+// codes), so the persistent warps run them as a software pipeline: while tile w folds, the
+// first code chunk of tile w+W, the unit records of tile w+2W and the tile record of tile w+3W
+// are in flight (W = warps in the grid).  Operands, order and operations are those of
+// fold_direct and k_fold_entries.
+// ------------------------------------------------------------------------------------------
+constexpr int FLAT_CAP = 448;  // staged active codes per tile; a larger tile folds from the list
+
+// address of the operand that contributor `code` supplies to entry q of its unit
+__device__ __forceinline__ const double *entry_operand(const FoldArgs &A, int32_t code, bool dgl,
+                                                       int q) {
+    const int la = (code >> 2) & 3, lb = code & 3;
+    const double *rec = A.Ke + (size_t)code_tet(code) * KE_STRIDE;
+    if (dgl) return rec + 6 * la + q;
+    const int lo = la < lb ? la : lb, hi = la < lb ? lb : la;
+    return rec + 24 + 10 * pair_index(lo, hi) + (la < lb ? q : 3 * (q % 3) + q / 3);
+}
+
+struct FlatLane {
+    int32_t u;  // unit
+    int q;      // entry of the unit
+    bool dgl, valid;
+    int nv;     // entries in the tile (lanes 0 .. nv-1 valid)
+};
+
+__device__ __forceinline__ FlatLane flat_lane(int2 r, int lane) {
+    FlatLane L;
+    L.dgl = (r.y >> 4) & 1;
+    L.nv = r.y >> 5;
+    L.valid = lane < L.nv;
+    const int e = (r.y & 15) + lane;
+    const int du = L.dgl ? e / FOLD_TASKS_DIAG : e / FOLD_TASKS_PAIR;
+    L.u = r.x + du;
+    L.q = e - (L.dgl ? FOLD_TASKS_DIAG : FOLD_TASKS_PAIR) * du;
+    return L;
+}
+
+__device__ __forceinline__ int2 flat_rec(const int2 *__restrict__ trec, int64_t w, int64_t ntiles) {
+    return w < ntiles ? __ldg(trec + w) : make_int2(0, 0);  // nv = 0: no valid lane
+}
+
+template <int WARPS>  // warps per CTA: 2, 4 or 8 (at most 64 registers a thread)
+__global__ void __launch_bounds__(WARPS * 32, 32 / WARPS)
+k_fold_flat(FoldArgs A, const int2 *__restrict__ trec, int64_t ntiles) {
+    __shared__ int32_t sbuf[WARPS][FLAT_CAP];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    int32_t *scode = sbuf[threadIdx.x >> 5];
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int4 Z4 = make_int4(0, 0, 0, 0);
+    const bool has_eps = A.eps != 0.0;
+
+    // pipeline prologue: records of tiles w, w+W, w+2W; unit records of w, w+W; codes of w
+    int64_t w = warp;
+    int2 r0 = flat_rec(trec, w, ntiles), r1 = flat_rec(trec, w + W, ntiles),
+         r2 = flat_rec(trec, w + 2 * W, ntiles);
+    FlatLane L = flat_lane(r0, lane);
+    int4 bm0 = L.valid ? __ldg(A.bmeta + L.u) : Z4;
+    int2 mir0 = L.valid && !L.dgl ? __ldg(A.bmirror + L.u) : make_int2(0, 0);
+    FlatLane L1 = flat_lane(r1, lane);
+    int4 bm1 = L1.valid ? __ldg(A.bmeta + L1.u) : Z4;
+    int32_t cr0 = __shfl_sync(FULL, bm0.z, 0), cr1 = __shfl_sync(FULL, bm0.w, L.nv > 0 ? L.nv - 1 : 0);
+    if (L.nv == 0) cr0 = cr1 = 0;
+    int32_t code0 = cr0 + lane < cr1 ? __ldg(A.ccode + cr0 + lane) : 0;
+
+    for (; w < ntiles; w += W) {  // warp-uniform
+        // stage 0: tile record of w + 3W
+        const int2 r3 = flat_rec(trec, w + 3 * W, ntiles);
+        // stage 1: unit records of w + 2W
+        const FlatLane L2 = flat_lane(r2, lane);
+        const int4 bm2 = L2.valid ? __ldg(A.bmeta + L2.u) : Z4;
+        // stage 2: first code chunk and mirror records of w + W
+        int32_t nr0 = __shfl_sync(FULL, bm1.z, 0), nr1 = __shfl_sync(FULL, bm1.w, L1.nv > 0 ? L1.nv - 1 : 0);
+        if (L1.nv == 0) nr0 = nr1 = 0;
+        const int32_t code1 = nr0 + lane < nr1 ? __ldg(A.ccode + nr0 + lane) : 0;
+        const int2 mir1 = L1.valid && !L1.dgl ? __ldg(A.bmirror + L1.u) : make_int2(0, 0);
+
+        // stage 3: tile w -- compact its active codes
+        int base = 0, lo = 0, hi = 0;
+        for (int32_t c0 = cr0; c0 < cr1; c0 += 32) {  // warp-uniform
+            const int32_t c = c0 + lane;
+            const int32_t code = c0 == cr0 ? code0 : (c < cr1 ? __ldg(A.ccode + c) : 0);
+            const unsigned m = __ballot_sync(FULL, code < 0);
+            const int pos = base + __popc(m & below);
+            if (code < 0 && pos < FLAT_CAP) scode[pos] = (int32_t)operand_base(code);
+            const int dz = bm0.z - c0, dw = bm0.w - c0;
+            if (dz >= 0 && dz < 32) lo = base + __popc(m & ((1u << dz) - 1u));
+            if (dw >= 0 && dw < 32) hi = base + __popc(m & ((1u << dw) - 1u));
+            base += __popc(m);
+        }
+        if (bm0.z >= cr1) lo = base;
+        if (bm0.w >= cr1) hi = base;
+        __syncwarp();
+        const int n = L.valid ? hi - lo : 0;
+        const bool dgl = L.dgl;
+        const int q = L.q;
+        double acc = 0.0;
+        if (base <= FLAT_CAP) {
+            const int maxn = __reduce_max_sync(FULL, n);
+            // staged entries are operand bases (operand_base), not codes
+            const uint32_t *sc = reinterpret_cast<const uint32_t *>(scode) + lo;
+            const int qt = dgl ? q : 3 * (q % 3) + q / 3;  // entry of a transposed run
+            // every guard on maxn is warp-uniform: a tile issues no operand work past its
+            // longest fold (a tile of units without active contributors issues none at all)
+#define STA_LD(j) ((j) < n ? __ldg(A.Ke + (sc[(j)] >> 1) + ((sc[(j)] & 1u) ? qt : q)) : 0.0)
+            if (maxn > 0) {
+                acc = plus_zero(STA_LD(0));  // the first contribution: +0.0 + v, no FP64 add
+                double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+                if (maxn > 1) v0 = STA_LD(1);
+                if (maxn > 2) v1 = STA_LD(2);
+                if (maxn > 3) v2 = STA_LD(3);
+                if (maxn > 4) v3 = STA_LD(4);
+                int j = 1;
+                for (; j + 4 <= maxn; j += 4) {  // next 4 operands in flight
+                    double x0 = 0.0, x1 = 0.0, x2 = 0.0, x3 = 0.0;
+                    if (j + 4 < maxn) x0 = STA_LD(j + 4);
+                    if (j + 5 < maxn) x1 = STA_LD(j + 5);
+                    if (j + 6 < maxn) x2 = STA_LD(j + 6);
+                    if (j + 7 < maxn) x3 = STA_LD(j + 7);
+                    if (j < n) acc += v0;
+                    if (j + 1 < n) acc += v1;
+                    if (j + 2 < n) acc += v2;
+                    if (j + 3 < n) acc += v3;
+                    v0 = x0;
+                    v1 = x1;
+                    v2 = x2;
+                    v3 = x3;
+                }
+                if (j < maxn && j < n) acc += v0;
+                if (j + 1 < maxn && j + 1 < n) acc += v1;
+                if (j + 2 < maxn && j + 2 < n) acc += v2;
+            }
+#undef STA_LD
+        } else if (L.valid) {  // rare: more active codes than staged; fold from the list itself
+            int j = 0;
+            for (int32_t c = bm0.z; c < bm0.w; ++c) {
+                const int32_t code = __ldg(A.ccode + c);
+                if (code >= 0) continue;
+                const double v = __ldg(entry_operand(A, code, dgl, q));
+                acc = j == 0 ? plus_zero(v) : acc + v;
+                ++j;
+            }
+        }
+        if (L.valid) {
+            const int rs = bm0.y >> 1;
+            if (dgl) {  // 6-run entry q = (i, j), i <= j, mirrored; eps on the diagonal
+                const int i = q < 3 ? 0 : (q < 5 ? 1 : 2), j = q < 3 ? q : (q < 5 ? q - 2 : 2);
+                double a = acc;
+                if (i == j && has_eps) a += A.eps;
+                A.val[bm0.x + i * rs + j] = a;
+                if (i != j) A.val[bm0.x + j * rs + i] = a;
+            } else {
+                const int qi = q / 3, qj = q % 3;
+                A.val[bm0.x + qi * rs + qj] = acc;
+                A.val[mir0.x + qj * mir0.y + qi] = acc;
+            }
+        }
+        __syncwarp();
+        // advance the pipeline
+        L = L1;
+        bm0 = bm1;
+        mir0 = mir1;
+        cr0 = nr0;
+        cr1 = nr1;
+        code0 = code1;
+        L1 = L2;
+        bm1 = bm2;
+        r2 = r3;
     }
 }
 
@@ -846,7 +543,6 @@ __global__ void k_stream_compact_dc(const int32_t *__restrict__ edited, const in
 
 }  // namespace
 
-int max_block_contributors() { return STAGE_CODES; }
 
 namespace {
 
@@ -856,10 +552,10 @@ FoldArgs fold_args(const Ctx *c) {
 
 }  // namespace
 
-int persistent_grid(const Ctx *c, const void *kernel, int threads, int64_t items, size_t smem) {
-    int per_sm = c->blocks_per_sm;
+int persistent_grid(const Ctx *c, const void *kernel, int threads, int64_t items, bool tuned) {
+    int per_sm = tuned ? c->blocks_per_sm : 0;
     if (per_sm <= 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
     }
@@ -869,68 +565,34 @@ int persistent_grid(const Ctx *c, const void *kernel, int threads, int64_t items
     return (int)(g < 1 ? 1 : g);
 }
 
-// Launch the fold with the context's CTA shape (block_threads 64, 128 or 256).
-template <int MODE>
-int launch_fold(Ctx *c, const int32_t *list, const unsigned long long *count, int64_t nitems,
-                int64_t max_items, cudaStream_t s) {
-    const int threads = c->block_threads == 64 || c->block_threads == 256 ? c->block_threads : 128;
-    const void *kern = threads == 64    ? (const void *)k_fold<MODE, 2>
-                       : threads == 256 ? (const void *)k_fold<MODE, 8>
-                                        : (const void *)k_fold<MODE, 4>;
-    const size_t smem = FOLD_WARP_SMEM * (threads / 32);
-    const int grid = persistent_grid(c, kern, threads, max_items, smem);
-    if (threads == 64)
-        k_fold<MODE, 2><<<grid, threads, smem, s>>>(fold_args(c), list, count, nitems);
-    else if (threads == 256)
-        k_fold<MODE, 8><<<grid, threads, smem, s>>>(fold_args(c), list, count, nitems);
-    else
-        k_fold<MODE, 4><<<grid, threads, smem, s>>>(fold_args(c), list, count, nitems);
-    STA_CUDA_TRY(cudaGetLastError());
-    return STA_OK;
-}
-
-// Dynamic shared memory limits of the fold instantiations (set once per context creation,
-// outside any stream capture).
-int init_fold_attributes() {
-    const void *k[6] = {(const void *)k_fold<0, 2>, (const void *)k_fold<0, 4>,
-                        (const void *)k_fold<0, 8>, (const void *)k_fold<1, 2>,
-                        (const void *)k_fold<1, 4>, (const void *)k_fold<1, 8>};
-    const int w[6] = {2, 4, 8, 2, 4, 8};
-    for (int i = 0; i < 6; ++i)
-        STA_CUDA_TRY(cudaFuncSetAttribute(k[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)(FOLD_WARP_SMEM * w[i])));
-    STA_CUDA_TRY(cudaFuncSetAttribute((const void *)k_fold_list,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(LIST_WARP_SMEM * LIST_WARPS)));
-    return STA_OK;
-}
-
 int launch_fold_list(Ctx *c, const int32_t *list, const unsigned long long *count,
                      int64_t max_items, cudaStream_t s) {
     const int threads = ENT_WARPS * 32;
     // one unit per 9 lanes (3 per warp) for the largest possible list, at most the resident CTAs
-    const int grid = persistent_grid(c, (const void *)k_fold_entries<1>, threads,
+    const int grid = persistent_grid(c, (const void *)k_fold_entries, threads,
                                      (max_items + ENT_UNITS - 1) / ENT_UNITS * 32);
-    k_fold_entries<1><<<grid, threads, 0, s>>>(fold_args(c), list, count, 0);
+    k_fold_entries<<<grid, threads, 0, s>>>(fold_args(c), list, count);
     STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;
 }
 
-#ifndef STA_REBUILD_ENTRIES
-#define STA_REBUILD_ENTRIES 0
-#endif
-
+// Full rebuild: the flat entry-parallel fold over all tiles, with the context's CTA shape
+// (block_threads 64, 128 or 256; blocks_per_sm 0 = occupancy maximum).
 int launch_rebuild(Ctx *c, cudaStream_t s) {
-    if (c->nunits == 0) return STA_OK;
-    if (STA_REBUILD_ENTRIES) {
-        const int threads = ENT_WARPS * 32;
-        const int grid = persistent_grid(c, (const void *)k_fold_entries<0>, threads,
-                                         (c->nunits + ENT_UNITS - 1) / ENT_UNITS * 32);
-        k_fold_entries<0><<<grid, threads, 0, s>>>(fold_args(c), nullptr, nullptr, c->nunits);
-        STA_CUDA_TRY(cudaGetLastError());
-        return STA_OK;
-    }
-    return launch_fold<0>(c, nullptr, nullptr, c->nunits, c->nunits, s);
+    if (c->ntiles == 0) return STA_OK;
+    const int threads = c->block_threads == 64 || c->block_threads == 256 ? c->block_threads : 128;
+    const void *kern = threads == 64    ? (const void *)k_fold_flat<2>
+                       : threads == 256 ? (const void *)k_fold_flat<8>
+                                        : (const void *)k_fold_flat<4>;
+    const int grid = persistent_grid(c, kern, threads, c->ntiles * 32, true);
+    if (threads == 64)
+        k_fold_flat<2><<<grid, threads, 0, s>>>(fold_args(c), c->ftile, c->ntiles);
+    else if (threads == 256)
+        k_fold_flat<8><<<grid, threads, 0, s>>>(fold_args(c), c->ftile, c->ntiles);
+    else
+        k_fold_flat<4><<<grid, threads, 0, s>>>(fold_args(c), c->ftile, c->ntiles);
+    STA_CUDA_TRY(cudaGetLastError());
+    return STA_OK;
 }
 
 int launch_mask_bits(Ctx *c, cudaStream_t s) {

@@ -11,6 +11,7 @@
 //   fold units (node pairs a <= b) with their contributors in ascending tet id, and each
 //   tetrahedron's 10 unit slots                      bmeta / bmirror / ccode / cslot / tunit
 // Lists filled with atomics are sorted afterwards, so every array is deterministic.
+#include <algorithm>
 #include <climits>
 
 #include "sta_internal.cuh"
@@ -277,6 +278,31 @@ __global__ void k_unit_of_block(int64_t nblocks, const int32_t *block_node, cons
     }
 }
 
+// diagonal flag of every unit (upper blocks with a == b)
+__global__ void k_unit_diag(int64_t nblocks, const int32_t *block_node, const int32_t *adj,
+                            const int32_t *upper, const int64_t *uid, uint8_t *diag) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nblocks;
+         g += (int64_t)gridDim.x * blockDim.x)
+        if (upper[g]) diag[uid[g]] = block_node[g] == adj[g] ? 1 : 0;
+}
+
+// lowest contributing tetrahedron of every unit
+__global__ void k_unit_min_tet(const int32_t *tunit, int64_t T, int32_t *umin) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < 10 * T;
+         k += (int64_t)gridDim.x * blockDim.x)
+        atomicMin(&umin[tunit[k]], (int32_t)(k / 10));
+}
+
+// apply a unit renumbering rn (old id -> new id) to the block -> unit maps
+__global__ void k_unit_renumber(int64_t nblocks, const int32_t *upper, const int32_t *rn,
+                                int64_t *uid, int32_t *ublk) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nblocks;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        ublk[g] = rn[ublk[g]];
+        if (upper[g]) uid[g] = rn[uid[g]];
+    }
+}
+
 // tunit[10 t + s] = unit of slot s of tetrahedron t; counts per unit
 __global__ void k_unit_count(const int32_t *tblk, const int32_t *ublk, int64_t T, int32_t *tunit,
                              int32_t *cnt) {
@@ -335,18 +361,6 @@ __global__ void k_unit_meta(int64_t nblocks, const int32_t *block_node, const in
     }
 }
 
-__global__ void k_max_i32(const int32_t *in, int64_t m, int64_t *out) {
-    int32_t mx = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x)
-        mx = in[i] > mx ? in[i] : mx;
-    for (int o = 16; o > 0; o >>= 1) {
-        int32_t y = __shfl_down_sync(0xffffffffu, mx, o);
-        mx = y > mx ? y : mx;
-    }
-    if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long *)out, (unsigned long long)mx);
-}
-
 __global__ void k_to_i32(const int64_t *in, int64_t m, int32_t *out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -372,6 +386,48 @@ struct Scratch {
         return STA_OK;
     }
 };
+
+// Unit order and fold tiles.  The units (node order) are cut into windows of UNIT_WINDOW;
+// inside a window the diagonal units come first, then the off-diagonal ones, each group with
+// the longest contributor lists first.  The rebuild (k_fold_flat) gives every fold entry a
+// lane -- 6 entries per diagonal unit, 9 per off-diagonal unit -- and takes 32 consecutive
+// entries of one group per warp tile, so tiles never mix the two kinds, neighbouring units
+// have lists of equal length (the tile waits for its longest), and a window's values are
+// written close together in time.  Any order gives the same values: each unit folds its own
+// list in its own order.
+// Tile record: {first unit, entry offset in it | diagonal << 4 | entries in the tile << 5}.
+#ifndef STA_UNIT_WINDOW
+#define STA_UNIT_WINDOW 2048
+#endif
+
+void unit_order(const std::vector<int32_t> &cnt, const std::vector<int32_t> &umin,
+                const std::vector<uint8_t> &diag, std::vector<int32_t> &rn, std::vector<int2> &tiles) {
+    const int64_t m = (int64_t)cnt.size();
+    const int64_t W = STA_UNIT_WINDOW > 1 ? STA_UNIT_WINDOW : 1;
+    std::vector<int32_t> order;
+    order.reserve(m);
+    rn.assign(m, 0);
+    tiles.clear();
+    for (int64_t w0 = 0; w0 < m; w0 += W) {
+        const int64_t w1 = std::min(m, w0 + W);
+        for (int cls = 1; cls >= 0; --cls) {
+            const size_t first = order.size();
+            for (int64_t u = w0; u < w1; ++u)
+                if (diag[u] == cls) order.push_back((int32_t)u);
+            std::stable_sort(order.begin() + first, order.end(), [&](int32_t a, int32_t b) {
+                return cnt[a] != cnt[b] ? cnt[a] > cnt[b] : umin[a] < umin[b];
+            });
+            const int64_t per = cls ? FOLD_TASKS_DIAG : FOLD_TASKS_PAIR;
+            const int64_t nent = per * (int64_t)(order.size() - first);
+            for (int64_t e = 0; e < nent; e += 32) {
+                const int64_t k = std::min<int64_t>(32, nent - e);
+                tiles.push_back(make_int2((int32_t)(first + e / per),
+                                          (int32_t)(e % per) | cls << 4 | (int32_t)k << 5));
+            }
+        }
+    }
+    for (int64_t k = 0; k < m; ++k) rn[order[k]] = (int32_t)k;
+}
 
 }  // namespace
 
@@ -458,15 +514,36 @@ int build_pattern(Ctx *c, cudaStream_t s) {
     STA_TRY(sc.get(&uptr, nunits + 1));
     STA_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nunits > 0 ? nunits : 1), s));
     k_unit_count<<<grid_for(10 * T), TPB, 0, s>>>(c->tblk, ublk, T, c->tunit, cnt);
-    STA_CUDA_TRY(cudaMemsetAsync(tiles, 0, sizeof(int64_t), s));
-    k_max_i32<<<grid_for(nunits > 0 ? nunits : 1), TPB, 0, s>>>(cnt, nunits, tiles);
-    int64_t max_contrib = 0;
-    STA_CUDA_TRY(cudaMemcpyAsync(&max_contrib, tiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    STA_CUDA_TRY(cudaStreamSynchronize(s));
-    if (max_contrib > max_block_contributors())
-        return fail(STA_ERANGE, "a node pair is shared by " + std::to_string(max_contrib) +
-                                    " tetrahedra; the fold supports at most " +
-                                    std::to_string(max_block_contributors()));
+    if (nunits > 0) {  // renumber (windows: diagonal units first, longest lists first)
+        uint8_t *udiag = nullptr;
+        int32_t *rn_dev = nullptr;
+        STA_TRY(sc.get(&udiag, nunits));
+        STA_TRY(sc.get(&rn_dev, nunits));
+        k_unit_diag<<<grid_for(nblocks), TPB, 0, s>>>(nblocks, c->block_node, c->adj, upper, uid,
+                                                      udiag);
+        std::vector<int32_t> hcnt(nunits), hmin(nunits), rn;
+        std::vector<uint8_t> hdiag(nunits);
+        std::vector<int2> htiles;
+        k_fill_i32<<<grid_for(nunits), TPB, 0, s>>>(rn_dev, nunits, INT32_MAX);
+        k_unit_min_tet<<<grid_for(10 * T), TPB, 0, s>>>(c->tunit, T, rn_dev);
+        STA_CUDA_TRY(cudaMemcpyAsync(hmin.data(), rn_dev, sizeof(int32_t) * nunits,
+                                     cudaMemcpyDeviceToHost, s));
+        STA_CUDA_TRY(cudaMemcpyAsync(hcnt.data(), cnt, sizeof(int32_t) * nunits,
+                                     cudaMemcpyDeviceToHost, s));
+        STA_CUDA_TRY(cudaMemcpyAsync(hdiag.data(), udiag, nunits, cudaMemcpyDeviceToHost, s));
+        STA_CUDA_TRY(cudaStreamSynchronize(s));
+        unit_order(hcnt, hmin, hdiag, rn, htiles);
+        c->ntiles = (int64_t)htiles.size();
+        STA_TRY(dev_alloc(c, &c->ftile, c->ntiles));
+        STA_CUDA_TRY(cudaMemcpyAsync(c->ftile, htiles.data(), sizeof(int2) * c->ntiles,
+                                     cudaMemcpyHostToDevice, s));
+        STA_CUDA_TRY(cudaMemcpyAsync(rn_dev, rn.data(), sizeof(int32_t) * nunits,
+                                     cudaMemcpyHostToDevice, s));
+        k_unit_renumber<<<grid_for(nblocks), TPB, 0, s>>>(nblocks, upper, rn_dev, uid, ublk);
+        STA_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nunits, s));
+        k_unit_count<<<grid_for(10 * T), TPB, 0, s>>>(c->tblk, ublk, T, c->tunit, cnt);
+        STA_CUDA_TRY(cudaStreamSynchronize(s));  // host vectors go out of scope
+    }
     STA_TRY(exclusive_scan(c, cnt, nunits, uptr, tiles, s));
     STA_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nunits > 0 ? nunits : 1), s));
     k_unit_fill<<<grid_for(10 * T), TPB, 0, s>>>(c->tets, c->tunit, T, uptr, cnt, c->ccode);

@@ -73,6 +73,11 @@ __host__ __device__ inline int slot_of(int la, int lb) {  // unordered local pai
     return 4 + (lo == 0 ? hi - 1 : (lo == 1 ? hi + 1 : 5));
 }
 
+// Lanes of the rebuild fold per unit (one fold entry each): a diagonal unit folds its 6
+// distinct entries, an off-diagonal unit its 9.
+constexpr int FOLD_TASKS_DIAG = 6;
+constexpr int FOLD_TASKS_PAIR = 9;
+
 // ------------------------------------------------------------------------------------
 // Context
 // ------------------------------------------------------------------------------------
@@ -102,6 +107,8 @@ struct Ctx {
     // (3b+j, 3a+i) fold the same operands in the same order (the element matrices are exactly
     // symmetric), so one fold per unit writes both blocks.
     int64_t nunits = 0;
+    int64_t ntiles = 0;
+    int2 *ftile = nullptr;         // ntiles: rebuild fold tiles {first unit, q0 | diag << 4 | entries << 5}
     int4 *bmeta = nullptr;         // nunits: {value offset of (a,b), rs_a << 1 | diagonal, c0, c1}
     int2 *bmirror = nullptr;       // nunits: {value offset of (b,a), rs_b}
     int32_t *ccode = nullptr;      // 10 T: unit contributor codes, ascending tetrahedron id
@@ -159,9 +166,11 @@ template <typename T> int dev_alloc(Ctx *c, T **p, int64_t count) {
     return STA_OK;
 }
 
-// Persistent grid for an item count: min(ceil(items / threads), SMs * CTAs per SM).
+// Persistent grid for an item count: min(ceil(items / threads), SMs * CTAs per SM), CTAs per
+// SM = the context's blocks_per_sm (the rebuild's tuned shape) if `tuned` and it is set, else
+// the occupancy maximum.
 int persistent_grid(const Ctx *c, const void *kernel, int threads, int64_t items,
-                    size_t smem = 0);
+                    bool tuned = false);
 
 // ------------------------------------------------------------------------------------
 // Kernel launchers (each returns STA_OK or STA_ECUDA on a launch error)
@@ -174,12 +183,10 @@ int launch_spmv(Ctx *c, const double *val, const double *x, double *y, cudaStrea
 int launch_rebuild(Ctx *c, cudaStream_t s);                      // sta_assemble.cu
 int launch_stream(Ctx *c, int64_t n_edited, cudaStream_t s);
 int launch_mask_bits(Ctx *c, cudaStream_t s);                    // codes <- mask
-int init_fold_attributes();
 int launch_stream_scratch(Ctx *c, int64_t m, const int32_t *d_edited, int32_t *touched,
                           unsigned long long *counters, cudaStream_t s);
 int launch_stream_devcount(Ctx *c, const int32_t *d_edited, const int64_t *d_m, int64_t cap,
                            cudaStream_t s);
-int max_block_contributors();  // largest contributor list a fold can stage
 
 int create_impl(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
                 const double *young, const double *poisson, const sta_options *opt, void *stream,

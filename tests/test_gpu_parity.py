@@ -129,6 +129,13 @@ def test_streaming_eps_and_small_variants(sta, orc):
         _run_stream(sta, orc, wl)
 
 
+def test_long_contributor_lists(sta, orc):
+    # one node pair and both its nodes shared by K tetrahedra: lists longer than the folds'
+    # shared-memory staging (rebuild tiles and streamed units fall back to unstaged folds)
+    for K, eps in ((300, 0.0), (1000, 1e-2)):
+        _run_stream(sta, orc, W.edge_fan(seed=K, K=K), eps=eps)
+
+
 def test_edge_cases(sta, orc):
     # single tetrahedron with unused nodes around it
     X = np.random.default_rng(0).uniform(size=(7, 3))

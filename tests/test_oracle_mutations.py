@@ -1,9 +1,8 @@
-"""Mistakes planted in copies of the oracle (and of the integer-pipe add) must fail a pin.
+"""Mistakes planted in copies of the oracle must fail a pin.
 
 Each mutation is a plausible slip -- a transposed operand, a dropped term, a wrong sign or
 index, an ignored mask -- compiled on the CPU from a modified copy of the source; the oracle
 wrapper is re-bound to it and the relevant pins of test_oracle_pins run and must fail."""
-import shutil
 import subprocess
 from pathlib import Path
 
@@ -66,16 +65,3 @@ def test_planted_oracle_mistake_fails_a_pin(name, tmp_path):
         assert failed > 0, f"mutation {name} passed every pin"
     finally:
         oracle.use_library(None)
-
-
-@pytest.mark.skipif(shutil.which("g++") is None, reason="needs g++")
-def test_planted_rounding_mistake_in_int_add_is_caught(tmp_path):
-    hdr = (ROOT / "paper_2605_11673_gb300" / "csrc" / "softfloat.cuh").read_text()
-    old = "if (rem > 0x200 || (rem == 0x200 && (sig & 1))) ++sig;"
-    assert hdr.count(old) == 1
-    (tmp_path / "softfloat.cuh").write_text(hdr.replace(old, "if (rem >= 0x200) ++sig;"))
-    exe = tmp_path / "check"
-    subprocess.check_call(["g++", "-O2", "-ffp-contract=off", "-std=c++17", f"-I{tmp_path}",
-                           str(ROOT / "tests" / "native" / "int_add_check.cpp"), "-o", str(exe)])
-    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=600)
-    assert r.returncode != 0 and int(r.stdout.split()[-1]) > 0

@@ -186,6 +186,26 @@ def plain_small(seed: int = 0, N: int = 6, frames: int = 24) -> Workload:
                     {"N": N, "grid_index": gi})
 
 
+def edge_fan(seed: int = 0, K: int = 300, frames: int = 12) -> Workload:
+    """K tetrahedra around one edge: axis nodes 0 = (0,0,0) and 1 = (0,0,1), a ring of K
+    jittered nodes at height 0.5, tets (0, 1, r_k, r_k+1).  The axis pair and both axis nodes
+    are shared by all K tets -- the longest contributor lists a fold meets (edge cases of the
+    fold's shared-memory staging).  70% active at start; each frame deactivates 10% of the
+    active tets and reactivates 10% of T."""
+    rng = rng_for(6, seed)
+    th = 2 * np.pi * (np.arange(K) + rng.uniform(-0.2, 0.2, K)) / K
+    ring = np.stack([np.cos(th), np.sin(th), 0.5 + rng.uniform(-0.1, 0.1, K)], axis=1)
+    X = np.concatenate([[[0.0, 0.0, 0.0], [0.0, 0.0, 1.0]], ring])
+    k = np.arange(K)
+    tets = np.stack([np.zeros(K, int), np.ones(K, int), 2 + k, 2 + (k + 1) % K], axis=1)
+    tets = _orient_positive(X, tets.astype(np.int32))
+    _check_positive(X, tets)
+    mask0 = (rng.uniform(size=K) < 0.7).astype(np.uint8)
+    fr = deact_react_stream(rng, K, mask0, frames, 0.1, 0.1)
+    return Workload(f"edge_fan_K{K}", X, tets, lognormal_E(rng, K), np.full(K, 0.3), mask0, fr,
+                    {"K": K})
+
+
 def prefractured_block(seed: int = 0, N: int = 40, sites: int = 64, frames: int = 24,
                        interfaces_per_frame: int = 3) -> Workload:
     """Pre-fractured block: N^3 hexes x 6 on [0,1]^3, jitter +-0.2h, E lognormal (median 1e5,
