@@ -24,7 +24,7 @@ namespace {
 struct FoldArgs {
     const int4 *__restrict__ bmeta;     // per unit: value offset of (a,b), rs_a << 1 | diag, c0, c1
     const int2 *__restrict__ bmirror;   // per unit: value offset of (b,a), rs_b
-    const int32_t *__restrict__ ccode;  // contributor codes, bit 31 = active
+    const int32_t *__restrict__ ccode;  // contributor words: element-cache offset | active << 31
     const double *__restrict__ Ke;
     double *__restrict__ val;
     double eps;
@@ -36,38 +36,23 @@ __device__ __forceinline__ double plus_zero(double v) {
     return __longlong_as_double(bits == (long long)0x8000000000000000ULL ? 0LL : bits);
 }
 
-__device__ __forceinline__ int pair_index(int a, int b) {  // a < b
-    return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);
-}
-
-// The operands one contributor supplies to a fold unit (node pair a <= b; la, lb the local
-// indices of a and b in the contributing tetrahedron), read with 16-byte loads:
-//   diagonal unit (la == lb): the 6-run of (la, la): v[0..5] = (0,0) (0,1) (0,2) (1,1) (1,2)
-//                              (2,2); the mirrored entries (j, i) fold the same operands;
-//   off-diagonal, la < lb:     the 9-run of (la, lb), row-major: v[3i+j] = K[3la+i][3lb+j];
-//   off-diagonal, la > lb:     the 9-run of (lb, la), transposed.
+// The operands one contributor (word w) supplies to a fold unit {a, b}, id(a) <= id(b): its
+// run of the element cache read row-major, with 16-byte loads --
+//   diagonal unit:     the 6-run of (a, a): v[0..5] = (0,0) (0,1) (0,2) (1,1) (1,2) (2,2); the
+//                      mirrored entries (j, i) fold the same operands;
+//   off-diagonal unit: the 9-run, v[3i+j] = K[3la+i][3lb+j] (runs are stored oriented by id).
 // The mirror block (b, a) folds exactly the same operand sequence (K is stored exactly
 // symmetric), so one fold per unit gives both blocks' values bit for bit.
-__device__ __forceinline__ void load_contrib(const FoldArgs &A, int32_t code, double v[9]) {
-    const int la = (code >> 2) & 3, lb = code & 3;
-    const double *rec = A.Ke + (size_t)code_tet(code) * KE_STRIDE;
-    if (la == lb) {
-        const double2 *r = reinterpret_cast<const double2 *>(rec + 6 * la);
-        const double2 x = __ldg(r), y = __ldg(r + 1), z = __ldg(r + 2);
-        v[0] = x.x; v[1] = x.y; v[2] = y.x;
-        v[3] = y.y; v[4] = z.x; v[5] = z.y;
+__device__ __forceinline__ void load_contrib(const FoldArgs &A, int32_t w, bool diag, double v[9]) {
+    const double2 *r = reinterpret_cast<const double2 *>(A.Ke + word_offset((uint32_t)w));
+    const double2 p0 = __ldg(r), p1 = __ldg(r + 1), p2 = __ldg(r + 2);
+    v[0] = p0.x; v[1] = p0.y; v[2] = p1.x;
+    v[3] = p1.y; v[4] = p2.x; v[5] = p2.y;
+    if (diag) {
         v[6] = 0.0; v[7] = 0.0; v[8] = 0.0;
     } else {
-        const int lo = la < lb ? la : lb, hi = la < lb ? lb : la;
-        const double2 *r = reinterpret_cast<const double2 *>(rec + 24 + 10 * pair_index(lo, hi));
-        const double2 p0 = __ldg(r), p1 = __ldg(r + 1), p2 = __ldg(r + 2), p3 = __ldg(r + 3),
-                      p4 = __ldg(r + 4);
-        const double w[9] = {p0.x, p0.y, p1.x, p1.y, p2.x, p2.y, p3.x, p3.y, p4.x};
-        const bool tr = la > lb;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) v[3 * i + j] = tr ? w[3 * j + i] : w[3 * i + j];
+        const double2 p3 = __ldg(r + 3), p4 = __ldg(r + 4);
+        v[6] = p3.x; v[7] = p3.y; v[8] = p4.x;
     }
 }
 
@@ -116,17 +101,18 @@ __device__ __forceinline__ void write_block(const FoldArgs &A, const BlockOut &o
 
 // One lane folds a whole unit from global memory (units larger than the shared buffers).
 __device__ void fold_direct(const FoldArgs &A, const int4 bm, const int2 mir) {
+    const bool diag = (bm.y & 1) != 0;
     double acc[9], v[9];
     int32_t c = next_active(A, bm.z, bm.w);
     if (c == bm.w) {
 #pragma unroll
         for (int q = 0; q < 9; ++q) acc[q] = 0.0;
     } else {
-        load_contrib(A, __ldg(A.ccode + c), acc);
+        load_contrib(A, __ldg(A.ccode + c), diag, acc);
 #pragma unroll
         for (int q = 0; q < 9; ++q) acc[q] = plus_zero(acc[q]);
         for (c = next_active(A, c + 1, bm.w); c < bm.w; c = next_active(A, c + 1, bm.w)) {
-            load_contrib(A, __ldg(A.ccode + c), v);
+            load_contrib(A, __ldg(A.ccode + c), diag, v);
 #pragma unroll
             for (int q = 0; q < 9; ++q) acc[q] += v[q];  // (diagonal: entries 6..8 unused)
         }
@@ -146,18 +132,6 @@ __device__ void fold_direct(const FoldArgs &A, const int4 bm, const int2 mir) {
 constexpr int ENT_UNITS = 3;    // units per warp round (27 lanes)
 constexpr int ENT_CAP = 96;     // active contributions staged per unit; larger units fold directly
 constexpr int ENT_WARPS = 4;
-
-// Operand base of contributor `code` for the entry-parallel folds, encoded as
-// (record offset << 1) | transposed: a diagonal unit reads entry q of the 6-run of (la, la); an
-// off-diagonal unit entry q = 3i + j of the 9-run of (lo, hi), or -- contributor with la > lb --
-// its transposed entry 3j + i.  T * KE_STRIDE < 2^31 is checked at create.
-__device__ __forceinline__ uint32_t operand_base(int32_t code) {
-    const int la = (code >> 2) & 3, lb = code & 3;
-    const uint32_t rec = (uint32_t)code_tet(code) * KE_STRIDE;
-    if (la == lb) return (rec + 6 * la) << 1;
-    const int lo = la < lb ? la : lb, hi = la < lb ? lb : la;
-    return ((rec + 24 + 10 * pair_index(lo, hi)) << 1) | (la > lb ? 1u : 0u);
-}
 
 __global__ void __launch_bounds__(ENT_WARPS * 32)
 k_fold_entries(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *__restrict__ count) {
@@ -191,7 +165,7 @@ k_fold_entries(FoldArgs A, const int32_t *__restrict__ list, const unsigned long
             const unsigned m = __ballot_sync(FULL, code < 0);
             const unsigned gm = (m >> (9 * g)) & 0x1ffu;
             const int pos = nact + __popc(gm & ((1u << q) - 1u));
-            if (code < 0 && pos < ENT_CAP) sop[pos] = operand_base(code);
+            if (code < 0 && pos < ENT_CAP) sop[pos] = word_offset((uint32_t)code);
             nact += __popc(gm);
         }
         __syncwarp();
@@ -200,10 +174,9 @@ k_fold_entries(FoldArgs A, const int32_t *__restrict__ list, const unsigned long
         const bool diag = (bm.y & 1) != 0;
         const bool mine = valid && !big && (!diag || q < 6);  // a diagonal unit folds 6 entries
         const int n = mine ? nact : 0;
-        const int qt = diag ? q : 3 * qj + qi;  // entry of a transposed run
         double acc = 0.0;
         const int maxn = __reduce_max_sync(FULL, n);
-#define STA_LD(j) ((j) < n ? __ldg(A.Ke + (sop[(j)] >> 1) + ((sop[(j)] & 1u) ? qt : q)) : 0.0)
+#define STA_LD(j) ((j) < n ? __ldg(A.Ke + sop[(j)] + q) : 0.0)
         if (maxn > 0) {  // warp-uniform guards, as in k_fold_flat
             acc = plus_zero(STA_LD(0));  // the first contribution: +0.0 + v, no FP64 add
             double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
@@ -268,15 +241,6 @@ k_fold_entries(FoldArgs A, const int32_t *__restrict__ list, const unsigned long
 // ------------------------------------------------------------------------------------------
 constexpr int FLAT_CAP = 448;  // staged active codes per tile; a larger tile folds from the list
 
-// address of the operand that contributor `code` supplies to entry q of its unit
-__device__ __forceinline__ const double *entry_operand(const FoldArgs &A, int32_t code, bool dgl,
-                                                       int q) {
-    const int la = (code >> 2) & 3, lb = code & 3;
-    const double *rec = A.Ke + (size_t)code_tet(code) * KE_STRIDE;
-    if (dgl) return rec + 6 * la + q;
-    const int lo = la < lb ? la : lb, hi = la < lb ? lb : la;
-    return rec + 24 + 10 * pair_index(lo, hi) + (la < lb ? q : 3 * (q % 3) + q / 3);
-}
 
 struct FlatLane {
     int32_t u;  // unit
@@ -346,7 +310,7 @@ k_fold_flat(FoldArgs A, const int2 *__restrict__ trec, int64_t ntiles) {
             const int32_t code = c0 == cr0 ? code0 : (c < cr1 ? __ldg(A.ccode + c) : 0);
             const unsigned m = __ballot_sync(FULL, code < 0);
             const int pos = base + __popc(m & below);
-            if (code < 0 && pos < FLAT_CAP) scode[pos] = (int32_t)operand_base(code);
+            if (code < 0 && pos < FLAT_CAP) scode[pos] = (int32_t)word_offset((uint32_t)code);
             const int dz = bm0.z - c0, dw = bm0.w - c0;
             if (dz >= 0 && dz < 32) lo = base + __popc(m & ((1u << dz) - 1u));
             if (dw >= 0 && dw < 32) hi = base + __popc(m & ((1u << dw) - 1u));
@@ -361,12 +325,11 @@ k_fold_flat(FoldArgs A, const int2 *__restrict__ trec, int64_t ntiles) {
         double acc = 0.0;
         if (base <= FLAT_CAP) {
             const int maxn = __reduce_max_sync(FULL, n);
-            // staged entries are operand bases (operand_base), not codes
+            // staged entries are element-cache offsets of the contributors' runs
             const uint32_t *sc = reinterpret_cast<const uint32_t *>(scode) + lo;
-            const int qt = dgl ? q : 3 * (q % 3) + q / 3;  // entry of a transposed run
             // every guard on maxn is warp-uniform: a tile issues no operand work past its
             // longest fold (a tile of units without active contributors issues none at all)
-#define STA_LD(j) ((j) < n ? __ldg(A.Ke + (sc[(j)] >> 1) + ((sc[(j)] & 1u) ? qt : q)) : 0.0)
+#define STA_LD(j) ((j) < n ? __ldg(A.Ke + sc[(j)] + q) : 0.0)
             if (maxn > 0) {
                 acc = plus_zero(STA_LD(0));  // the first contribution: +0.0 + v, no FP64 add
                 double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
@@ -400,7 +363,7 @@ k_fold_flat(FoldArgs A, const int2 *__restrict__ trec, int64_t ntiles) {
             for (int32_t c = bm0.z; c < bm0.w; ++c) {
                 const int32_t code = __ldg(A.ccode + c);
                 if (code >= 0) continue;
-                const double v = __ldg(entry_operand(A, code, dgl, q));
+                const double v = __ldg(A.Ke + word_offset((uint32_t)code) + q);
                 acc = j == 0 ? plus_zero(v) : acc + v;
                 ++j;
             }
@@ -462,7 +425,7 @@ __global__ void k_mask_bits(int32_t *__restrict__ ccode, int64_t n, const uint8_
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t code = (uint32_t)ccode[k];
-        const uint32_t on = mask[code_tet((int32_t)code)] ? CODE_ACTIVE : 0u;
+        const uint32_t on = mask[word_tet(code)] ? CODE_ACTIVE : 0u;
         ccode[k] = (int32_t)((code & ~CODE_ACTIVE) | on);
     }
 }

@@ -30,10 +30,11 @@ __device__ __forceinline__ V3 cross_fma(const V3 &u, const V3 &v) {
 
 __device__ __forceinline__ double gc(const V3 &g, int i) { return i == 0 ? g.x : (i == 1 ? g.y : g.z); }
 
-// Computes the 78-entry record of one tetrahedron into rec[] (registers or shared memory).
-// Returns false when det <= 0 (record filled with zeros).
+// Computes the 78-entry record of one tetrahedron (node ids q) into rec[] (registers or shared
+// memory).  Returns false when det <= 0 (record filled with zeros).
 __device__ __forceinline__ bool element_record(double4_32a x0, double4_32a x1, double4_32a x2, double4_32a x3,
-                                               double E, double nu, double *rec) {
+                                               double E, double nu, int4 q, double *rec) {
+    const int gid[4] = {q.x, q.y, q.z, q.w};
     V3 d1 = sub(x1, x0), d2 = sub(x2, x0), d3 = sub(x3, x0);
     V3 c1 = cross_fma(d2, d3), c2 = cross_fma(d3, d1), c3 = cross_fma(d1, d2);
     double det = __fma_rn(d1.z, c1.z, __fma_rn(d1.y, c1.y, d1.x * c1.x));
@@ -84,6 +85,7 @@ __device__ __forceinline__ bool element_record(double4_32a x0, double4_32a x1, d
         for (int b = a + 1; b < 4; ++b) {
             double D = Vm * __fma_rn(g[a].z, g[b].z, __fma_rn(g[a].y, g[b].y, g[a].x * g[b].x));
             double *o = rec + ke_off_off(a, b);
+            const bool tr = gid[a] > gid[b];  // run stored with the lower node id's rows
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -91,7 +93,7 @@ __device__ __forceinline__ bool element_record(double4_32a x0, double4_32a x1, d
                     double v = (i != j)
                                    ? __fma_rn(P[a][i], gc(g[b], j), Q[a][j] * gc(g[b], i))
                                    : __fma_rn(P[a][i], gc(g[b], i), __fma_rn(Q[a][i], gc(g[b], i), D));
-                    o[3 * i + j] = v;
+                    o[tr ? 3 * j + i : 3 * i + j] = v;
                 }
             o[9] = 0.0;  // pad to a 16-byte aligned run
         }
@@ -115,7 +117,7 @@ k_elements(const double4_32a *__restrict__ X, const int4 *__restrict__ tets,
         if (doit) {
             int4 q = tets[t];
             double2 m = mat[t];
-            bool ok = element_record(X[q.x], X[q.y], X[q.z], X[q.w], m.x, m.y,
+            bool ok = element_record(X[q.x], X[q.y], X[q.z], X[q.w], m.x, m.y, q,
                                      wrec + (size_t)lane * KE_STRIDE);
             if (!ok) {
                 atomicAdd(&bad[0], 1ull);
@@ -272,8 +274,8 @@ __global__ void k_spmv(const int32_t *__restrict__ row_ptr, const int32_t *__res
 }
 
 // Expand cached records of selected tetrahedra to full 12x12 row-major matrices.
-__global__ void k_expand(const double *__restrict__ Ke, int64_t T, const int32_t *ids,
-                         int64_t n, double *out) {
+__global__ void k_expand(const double *__restrict__ Ke, const int4 *__restrict__ tets, int64_t T,
+                         const int32_t *ids, int64_t n, double *out) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < 144 * n;
          k += (int64_t)gridDim.x * blockDim.x) {
         int64_t e = k / 144;
@@ -289,7 +291,11 @@ __global__ void k_expand(const double *__restrict__ Ke, int64_t T, const int32_t
             a = b; i = j; b = ta; j = ti;
         }
         const double *rec = Ke + (size_t)t * KE_STRIDE;
-        out[k] = (a == b) ? rec[ke_diag_off(a) + ke_tri(i, j)] : rec[ke_off_off(a, b) + 3 * i + j];
+        const int4 tq = tets[t];
+        const int gid[4] = {tq.x, tq.y, tq.z, tq.w};
+        out[k] = (a == b)             ? rec[ke_diag_off(a) + ke_tri(i, j)]
+                 : gid[a] < gid[b] ? rec[ke_off_off(a, b) + 3 * i + j]
+                                   : rec[ke_off_off(a, b) + 3 * j + i];
     }
 }
 
@@ -348,7 +354,7 @@ int launch_expand_elements(Ctx *c, const int32_t *ids, int64_t n, double *out, c
     int64_t items = 144 * n;
     int64_t blocks = (items + 255) / 256;
     if (blocks > 65535LL * 16) blocks = 65535LL * 16;
-    k_expand<<<(unsigned)blocks, 256, 0, s>>>(c->Ke, c->T, ids, n, out);
+    k_expand<<<(unsigned)blocks, 256, 0, s>>>(c->Ke, c->tets, c->T, ids, n, out);
     STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;
 }

@@ -36,9 +36,13 @@ int fail(int code, const std::string &msg);
 // Element cache record: the 78 unique entries of the symmetric 12x12 element matrix,
 // grouped by 3x3 node-pair block so that one block is one contiguous, 16-byte aligned run:
 //   diagonal block (a, a), a = 0..3:  6 entries (i <= j, row-major) at 6a
-//   off-diagonal block (a, b), a < b:   9 entries (i, j row-major) + 1 pad at 24 + 10 pair(a, b)
+//   off-diagonal pair {a, b}, a < b:   9 entries + 1 pad at 24 + 10 pair(a, b), row-major over
+//                                      the block of the node with the LOWER global id, i.e.
+//                                      K[3a+i][3b+j] at 3i+j if id(a) < id(b), else at 3j+i
 // with pair(0,1..3) = 0..2, pair(1,2..3) = 3..4, pair(2,3) = 5.  84 doubles (672 B) per
-// tetrahedron; every run starts on a 16-byte boundary so a fold reads it with 16-byte loads.
+// tetrahedron; every run starts on a 16-byte boundary.  Oriented this way, the contribution of
+// any tetrahedron to the node-pair block (a, b), id(a) < id(b), is its run read row-major:
+// the folds never transpose.
 // ------------------------------------------------------------------------------------
 constexpr int KE_STRIDE = 84;
 
@@ -60,6 +64,11 @@ __host__ __device__ inline int32_t contrib_code(int32_t t, int la, int lb) {
     return (t << 4) | (la << 2) | lb;
 }
 __host__ __device__ inline int32_t code_tet(int32_t code) { return (code >> 4) & 0x07ffffff; }
+
+// Contributor word of a unit list (ccode after create): the element-cache offset of the
+// contributor's run for the unit (t * KE_STRIDE + run offset) | active << 31.
+__host__ __device__ inline uint32_t word_offset(uint32_t w) { return w & 0x7fffffffu; }
+__host__ __device__ inline int32_t word_tet(uint32_t w) { return (int32_t)(word_offset(w) / KE_STRIDE); }
 
 // The 10 unit slots of a tetrahedron: 0..3 diagonal (la, la), 4..9 the pairs (0,1) (0,2) (0,3)
 // (1,2) (1,3) (2,3).
@@ -111,7 +120,7 @@ struct Ctx {
     int2 *ftile = nullptr;         // ntiles: rebuild fold tiles {first unit, q0 | diag << 4 | entries << 5}
     int4 *bmeta = nullptr;         // nunits: {value offset of (a,b), rs_a << 1 | diagonal, c0, c1}
     int2 *bmirror = nullptr;       // nunits: {value offset of (b,a), rs_b}
-    int32_t *ccode = nullptr;      // 10 T: unit contributor codes, ascending tetrahedron id
+    int32_t *ccode = nullptr;      // 10 T: unit contributor words (word_offset), ascending tet id
     int32_t *cslot = nullptr;      // T x 10: position in ccode of tet t's unit slot
     int32_t *tunit = nullptr;      // T x 10: unit of tet t's slot (4 diagonal, 6 pairs)
     int32_t *nt_ptr = nullptr;     // n + 1: node -> incident tetrahedra
