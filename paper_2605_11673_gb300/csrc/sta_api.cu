@@ -1,5 +1,6 @@
 // C-ABI entry points of libsta (declared in include/sta.h): argument and edit validation on
 // the host, device memory management, and the launch sequence of each call.
+#include <algorithm>
 #include <climits>
 #include <cstdio>
 #include <cstring>
@@ -35,8 +36,8 @@ static void free_ctx(sta_ctx *x) {
     if (!x) return;
     for (void *p : x->c.allocations) cudaFree(p);
     x->c.allocations.clear();
-    if (x->c.h_edited) cudaFreeHost(x->c.h_edited);
-    if (x->c.d_edited) cudaFree(x->c.d_edited);
+    if (x->c.h_frame) cudaFreeHost(x->c.h_frame);
+    if (x->c.d_frame) cudaFree(x->c.d_frame);
     if (x->h_mask) cudaFreeHost(x->h_mask);
     if (x->h2d_done) cudaEventDestroy(x->h2d_done);
     graph_release(&x->c);
@@ -161,6 +162,8 @@ int sta::create_impl(const double *nodes, int64_t n_nodes, const int32_t *tets, 
                                          std::to_string(back[2]) + ")"));
     c->host_mask.assign((size_t)n_tets, 0);
     c->seen.assign((size_t)n_tets, 0);
+    c->stamp.assign((size_t)n_tets, 0);
+    c->last_counters = c->counters;
     if (cudaMallocHost((void **)&x->h_mask, (size_t)(n_tets > 0 ? n_tets : 1)) != cudaSuccess)
         return bail(fail(STA_ENOMEM, "pinned mask buffer"));
     *out = x;
@@ -234,108 +237,120 @@ int sta_apply_edits(sta_ctx *x, const sta_edit *edits, int64_t n_edits, void *st
     if (n_edits < 0 || (n_edits > 0 && !edits)) return fail(STA_EINVAL, "bad edit list");
     if (n_edits > (INT32_MAX / 32)) return fail(STA_ERANGE, "too many edits in one call");
     cudaStream_t s = (cudaStream_t)stream;
-    // validate against the host mirror; `seen` is all zero at rest
-    int64_t bad = -1;
-    std::string why;
-    int64_t m = 0;
-    for (int64_t e = 0; e < n_edits && bad < 0; ++e) {
-        const sta_edit &E = edits[e];
-        if (E.op < 0 || E.op > 2) { bad = e; why = "bad op"; break; }
-        if (E.tet < 0 || E.tet >= c->T) { bad = e; why = "tet out of range"; break; }
-        if (c->seen[E.tet]) { bad = e; why = "tet named twice"; break; }
-        c->seen[E.tet] = 1;
-        if (E.op == STA_DEACTIVATE && !c->host_mask[E.tet]) { bad = e; why = "deactivating an inactive tet"; }
-        if (E.op == STA_ACTIVATE && c->host_mask[E.tet]) { bad = e; why = "activating an active tet"; }
-        if (E.op == STA_SWAP) {
-            if (E.tet2 < 0 || E.tet2 >= c->T) { bad = e; why = "tet2 out of range"; break; }
-            if (c->seen[E.tet2]) { bad = e; why = "tet2 named twice"; break; }
-            c->seen[E.tet2] = 1;
-            if (!c->host_mask[E.tet] || c->host_mask[E.tet2]) { bad = e; why = "swap needs an active tet and an inactive tet2"; }
-            ++m;
-        }
-        ++m;
-    }
-    for (int64_t e = 0; e < n_edits; ++e) {  // reset scratch
-        if (edits[e].tet >= 0 && edits[e].tet < c->T) c->seen[edits[e].tet] = 0;
-        if (edits[e].op == STA_SWAP && edits[e].tet2 >= 0 && edits[e].tet2 < c->T)
-            c->seen[edits[e].tet2] = 0;
-    }
-    if (bad >= 0) return fail(STA_EINVAL, "edit " + std::to_string(bad) + ": " + why);
+    int64_t m = n_edits;  // edited tetrahedra: a swap edits two
+    for (int64_t e = 0; e < n_edits; ++e) m += edits[e].op == STA_SWAP;
 
+    // the frame block to stage into: the graph's (fixed) or the context's (grown on demand)
     const bool use_graph = c->graph_on && m <= c->gcap;
-    int32_t *stage = nullptr;
+    FrameHeader *h = nullptr, *d = nullptr;
     if (use_graph) {
         if (c->g_pending) {
             STA_CUDA_TRY(cudaEventSynchronize(c->g_h2d));
             c->g_pending = false;
         }
-        stage = c->h_gedit;
-    }
-    if (!use_graph && m > c->edit_cap) {
+        h = c->h_gframe;
+        d = c->d_gframe;
+    } else {
         STA_TRY(wait_staging(x));
-        int64_t cap = m < 1024 ? 1024 : m + m / 2;
-        if (c->h_edited) cudaFreeHost(c->h_edited);
-        c->h_edited = nullptr;
-        if (c->d_edited) {
-            cudaFree(c->d_edited);  // implicit device synchronisation
-            c->device_bytes -= (int64_t)sizeof(int32_t) * c->edit_cap;
+        if (m > c->edit_cap || !c->h_frame) {
+            const int64_t cap = m < 1024 ? 1024 : m + m / 2;
+            if (c->h_frame) cudaFreeHost(c->h_frame);
+            c->h_frame = nullptr;
+            if (c->d_frame) {
+                if (c->last_counters == frame_counters(c->d_frame)) {
+                    STA_CUDA_TRY(cudaMemcpyAsync(c->counters + 1, c->last_counters + 1,
+                                                 3 * sizeof(unsigned long long),
+                                                 cudaMemcpyDeviceToDevice, s));
+                    c->last_counters = c->counters;
+                }
+                cudaFree(c->d_frame);  // implicit device synchronisation
+                c->device_bytes -= (int64_t)frame_bytes(c->edit_cap);
+            }
+            c->d_frame = nullptr;
+            c->edit_cap = 0;
+            if (cudaMallocHost((void **)&c->h_frame, frame_bytes(cap)) != cudaSuccess)
+                return fail(STA_ENOMEM, "pinned edit buffer");
+            if (cudaMalloc((void **)&c->d_frame, frame_bytes(cap)) != cudaSuccess)
+                return fail(STA_ENOMEM, "device edit buffer");
+            c->device_bytes += (int64_t)frame_bytes(cap);
+            c->edit_cap = cap;
         }
-        c->d_edited = nullptr;
-        c->edit_cap = 0;
-        if (cudaMallocHost((void **)&c->h_edited, sizeof(int32_t) * cap) != cudaSuccess)
-            return fail(STA_ENOMEM, "pinned edit buffer");
-        if (cudaMalloc((void **)&c->d_edited, sizeof(int32_t) * cap) != cudaSuccess)
-            return fail(STA_ENOMEM, "device edit buffer");
-        c->device_bytes += (int64_t)sizeof(int32_t) * cap;
-        c->edit_cap = cap;
+        h = c->h_frame;
+        d = c->d_frame;
     }
-    if (!use_graph) {
-        STA_TRY(wait_staging(x));
-        stage = c->h_edited;
+
+    // one pass: validate each edit against the host mirror of the mask, stage it and apply it
+    // to the mirror; on a bad edit, undo the mirror changes made so far and change nothing
+    if (++c->stamp_gen == 0) {  // stamps wrapped: clear them
+        std::fill(c->stamp.begin(), c->stamp.end(), 0u);
+        c->stamp_gen = 1;
     }
-    int64_t k = 0;
-    for (int64_t e = 0; e < n_edits; ++e) {
+    const uint32_t gen = c->stamp_gen;
+    uint32_t *stamp = c->stamp.data();
+    uint8_t *hm = c->host_mask.data();
+    int32_t *stage = frame_edited(h);
+    int64_t k = 0, e = 0;
+    const char *why = nullptr;
+    for (; e < n_edits; ++e) {
         const sta_edit &E = edits[e];
+        if (E.op < 0 || E.op > 2) { why = "bad op"; break; }
+        if (E.tet < 0 || E.tet >= c->T) { why = "tet out of range"; break; }
+        if (stamp[E.tet] == gen) { why = "tet named twice"; break; }
         if (E.op == STA_DEACTIVATE) {
+            if (!hm[E.tet]) { why = "deactivating an inactive tet"; break; }
+            stamp[E.tet] = gen;
             stage[k++] = E.tet;
-            c->host_mask[E.tet] = 0;
+            hm[E.tet] = 0;
         } else if (E.op == STA_ACTIVATE) {
+            if (hm[E.tet]) { why = "activating an active tet"; break; }
+            stamp[E.tet] = gen;
             stage[k++] = (int32_t)((uint32_t)E.tet | 0x80000000u);
-            c->host_mask[E.tet] = 1;
+            hm[E.tet] = 1;
         } else {
+            if (E.tet2 < 0 || E.tet2 >= c->T) { why = "tet2 out of range"; break; }
+            if (E.tet2 == E.tet || stamp[E.tet2] == gen) { why = "tet2 named twice"; break; }
+            if (!hm[E.tet] || hm[E.tet2]) { why = "swap needs an active tet and an inactive tet2"; break; }
+            stamp[E.tet] = gen;
+            stamp[E.tet2] = gen;
             stage[k++] = E.tet;
             stage[k++] = (int32_t)((uint32_t)E.tet2 | 0x80000000u);
-            c->host_mask[E.tet] = 0;
-            c->host_mask[E.tet2] = 1;
+            hm[E.tet] = 0;
+            hm[E.tet2] = 1;
         }
     }
+    if (why) {
+        for (int64_t r = 0; r < e; ++r) {  // undo (each tet appears once, so this is exact)
+            const sta_edit &E = edits[r];
+            if (E.op == STA_DEACTIVATE) hm[E.tet] = 1;
+            else if (E.op == STA_ACTIVATE) hm[E.tet] = 0;
+            else { hm[E.tet] = 1; hm[E.tet2] = 0; }
+        }
+        return fail(STA_EINVAL, "edit " + std::to_string(e) + ": " + why);
+    }
+
+    // header (count, zeroed counters) and list go to the device in one copy
+    h->m = m;
+    h->cnt[0] = h->cnt[1] = h->cnt[2] = 0ull;
     c->last_edited = m;
-    if (use_graph) {  // fixed buffers, one captured launch sequence for every frame
-        *c->h_gcount = m;
-        if (m > 0)
-            STA_CUDA_TRY(cudaMemcpyAsync(c->d_gedit, c->h_gedit, sizeof(int32_t) * m,
-                                         cudaMemcpyHostToDevice, s));
-        STA_CUDA_TRY(cudaMemcpyAsync(c->d_gcount, c->h_gcount, sizeof(int64_t),
-                                     cudaMemcpyHostToDevice, s));
+    c->last_counters = frame_counters(d);
+    STA_CUDA_TRY(cudaMemcpyAsync(d, h, frame_bytes(m), cudaMemcpyHostToDevice, s));
+    if (use_graph) {  // one captured launch sequence for every frame
         STA_CUDA_TRY(cudaEventRecord(c->g_h2d, s));
         c->g_pending = true;
         STA_CUDA_TRY(cudaGraphLaunch(c->g_stream, s));
         return STA_OK;
     }
-    if (m > 0) {
-        STA_CUDA_TRY(cudaMemcpyAsync(c->d_edited, c->h_edited, sizeof(int32_t) * m,
-                                     cudaMemcpyHostToDevice, s));
-        STA_CUDA_TRY(cudaEventRecord(x->h2d_done, s));
-        x->h2d_pending = true;
-    }
-    return launch_stream(c, m, s);
+    STA_CUDA_TRY(cudaEventRecord(x->h2d_done, s));
+    x->h2d_pending = true;
+    if (m == 0) return STA_OK;  // the copy has zeroed the frame's counters
+    return launch_stream_frame(c, d, m, s);
 }
 
 int sta_last_touched(sta_ctx *x, int64_t *touched_nnz, void *stream) {
     if (!x || !touched_nnz) return fail(STA_EINVAL, "NULL argument");
     unsigned long long v = 0;
     cudaStream_t s = (cudaStream_t)stream;
-    STA_CUDA_TRY(cudaMemcpyAsync(&v, x->c.counters + 3, sizeof v, cudaMemcpyDeviceToHost, s));
+    STA_CUDA_TRY(cudaMemcpyAsync(&v, x->c.last_counters + 3, sizeof v, cudaMemcpyDeviceToHost, s));
     STA_CUDA_TRY(cudaStreamSynchronize(s));
     *touched_nnz = (int64_t)v;
     return STA_OK;

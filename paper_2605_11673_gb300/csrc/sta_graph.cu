@@ -11,14 +11,11 @@ void graph_release(Ctx *c) {
     if (c->g_stream) cudaGraphExecDestroy(c->g_stream);
     if (c->g_refold) cudaGraphExecDestroy(c->g_refold);
     if (c->g_rebuild) cudaGraphExecDestroy(c->g_rebuild);
-    if (c->d_gedit) cudaFree(c->d_gedit);
-    if (c->d_gcount) cudaFree(c->d_gcount);
-    if (c->h_gedit) cudaFreeHost(c->h_gedit);
-    if (c->h_gcount) cudaFreeHost(c->h_gcount);
+    if (c->d_gframe) cudaFree(c->d_gframe);
+    if (c->h_gframe) cudaFreeHost(c->h_gframe);
     if (c->g_h2d) cudaEventDestroy(c->g_h2d);
     c->g_stream = c->g_refold = c->g_rebuild = nullptr;
-    c->d_gedit = c->h_gedit = nullptr;
-    c->d_gcount = c->h_gcount = nullptr;
+    c->d_gframe = c->h_gframe = nullptr;
     c->g_h2d = nullptr;
     c->graph_on = false;
     c->g_pending = false;
@@ -26,6 +23,16 @@ void graph_release(Ctx *c) {
 }
 
 namespace {
+
+// Keep the last frame's touched counts when the graph staging goes away (sta_last_touched).
+int keep_last_counters(Ctx *c) {
+    if (c->d_gframe && c->last_counters == frame_counters(c->d_gframe)) {
+        STA_CUDA_TRY(cudaMemcpy(c->counters + 1, c->last_counters + 1,
+                                3 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice));
+        c->last_counters = c->counters;
+    }
+    return STA_OK;
+}
 
 template <typename F> int capture(cudaStream_t cs, F &&body, cudaGraphExec_t *exec) {
     cudaGraph_t g = nullptr;
@@ -55,6 +62,7 @@ extern "C" int sta_graph_enable(sta_ctx *x, int64_t max_edited, void *stream) {
         return fail(STA_EINVAL, "max_edited must be in [1, 2^26]");
     Ctx *c = &x->c;
     STA_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    STA_TRY(keep_last_counters(c));
     graph_release(c);
     int rc = STA_OK;
     cudaStream_t cs = nullptr;
@@ -63,17 +71,15 @@ extern "C" int sta_graph_enable(sta_ctx *x, int64_t max_edited, void *stream) {
         graph_release(c);
         return code;
     };
-    if (cudaMalloc((void **)&c->d_gedit, sizeof(int32_t) * max_edited) != cudaSuccess ||
-        cudaMalloc((void **)&c->d_gcount, sizeof(int64_t)) != cudaSuccess ||
-        cudaMallocHost((void **)&c->h_gedit, sizeof(int32_t) * max_edited) != cudaSuccess ||
-        cudaMallocHost((void **)&c->h_gcount, sizeof(int64_t)) != cudaSuccess)
+    if (cudaMalloc((void **)&c->d_gframe, frame_bytes(max_edited)) != cudaSuccess ||
+        cudaMallocHost((void **)&c->h_gframe, frame_bytes(max_edited)) != cudaSuccess)
         return bail(fail(STA_ENOMEM, "graph staging buffers"));
     if (cudaEventCreateWithFlags(&c->g_h2d, cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(STA_ECUDA, "graph stream/event"));
     c->gcap = max_edited;
     if ((rc = capture(cs, [&](cudaStream_t s) {
-             return launch_stream_devcount(c, c->d_gedit, c->d_gcount, c->gcap, s);
+             return launch_stream_frame(c, c->d_gframe, c->gcap, s);
          }, &c->g_stream)))
         return bail(rc);
     if ((rc = capture(cs, [&](cudaStream_t s) { return launch_rebuild(c, s); }, &c->g_refold)))
@@ -91,6 +97,7 @@ extern "C" int sta_graph_enable(sta_ctx *x, int64_t max_edited, void *stream) {
 extern "C" int sta_graph_disable(sta_ctx *x, void *stream) {
     if (!x) return fail(STA_EINVAL, "ctx is NULL");
     STA_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    STA_TRY(keep_last_counters(&x->c));
     graph_release(&x->c);
     return STA_OK;
 }

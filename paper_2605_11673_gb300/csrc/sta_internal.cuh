@@ -87,6 +87,21 @@ __host__ __device__ inline int slot_of(int la, int lb) {  // unordered local pai
 constexpr int FOLD_TASKS_DIAG = 6;
 constexpr int FOLD_TASKS_PAIR = 9;
 
+// Frame block: what one streaming frame moves to the device in a single transfer -- the
+// edited count, the frame's counters (zeroed by the host) and the edited list (tet id | new
+// state << 31) right after the header.
+struct FrameHeader {
+    int64_t m;                     // edited tetrahedra
+    unsigned long long cnt[3];     // touched units, unused, touched CSR entries
+};
+static_assert(sizeof(FrameHeader) == 32, "frame header layout");
+// counter view with the indices of Ctx::counters: [1] touched units, [3] touched entries
+inline unsigned long long *frame_counters(FrameHeader *f) {
+    return reinterpret_cast<unsigned long long *>(f);
+}
+inline int32_t *frame_edited(FrameHeader *f) { return reinterpret_cast<int32_t *>(f + 1); }
+inline size_t frame_bytes(int64_t m) { return sizeof(FrameHeader) + sizeof(int32_t) * (size_t)m; }
+
 // ------------------------------------------------------------------------------------
 // Context
 // ------------------------------------------------------------------------------------
@@ -136,18 +151,19 @@ struct Ctx {
     // [0] bad elements, [1] touched units, [2] first bad element, [3] touched CSR entries
     unsigned long long *counters = nullptr;
 
-    // streaming staging
-    int32_t *d_edited = nullptr;  // capacity: edited tetrahedra (id | new state << 31)
-    int32_t *h_edited = nullptr;  // pinned
-    int64_t edit_cap = 0;
+    // streaming staging: one frame block on the device and its pinned host copy
+    FrameHeader *d_frame = nullptr, *h_frame = nullptr;
+    int64_t edit_cap = 0;         // edited tetrahedra a frame block holds
     int64_t last_edited = 0;
+    unsigned long long *last_counters = nullptr;  // device counters of the last frame
+    std::vector<uint32_t> stamp;  // host: edit-list duplicate check, stamp_gen = "seen"
+    uint32_t stamp_gen = 0;
 
     // CUDA-graph mode (sta_graph_enable): captured frame sequences and fixed staging
     bool graph_on = false;
     cudaGraphExec_t g_stream = nullptr, g_refold = nullptr, g_rebuild = nullptr;
     int64_t gcap = 0;
-    int32_t *d_gedit = nullptr, *h_gedit = nullptr;  // device / pinned, gcap entries
-    int64_t *d_gcount = nullptr, *h_gcount = nullptr;
+    FrameHeader *d_gframe = nullptr, *h_gframe = nullptr;  // device / pinned, gcap entries
     cudaEvent_t g_h2d = nullptr;
     bool g_pending = false;
 
@@ -190,12 +206,10 @@ int launch_expand_elements(Ctx *c, const int32_t *ids, int64_t n, double *out, c
 int launch_adjoint(Ctx *c, const double *gval, double *dE, double *dnu, double *dX, cudaStream_t s);
 int launch_spmv(Ctx *c, const double *val, const double *x, double *y, cudaStream_t s);
 int launch_rebuild(Ctx *c, cudaStream_t s);                      // sta_assemble.cu
-int launch_stream(Ctx *c, int64_t n_edited, cudaStream_t s);
+int launch_stream_frame(Ctx *c, FrameHeader *frame, int64_t cap, cudaStream_t s);  // sta_stream.cu
 int launch_mask_bits(Ctx *c, cudaStream_t s);                    // codes <- mask
 int launch_stream_scratch(Ctx *c, int64_t m, const int32_t *d_edited, int32_t *touched,
                           unsigned long long *counters, cudaStream_t s);
-int launch_stream_devcount(Ctx *c, const int32_t *d_edited, const int64_t *d_m, int64_t cap,
-                           cudaStream_t s);
 
 int create_impl(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
                 const double *young, const double *poisson, const sta_options *opt, void *stream,
