@@ -407,13 +407,14 @@ struct Scratch {
 // have lists of equal length (the tile waits for its longest), and a window's values are
 // written close together in time.  Any order gives the same values: each unit folds its own
 // list in its own order.
-// Tile record: {first unit, entry offset in it | diagonal << 4 | entries in the tile << 5}.
+// Tile record: {first unit, entry offset in it | diagonal << 4 | entries in the tile << 5,
+// first code of the tile's units, end of their codes}.
 #ifndef STA_UNIT_WINDOW
 #define STA_UNIT_WINDOW 2048
 #endif
 
 void unit_order(const std::vector<int32_t> &cnt, const std::vector<int32_t> &umin,
-                const std::vector<uint8_t> &diag, std::vector<int32_t> &rn, std::vector<int2> &tiles) {
+                const std::vector<uint8_t> &diag, std::vector<int32_t> &rn, std::vector<int4> &tiles) {
     const int64_t m = (int64_t)cnt.size();
     const int64_t W = STA_UNIT_WINDOW > 1 ? STA_UNIT_WINDOW : 1;
     std::vector<int32_t> order;
@@ -433,12 +434,22 @@ void unit_order(const std::vector<int32_t> &cnt, const std::vector<int32_t> &umi
             const int64_t nent = per * (int64_t)(order.size() - first);
             for (int64_t e = 0; e < nent; e += 32) {
                 const int64_t k = std::min<int64_t>(32, nent - e);
-                tiles.push_back(make_int2((int32_t)(first + e / per),
-                                          (int32_t)(e % per) | cls << 4 | (int32_t)k << 5));
+                // code range filled in below, once every unit's list position is known
+                tiles.push_back(make_int4((int32_t)(first + e / per),
+                                          (int32_t)(e % per) | cls << 4 | (int32_t)k << 5,
+                                          (int32_t)(first + (e + k - 1) / per), 0));
             }
         }
     }
     for (int64_t k = 0; k < m; ++k) rn[order[k]] = (int32_t)k;
+    // lists are stored in new-id order: unit k's codes start at the sum of the earlier counts
+    std::vector<int64_t> cs(m + 1, 0);
+    for (int64_t k = 0; k < m; ++k) cs[k + 1] = cs[k] + cnt[order[k]];
+    for (auto &t : tiles) {
+        const int64_t last = t.z;
+        t.z = (int32_t)cs[t.x];
+        t.w = (int32_t)cs[last + 1];
+    }
 }
 
 }  // namespace
@@ -535,7 +546,7 @@ int build_pattern(Ctx *c, cudaStream_t s) {
                                                       udiag);
         std::vector<int32_t> hcnt(nunits), hmin(nunits), rn;
         std::vector<uint8_t> hdiag(nunits);
-        std::vector<int2> htiles;
+        std::vector<int4> htiles;
         k_fill_i32<<<grid_for(nunits), TPB, 0, s>>>(rn_dev, nunits, INT32_MAX);
         k_unit_min_tet<<<grid_for(10 * T), TPB, 0, s>>>(c->tunit, T, rn_dev);
         STA_CUDA_TRY(cudaMemcpyAsync(hmin.data(), rn_dev, sizeof(int32_t) * nunits,
@@ -547,7 +558,7 @@ int build_pattern(Ctx *c, cudaStream_t s) {
         unit_order(hcnt, hmin, hdiag, rn, htiles);
         c->ntiles = (int64_t)htiles.size();
         STA_TRY(dev_alloc(c, &c->ftile, c->ntiles));
-        STA_CUDA_TRY(cudaMemcpyAsync(c->ftile, htiles.data(), sizeof(int2) * c->ntiles,
+        STA_CUDA_TRY(cudaMemcpyAsync(c->ftile, htiles.data(), sizeof(int4) * c->ntiles,
                                      cudaMemcpyHostToDevice, s));
         STA_CUDA_TRY(cudaMemcpyAsync(rn_dev, rn.data(), sizeof(int32_t) * nunits,
                                      cudaMemcpyHostToDevice, s));

@@ -132,7 +132,8 @@ struct Ctx {
     // symmetric), so one fold per unit writes both blocks.
     int64_t nunits = 0;
     int64_t ntiles = 0;
-    int2 *ftile = nullptr;         // ntiles: rebuild fold tiles {first unit, q0 | diag << 4 | entries << 5}
+    int4 *ftile = nullptr;         // ntiles: rebuild fold tiles {first unit, q0 | diag << 4 |
+                                   //   entries << 5, code range of the tile's units}
     int4 *bmeta = nullptr;         // nunits: {value offset of (a,b), rs_a << 1 | diagonal, c0, c1}
     int2 *bmirror = nullptr;       // nunits: {value offset of (b,a), rs_b}
     int32_t *ccode = nullptr;      // 10 T: unit contributor words (word_offset), ascending tet id

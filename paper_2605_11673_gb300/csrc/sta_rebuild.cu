@@ -9,13 +9,13 @@ namespace {
 // ------------------------------------------------------------------------------------------
 // Flat entry-parallel rebuild.  Every fold entry of the pattern gets a lane: 6 per diagonal
 // unit, 9 per off-diagonal unit.  A warp tile is 32 consecutive entries of units of one kind
-// (tile records built at create: first unit, entry offset, kind, entry count); its units (up to
-// 7) have contiguous contributor codes.  The warp compacts the active codes of that range into
+// (tile records built at create: first unit, entry offset, kind, entry count, and the code
+// range of its units (up to 7), which is contiguous).  The warp compacts the active codes of that range into
 // shared memory with ballots (list order kept, so each unit's active codes form one segment),
 // each lane locates its unit's segment from the same ballots, and every FP64 add instruction
 // then advances up to 32 folds.  Units are ordered so that a tile's lists have equal length.
 //
-// Each tile needs three dependent loads before its first add (tile record -> unit record ->
+// Each tile needs two dependent loads before its first add (tile record -> unit records and
 // codes), so the persistent warps run them as a software pipeline: while tile w folds, the
 // first code chunk of tile w+W, the unit records of tile w+2W and the tile record of tile w+3W
 // are in flight (W = warps in the grid).  Operands, order and operations are those of
@@ -31,7 +31,7 @@ struct FlatLane {
     int nv;     // entries in the tile (lanes 0 .. nv-1 valid)
 };
 
-__device__ __forceinline__ FlatLane flat_lane(int2 r, int lane) {
+__device__ __forceinline__ FlatLane flat_lane(int4 r, int lane) {
     FlatLane L;
     L.dgl = (r.y >> 4) & 1;
     L.nv = r.y >> 5;
@@ -43,13 +43,13 @@ __device__ __forceinline__ FlatLane flat_lane(int2 r, int lane) {
     return L;
 }
 
-__device__ __forceinline__ int2 flat_rec(const int2 *__restrict__ trec, int64_t w, int64_t ntiles) {
-    return w < ntiles ? __ldg(trec + w) : make_int2(0, 0);  // nv = 0: no valid lane
+__device__ __forceinline__ int4 flat_rec(const int4 *__restrict__ trec, int64_t w, int64_t ntiles) {
+    return w < ntiles ? __ldg(trec + w) : make_int4(0, 0, 0, 0);  // no valid lane, no codes
 }
 
 template <int WARPS>  // warps per CTA: 2, 4 or 8 (at most 64 registers a thread)
 __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS)
-k_fold_flat(FoldArgs A, const int2 *__restrict__ trec, int64_t ntiles) {
+k_fold_flat(FoldArgs A, const int4 *__restrict__ trec, int64_t ntiles) {
     __shared__ int32_t sbuf[WARPS][FLAT_CAP];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -62,26 +62,24 @@ k_fold_flat(FoldArgs A, const int2 *__restrict__ trec, int64_t ntiles) {
 
     // pipeline prologue: records of tiles w, w+W, w+2W; unit records of w, w+W; codes of w
     int64_t w = warp;
-    int2 r0 = flat_rec(trec, w, ntiles), r1 = flat_rec(trec, w + W, ntiles),
-         r2 = flat_rec(trec, w + 2 * W, ntiles);
+    const int4 r0 = flat_rec(trec, w, ntiles), r1 = flat_rec(trec, w + W, ntiles);
+    int4 r2 = flat_rec(trec, w + 2 * W, ntiles);
     FlatLane L = flat_lane(r0, lane);
     int4 bm0 = L.valid ? __ldg(A.bmeta + L.u) : Z4;
     int2 mir0 = L.valid && !L.dgl ? __ldg(A.bmirror + L.u) : make_int2(0, 0);
     FlatLane L1 = flat_lane(r1, lane);
     int4 bm1 = L1.valid ? __ldg(A.bmeta + L1.u) : Z4;
-    int32_t cr0 = __shfl_sync(FULL, bm0.z, 0), cr1 = __shfl_sync(FULL, bm0.w, L.nv > 0 ? L.nv - 1 : 0);
-    if (L.nv == 0) cr0 = cr1 = 0;
+    int32_t cr0 = r0.z, cr1 = r0.w;  // the tile's code range
     int32_t code0 = cr0 + lane < cr1 ? __ldg(A.ccode + cr0 + lane) : 0;
+    int32_t nr0 = r1.z, nr1 = r1.w;
 
     for (; w < ntiles; w += W) {  // warp-uniform
         // stage 0: tile record of w + 3W
-        const int2 r3 = flat_rec(trec, w + 3 * W, ntiles);
+        const int4 r3 = flat_rec(trec, w + 3 * W, ntiles);
         // stage 1: unit records of w + 2W
         const FlatLane L2 = flat_lane(r2, lane);
         const int4 bm2 = L2.valid ? __ldg(A.bmeta + L2.u) : Z4;
         // stage 2: first code chunk and mirror records of w + W
-        int32_t nr0 = __shfl_sync(FULL, bm1.z, 0), nr1 = __shfl_sync(FULL, bm1.w, L1.nv > 0 ? L1.nv - 1 : 0);
-        if (L1.nv == 0) nr0 = nr1 = 0;
         const int32_t code1 = nr0 + lane < nr1 ? __ldg(A.ccode + nr0 + lane) : 0;
         const int2 mir1 = L1.valid && !L1.dgl ? __ldg(A.bmirror + L1.u) : make_int2(0, 0);
 
@@ -174,6 +172,8 @@ k_fold_flat(FoldArgs A, const int2 *__restrict__ trec, int64_t ntiles) {
         code0 = code1;
         L1 = L2;
         bm1 = bm2;
+        nr0 = r2.z;
+        nr1 = r2.w;
         r2 = r3;
     }
 }
