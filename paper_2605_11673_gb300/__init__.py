@@ -104,10 +104,16 @@ def _check(status: int) -> None:
         raise StaError(status, load_library().sta_last_error().decode())
 
 
+_cuda_ok = None
+
+
 def _stream_handle(stream) -> int:
+    global _cuda_ok
     if stream is None:
         import torch
-        if not torch.cuda.is_available():
+        if _cuda_ok is None:
+            _cuda_ok = torch.cuda.is_available()
+        if not _cuda_ok:
             return 0
         return torch.cuda.current_stream().cuda_stream
     if isinstance(stream, int):

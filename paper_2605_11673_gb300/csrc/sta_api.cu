@@ -281,17 +281,28 @@ int sta_apply_edits(sta_ctx *x, const sta_edit *edits, int64_t n_edits, void *st
 
     // one pass: validate each edit against the host mirror of the mask, stage it and apply it
     // to the mirror; on a bad edit, undo the mirror changes made so far and change nothing
-    if (++c->stamp_gen == 0) {  // stamps wrapped: clear them
-        std::fill(c->stamp.begin(), c->stamp.end(), 0u);
+    if (++c->stamp_gen == 0) {  // stamps wrapped (every 255 calls): clear them
+        std::fill(c->stamp.begin(), c->stamp.end(), (uint8_t)0);
         c->stamp_gen = 1;
     }
-    const uint32_t gen = c->stamp_gen;
-    uint32_t *stamp = c->stamp.data();
+    const uint8_t gen = c->stamp_gen;
+    uint8_t *stamp = c->stamp.data();
     uint8_t *hm = c->host_mask.data();
     int32_t *stage = frame_edited(h);
     int64_t k = 0, e = 0;
     const char *why = nullptr;
     for (; e < n_edits; ++e) {
+        if (e + 16 < n_edits) {  // the per-tet state is accessed at random: fetch it ahead
+            const sta_edit &F = edits[e + 16];
+            if (F.tet >= 0 && F.tet < c->T) {
+                __builtin_prefetch(stamp + F.tet, 1);
+                __builtin_prefetch(hm + F.tet, 1);
+            }
+            if (F.op == STA_SWAP && F.tet2 >= 0 && F.tet2 < c->T) {
+                __builtin_prefetch(stamp + F.tet2, 1);
+                __builtin_prefetch(hm + F.tet2, 1);
+            }
+        }
         const sta_edit &E = edits[e];
         if (E.op < 0 || E.op > 2) { why = "bad op"; break; }
         if (E.tet < 0 || E.tet >= c->T) { why = "tet out of range"; break; }

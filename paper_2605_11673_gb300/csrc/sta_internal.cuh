@@ -157,8 +157,8 @@ struct Ctx {
     int64_t edit_cap = 0;         // edited tetrahedra a frame block holds
     int64_t last_edited = 0;
     unsigned long long *last_counters = nullptr;  // device counters of the last frame
-    std::vector<uint32_t> stamp;  // host: edit-list duplicate check, stamp_gen = "seen"
-    uint32_t stamp_gen = 0;
+    std::vector<uint8_t> stamp;   // host: edit-list duplicate check, stamp_gen = "seen"; one
+    uint8_t stamp_gen = 0;        // byte per tet keeps it and the mask mirror cache-resident
 
     // CUDA-graph mode (sta_graph_enable): captured frame sequences and fixed staging
     bool graph_on = false;
