@@ -141,8 +141,11 @@ __global__ void k_stream_claim(const int32_t *__restrict__ edited, int64_t m,
             const int s = (int)(i % 10);
             if (s == 0) mask[t] = (uint8_t)on;
             const int32_t slot = cslot[10 * (int64_t)t + s];
-            ccode[slot] = (int32_t)(((uint32_t)ccode[slot] & ~CODE_ACTIVE) | (on << 31));
             u = tunit[10 * (int64_t)t + s];
+            // the word is (t, s)'s run offset | activity: written without reading it back
+            const uint32_t off = (uint32_t)t * KE_STRIDE +
+                                 (s < 4 ? ke_diag_off(s) : ke_off_off(slot_la(s), slot_lb(s)));
+            ccode[slot] = (int32_t)(off | (on << 31));
             diag = s < 4;
             won = atomicCAS(&owner[u], INT32_MAX, 0) == INT32_MAX;
         }
