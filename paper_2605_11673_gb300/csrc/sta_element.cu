@@ -103,35 +103,67 @@ __device__ __forceinline__ bool element_record(double4_32a x0, double4_32a x1, d
 // One thread per tetrahedron; a warp stages its 32 records in shared memory and writes
 // each record of an updated tetrahedron as one contiguous 624-byte run (coalesced).
 // active_only: tetrahedra with mask == 0 keep their cached record untouched.
+// Active tetrahedra, unordered (warp-aggregated append): the FP64 kernels below run over this
+// list so that every FP64 instruction carries full lanes when part of the superset is inactive.
+// With dE non-null, the adjoint outputs of inactive tets are zeroed on the way.
+__global__ void k_active_list(const uint8_t *__restrict__ mask, int64_t T, int32_t *__restrict__ list,
+                              unsigned long long *count, double *__restrict__ dE,
+                              double *__restrict__ dnu, double *__restrict__ dXe) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < T; i0 += stride) {  // warp-uniform
+        const int64_t t = i0 + threadIdx.x;
+        const bool act = t < T && mask[t];
+        if (dE && t < T && !act) {
+            dE[t] = 0.0;
+            dnu[t] = 0.0;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) dXe[12 * t + k] = 0.0;
+        }
+        const unsigned m = __ballot_sync(FULL, act);
+        unsigned long long base = 0;
+        if (lane == 0 && m) base = atomicAdd(count, (unsigned long long)__popc(m));
+        base = __shfl_sync(FULL, base, 0);
+        if (act) list[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)t;
+    }
+}
+
+// Element records of tets list[0 .. *count) (or of all tets 0 .. T-1 when list is null), one
+// per thread, staged per warp in shared memory and written out as contiguous records.
 __global__ void __launch_bounds__(EL_TPB)
 k_elements(const double4_32a *__restrict__ X, const int4 *__restrict__ tets,
-           const double2 *__restrict__ mat, const uint8_t *__restrict__ mask, int active_only,
-           int64_t T, double *__restrict__ Ke, unsigned long long *bad) {
+           const double2 *__restrict__ mat, const int32_t *__restrict__ list,
+           const unsigned long long *__restrict__ count, int64_t T, double *__restrict__ Ke,
+           unsigned long long *bad) {
     extern __shared__ double smem[];
+    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double *wrec = smem + (size_t)wid * 32 * KE_STRIDE;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < T;
-         base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = base + threadIdx.x;  // warp wid covers [base + 32 wid, +32)
-        bool doit = t < T && (!active_only || mask[t]);
+    const int64_t n = list ? (int64_t)*count : T;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {  // block-uniform
+        const int64_t i = base + threadIdx.x;
+        const bool doit = i < n;
+        const int32_t t = doit ? (list ? list[i] : (int32_t)i) : 0;
         if (doit) {
-            int4 q = tets[t];
-            double2 m = mat[t];
-            bool ok = element_record(X[q.x], X[q.y], X[q.z], X[q.w], m.x, m.y, q,
-                                     wrec + (size_t)lane * KE_STRIDE);
+            const int4 q = tets[t];
+            const double2 m = mat[t];
+            const bool ok = element_record(X[q.x], X[q.y], X[q.z], X[q.w], m.x, m.y, q,
+                                           wrec + (size_t)lane * KE_STRIDE);
             if (!ok) {
                 atomicAdd(&bad[0], 1ull);
                 atomicMin(&bad[2], (unsigned long long)t);
             }
         }
-        unsigned todo = __ballot_sync(0xffffffffu, doit);
+        unsigned todo = __ballot_sync(FULL, doit);
         __syncwarp();
-        const int64_t t0 = base + 32 * wid;
-        while (todo) {
-            int r = __ffs(todo) - 1;
+        while (todo) {  // coalesced copy-out, one record at a time
+            const int r = __ffs(todo) - 1;
             todo &= todo - 1;
+            const int32_t tr = __shfl_sync(FULL, t, r);
             const double2 *src = reinterpret_cast<const double2 *>(wrec + (size_t)r * KE_STRIDE);
-            double2 *dst = reinterpret_cast<double2 *>(Ke + (size_t)(t0 + r) * KE_STRIDE);
+            double2 *dst = reinterpret_cast<double2 *>(Ke + (size_t)tr * KE_STRIDE);
             for (int k = lane; k < KE_STRIDE / 2; k += 32) dst[k] = src[k];
         }
         __syncwarp();
@@ -151,19 +183,14 @@ k_elements(const double4_32a *__restrict__ X, const int4 *__restrict__ tets,
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(128)
 k_adjoint(const double4_32a *__restrict__ X, const int4 *__restrict__ tets,
-          const double2 *__restrict__ mat, const uint8_t *__restrict__ mask,
-          const int32_t *__restrict__ tblk, const int2 *__restrict__ boff,
-          const double *__restrict__ gval, int64_t T, double *__restrict__ dE,
-          double *__restrict__ dnu, double *__restrict__ dXe) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        if (!mask[t]) {
-            dE[t] = 0.0;
-            dnu[t] = 0.0;
-#pragma unroll
-            for (int k = 0; k < 12; ++k) dXe[12 * t + k] = 0.0;
-            continue;
-        }
+          const double2 *__restrict__ mat, const int32_t *__restrict__ list,
+          const unsigned long long *__restrict__ count, const int32_t *__restrict__ tblk,
+          const int2 *__restrict__ boff, const double *__restrict__ gval,
+          double *__restrict__ dE, double *__restrict__ dnu, double *__restrict__ dXe) {
+    const int64_t n = (int64_t)*count;  // active tets (inactive ones were zeroed beforehand)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = list[i];
         const int4 q = tets[t];
         const double4_32a x0 = X[q.x], x1 = X[q.y], x2 = X[q.z], x3 = X[q.w];
         V3 d1 = sub(x1, x0), d2 = sub(x2, x0), d3 = sub(x3, x0);
@@ -184,18 +211,30 @@ k_adjoint(const double4_32a *__restrict__ X, const int4 *__restrict__ tets,
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int m = 0; m < 3; ++m) hA[a][m] = hB[a][m] = 0.0;
+        // node pairs a <= b: for a < b the blocks (a,b) and (b,a) enter every sum through
+        // H = G_ab + G_ba^T (g_a^T G_ab g_b + g_b^T G_ba g_a = g_a^T H g_b, and likewise for
+        // SB and the h terms), so each unordered pair costs one set of products
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int2 bo = boff[tblk[16 * t + 4 * a + b]];
-                const double *G = gval + bo.x;
-                const int rs = bo.y;
+            for (int b = a; b < 4; ++b) {
                 double M[3][3];
+                {
+                    const int2 bo = boff[tblk[16 * t + 4 * a + b]];
+                    const double *G = gval + bo.x;
 #pragma unroll
-                for (int i = 0; i < 3; ++i)
+                    for (int i = 0; i < 3; ++i)
 #pragma unroll
-                    for (int j = 0; j < 3; ++j) M[i][j] = G[i * rs + j];
+                        for (int j = 0; j < 3; ++j) M[i][j] = G[i * bo.y + j];
+                }
+                if (a != b) {
+                    const int2 bo = boff[tblk[16 * t + 4 * b + a]];
+                    const double *G = gval + bo.x;
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) M[i][j] += G[j * bo.y + i];
+                }
                 const double tr = M[0][0] + M[1][1] + M[2][2];
                 double Mgb[3], Mtga[3], Mtgb[3], Mga[3];
 #pragma unroll
@@ -301,20 +340,42 @@ __global__ void k_expand(const double *__restrict__ Ke, const int4 *__restrict__
 
 }  // namespace
 
+namespace {
+
+// The unordered list of active tets (c->act_list, count in c->act_count), allocated on first use.
+int launch_active_list(Ctx *c, double *dE, double *dnu, double *dXe, cudaStream_t s) {
+    if (!c->act_list) {
+        STA_TRY(dev_alloc(c, &c->act_list, c->T));
+        STA_TRY(dev_alloc(c, &c->act_count, 1));
+    }
+    STA_CUDA_TRY(cudaMemsetAsync(c->act_count, 0, sizeof(unsigned long long), s));
+    int64_t grid = (c->T + 255) / 256;
+    const int64_t cap = (int64_t)c->num_sms * 16;
+    if (grid > cap) grid = cap;
+    k_active_list<<<(unsigned)grid, 256, 0, s>>>(c->mask, c->T, c->act_list, c->act_count, dE,
+                                                 dnu, dXe);
+    STA_CUDA_TRY(cudaGetLastError());
+    return STA_OK;
+}
+
+}  // namespace
+
 int launch_elements(Ctx *c, bool active_only, cudaStream_t s) {
     if (c->T == 0) return STA_OK;
-    size_t smem = (size_t)EL_TPB * KE_STRIDE * sizeof(double);  // 78 KB
+    size_t smem = (size_t)EL_TPB * KE_STRIDE * sizeof(double);  // 84 KB
     STA_CUDA_TRY(cudaFuncSetAttribute(k_elements, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
+    if (active_only) STA_TRY(launch_active_list(c, nullptr, nullptr, nullptr, s));
     int64_t blocks = (c->T + EL_TPB - 1) / EL_TPB;
     int per_sm = 0;
     STA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_elements, EL_TPB, smem));
     if (per_sm < 1) per_sm = 1;
     int64_t cap = (int64_t)per_sm * c->num_sms;
     if (blocks > cap) blocks = cap;
-    k_elements<<<(unsigned)blocks, EL_TPB, smem, s>>>(c->X, c->tets, c->mat, c->mask,
-                                                      active_only ? 1 : 0, c->T, c->Ke,
-                                                      c->counters);
+    k_elements<<<(unsigned)blocks, EL_TPB, smem, s>>>(c->X, c->tets, c->mat,
+                                                      active_only ? c->act_list : nullptr,
+                                                      active_only ? c->act_count : nullptr, c->T,
+                                                      c->Ke, c->counters);
     STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;
 }
@@ -323,11 +384,12 @@ int launch_adjoint(Ctx *c, const double *gval, double *dE, double *dnu, double *
                    cudaStream_t s) {
     if (!c->dXe) STA_TRY(dev_alloc(c, &c->dXe, 12 * c->T));
     if (c->T > 0) {
+        STA_TRY(launch_active_list(c, dE, dnu, c->dXe, s));
         int64_t grid = (c->T + 127) / 128;
         const int64_t cap = (int64_t)c->num_sms * 16;
         if (grid > cap) grid = cap;
-        k_adjoint<<<(unsigned)grid, 128, 0, s>>>(c->X, c->tets, c->mat, c->mask, c->tblk, c->boff,
-                                                gval, c->T, dE, dnu, c->dXe);
+        k_adjoint<<<(unsigned)grid, 128, 0, s>>>(c->X, c->tets, c->mat, c->act_list, c->act_count,
+                                                c->tblk, c->boff, gval, dE, dnu, c->dXe);
     }
     if (c->n > 0) {
         int64_t grid = (c->n + 255) / 256;

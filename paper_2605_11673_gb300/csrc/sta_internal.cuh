@@ -142,6 +142,8 @@ struct Ctx {
     int32_t *nt_ptr = nullptr;     // n + 1: node -> incident tetrahedra
     int32_t *nt_list = nullptr;    // 4 T: incident tetrahedra, ascending id
     double *dXe = nullptr;         // T x 12: per-element position gradients (adjoint, lazily)
+    int32_t *act_list = nullptr;   // T: active tets, unordered (element / adjoint kernels, lazily)
+    unsigned long long *act_count = nullptr;
 
     // state
     double *Ke = nullptr;       // T x 78 element cache
