@@ -348,13 +348,12 @@ __global__ void k_unit_slots(const int32_t *ccode, int64_t T, int32_t *cslot) {
 
 // contributor codes (t, la, lb) -> contributor words: offset of the element-cache run the
 // contributor supplies to its unit (word_offset), active bit clear
-__global__ void k_code_words(int32_t *ccode, int64_t n) {
+__global__ void k_code_words(int32_t *ccode, int64_t n, int64_t T) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         const int32_t code = ccode[k];
         const int la = (code >> 2) & 3, lb = code & 3;
-        const int off = la == lb ? ke_diag_off(la) : ke_off_off(la < lb ? la : lb, la < lb ? lb : la);
-        ccode[k] = (int32_t)((uint32_t)code_tet(code) * KE_STRIDE + off);
+        ccode[k] = (int32_t)ke_slot_at(T, code_tet(code), slot_of(la, lb));
     }
 }
 
@@ -572,7 +571,7 @@ int build_pattern(Ctx *c, cudaStream_t s) {
     k_unit_fill<<<grid_for(10 * T), TPB, 0, s>>>(c->tets, c->tunit, T, uptr, cnt, c->ccode);
     k_sort_segments<<<grid_for(nunits), TPB, 0, s>>>(uptr, nunits, c->ccode);
     k_unit_slots<<<grid_for(10 * T), TPB, 0, s>>>(c->ccode, T, c->cslot);
-    k_code_words<<<grid_for(10 * T), TPB, 0, s>>>(c->ccode, 10 * T);
+    k_code_words<<<grid_for(10 * T), TPB, 0, s>>>(c->ccode, 10 * T, T);
     k_unit_meta<<<grid_for(nblocks), TPB, 0, s>>>(nblocks, c->block_node, c->adj, c->adj_ptr,
                                                   c->boff, uid, upper, uptr, c->bmeta, c->bmirror);
     k_fill_i32<<<grid_for(nunits), TPB, 0, s>>>(c->owner, nunits, INT32_MAX);

@@ -158,13 +158,19 @@ k_elements(const double4_32a *__restrict__ X, const int4 *__restrict__ tets,
         }
         unsigned todo = __ballot_sync(FULL, doit);
         __syncwarp();
-        while (todo) {  // coalesced copy-out, one record at a time
+        while (todo) {  // coalesced copy-out, one record at a time, to its diagonal and pair rows
             const int r = __ffs(todo) - 1;
             todo &= todo - 1;
             const int32_t tr = __shfl_sync(FULL, t, r);
             const double2 *src = reinterpret_cast<const double2 *>(wrec + (size_t)r * KE_STRIDE);
-            double2 *dst = reinterpret_cast<double2 *>(Ke + (size_t)tr * KE_STRIDE);
-            for (int k = lane; k < KE_STRIDE / 2; k += 32) dst[k] = src[k];
+            double2 *dd = reinterpret_cast<double2 *>(Ke + ke_diag_at(T, tr, 0));
+            double2 *dp = reinterpret_cast<double2 *>(Ke + ke_pair_at(T, tr, 0));
+            for (int k = lane; k < KE_STRIDE / 2; k += 32) {
+                if (k < KE_DIAG / 2)
+                    dd[k] = src[k];
+                else
+                    dp[k - KE_DIAG / 2] = src[k];
+            }
         }
         __syncwarp();
     }
@@ -329,12 +335,12 @@ __global__ void k_expand(const double *__restrict__ Ke, const int4 *__restrict__
             int ta = a, ti = i;
             a = b; i = j; b = ta; j = ti;
         }
-        const double *rec = Ke + (size_t)t * KE_STRIDE;
         const int4 tq = tets[t];
         const int gid[4] = {tq.x, tq.y, tq.z, tq.w};
-        out[k] = (a == b)             ? rec[ke_diag_off(a) + ke_tri(i, j)]
-                 : gid[a] < gid[b] ? rec[ke_off_off(a, b) + 3 * i + j]
-                                   : rec[ke_off_off(a, b) + 3 * j + i];
+        const double *dg = Ke + ke_diag_at(T, t, a), *pr = Ke + ke_pair_at(T, t, ke_pair(a, b));
+        out[k] = (a == b)             ? dg[ke_tri(i, j)]
+                 : gid[a] < gid[b] ? pr[3 * i + j]
+                                   : pr[3 * j + i];
     }
 }
 

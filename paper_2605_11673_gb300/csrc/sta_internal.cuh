@@ -33,24 +33,36 @@ int fail(int code, const std::string &msg);
     } while (0)
 
 // ------------------------------------------------------------------------------------
-// Element cache record: the 78 unique entries of the symmetric 12x12 element matrix,
-// grouped by 3x3 node-pair block so that one block is one contiguous, 16-byte aligned run:
-//   diagonal block (a, a), a = 0..3:  6 entries (i <= j, row-major) at 6a
-//   off-diagonal pair {a, b}, a < b:   9 entries + 1 pad at 24 + 10 pair(a, b), row-major over
-//                                      the block of the node with the LOWER global id, i.e.
-//                                      K[3a+i][3b+j] at 3i+j if id(a) < id(b), else at 3j+i
-// with pair(0,1..3) = 0..2, pair(1,2..3) = 3..4, pair(2,3) = 5.  84 doubles (672 B) per
-// tetrahedron; every run starts on a 16-byte boundary.  Oriented this way, the contribution of
-// any tetrahedron to the node-pair block (a, b), id(a) < id(b), is its run read row-major:
-// the folds never transpose.
+// Element cache: the 78 unique entries of each symmetric 12x12 element matrix, grouped by 3x3
+// node-pair block into runs, stored as two row arrays in one allocation of 84 T doubles:
+//   Kd = Ke[0 .. 24T):   row 4t + a (6 doubles, 48 B): diagonal block (a, a), entries i <= j
+//                        row-major: (0,0) (0,1) (0,2) (1,1) (1,2) (2,2)
+//   Kp = Ke[24T .. 84T): row 6t + pair(a, b) (10 doubles, 80 B: 9 entries + a +0.0 pad), a < b
+//                        local indices: the block row-major over the node with the LOWER global
+//                        id, i.e. K[3a+i][3b+j] at 3i+j if id(a) < id(b), else at 3j+i
+// with pair(0,1..3) = 0..2, pair(1,2..3) = 3..4, pair(2,3) = 5.  Every run starts on a 16-byte
+// boundary.  Oriented this way, the contribution of any tetrahedron to the node-pair block
+// (a, b), id(a) < id(b), is one row read as is (the folds never transpose), and the rows of
+// one kind have one width (whole-row gathers).  A tet's record is computed in the order
+// diagonal runs then pair runs (84 doubles, KE_STRIDE), then split between the two arrays.
 // ------------------------------------------------------------------------------------
 constexpr int KE_STRIDE = 84;
+constexpr int KE_DIAG = 24;   // doubles of a tet's 4 diagonal runs (Kd)
+constexpr int KE_PAIR = 60;   // doubles of a tet's 6 pair runs (Kp)
 
 __host__ __device__ inline int ke_diag_off(int a) { return 6 * a; }
 __host__ __device__ inline int ke_pair(int a, int b) {  // a < b
     return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);
 }
 __host__ __device__ inline int ke_off_off(int a, int b) { return 24 + 10 * ke_pair(a, b); }
+// Ke offset of tet t's diagonal run a, and of its pair run p
+__host__ __device__ inline int64_t ke_diag_at(int64_t T, int64_t t, int a) {
+    (void)T;
+    return KE_DIAG * t + 6 * a;
+}
+__host__ __device__ inline int64_t ke_pair_at(int64_t T, int64_t t, int p) {
+    return KE_DIAG * T + KE_PAIR * t + 10 * p;
+}
 // index of (i, j), i <= j, inside a diagonal 6-run
 __host__ __device__ inline int ke_tri(int i, int j) {
     return i == 0 ? j : (i == 1 ? 2 + j : 5);
@@ -66,9 +78,16 @@ __host__ __device__ inline int32_t contrib_code(int32_t t, int la, int lb) {
 __host__ __device__ inline int32_t code_tet(int32_t code) { return (code >> 4) & 0x07ffffff; }
 
 // Contributor word of a unit list (ccode after create): the element-cache offset of the
-// contributor's run for the unit (t * KE_STRIDE + run offset) | active << 31.
+// contributor's run for the unit (ke_diag_at / ke_pair_at) | active << 31.
 __host__ __device__ inline uint32_t word_offset(uint32_t w) { return w & 0x7fffffffu; }
-__host__ __device__ inline int32_t word_tet(uint32_t w) { return (int32_t)(word_offset(w) / KE_STRIDE); }
+__host__ __device__ inline int32_t word_tet(uint32_t w, int64_t T) {
+    const int64_t off = word_offset(w);
+    return (int32_t)(off < KE_DIAG * T ? off / KE_DIAG : (off - KE_DIAG * T) / KE_PAIR);
+}
+// the run of tet t for unit slot s (0..3 diagonal, 4..9 pairs)
+__host__ __device__ inline int64_t ke_slot_at(int64_t T, int64_t t, int s) {
+    return s < 4 ? ke_diag_at(T, t, s) : ke_pair_at(T, t, s - 4);
+}
 
 // The 10 unit slots of a tetrahedron: 0..3 diagonal (la, la), 4..9 the pairs (0,1) (0,2) (0,3)
 // (1,2) (1,3) (2,3).
@@ -146,7 +165,7 @@ struct Ctx {
     unsigned long long *act_count = nullptr;
 
     // state
-    double *Ke = nullptr;       // T x 78 element cache
+    double *Ke = nullptr;       // 84 T: element cache, diagonal runs then pair runs (KE_DIAG, KE_PAIR)
     uint8_t *mask = nullptr;    // T
     double *val = nullptr;      // nnz
     int32_t *owner = nullptr;   // nunits: streaming dedupe slot, INT32_MAX when free

@@ -123,7 +123,8 @@ k_fold_entries(FoldArgs A, const int32_t *__restrict__ list, const unsigned long
 // edited[k] = tet id | (new state << 31); the edited count is *m_dev if m_dev, else m;
 // counters[1] (units) and counters[3] (entries) start at zero.
 __global__ void k_stream_claim(const int32_t *__restrict__ edited, int64_t m,
-                               const int64_t *__restrict__ m_dev, const int32_t *__restrict__ tunit,
+                               const int64_t *__restrict__ m_dev, int64_t T,
+                               const int32_t *__restrict__ tunit,
                                const int32_t *__restrict__ cslot, int32_t *__restrict__ ccode,
                                uint8_t *__restrict__ mask, int32_t *__restrict__ owner,
                                int32_t *__restrict__ list, unsigned long long *counters) {
@@ -143,9 +144,7 @@ __global__ void k_stream_claim(const int32_t *__restrict__ edited, int64_t m,
             const int32_t slot = cslot[10 * (int64_t)t + s];
             u = tunit[10 * (int64_t)t + s];
             // the word is (t, s)'s run offset | activity: written without reading it back
-            const uint32_t off = (uint32_t)t * KE_STRIDE +
-                                 (s < 4 ? ke_diag_off(s) : ke_off_off(slot_la(s), slot_lb(s)));
-            ccode[slot] = (int32_t)(off | (on << 31));
+            ccode[slot] = (int32_t)((uint32_t)ke_slot_at(T, t, s) | (on << 31));
             diag = s < 4;
             won = atomicCAS(&owner[u], INT32_MAX, 0) == INT32_MAX;
         }
@@ -162,11 +161,12 @@ __global__ void k_stream_claim(const int32_t *__restrict__ edited, int64_t m,
 }
 
 // Activity bits of all contributor codes from the mask (full rebuild with a new mask).
-__global__ void k_mask_bits(int32_t *__restrict__ ccode, int64_t n, const uint8_t *__restrict__ mask) {
+__global__ void k_mask_bits(int32_t *__restrict__ ccode, int64_t n, int64_t T,
+                            const uint8_t *__restrict__ mask) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t code = (uint32_t)ccode[k];
-        const uint32_t on = mask[word_tet(code)] ? CODE_ACTIVE : 0u;
+        const uint32_t on = mask[word_tet(code, T)] ? CODE_ACTIVE : 0u;
         ccode[k] = (int32_t)((code & ~CODE_ACTIVE) | on);
     }
 }
@@ -203,7 +203,7 @@ int launch_mask_bits(Ctx *c, cudaStream_t s) {
     int64_t grid = (n + 255) / 256;
     const int64_t cap = (int64_t)c->num_sms * 8;
     if (grid > cap) grid = cap;
-    k_mask_bits<<<(unsigned)grid, 256, 0, s>>>(c->ccode, n, c->mask);
+    k_mask_bits<<<(unsigned)grid, 256, 0, s>>>(c->ccode, n, c->T, c->mask);
     STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;
 }
@@ -218,7 +218,7 @@ int launch_stream_frame(Ctx *c, FrameHeader *frame, int64_t cap, cudaStream_t s)
     const int64_t gmax = (int64_t)c->num_sms * 16;
     g = g < 1 ? 1 : (g > gmax ? gmax : g);
     unsigned long long *cnt = frame_counters(frame);
-    k_stream_claim<<<(unsigned)g, threads, 0, s>>>(frame_edited(frame), 0, &frame->m, c->tunit,
+    k_stream_claim<<<(unsigned)g, threads, 0, s>>>(frame_edited(frame), 0, &frame->m, c->T, c->tunit,
                                                    c->cslot, c->ccode, c->mask, c->owner,
                                                    c->touched, cnt);
     STA_CUDA_TRY(cudaGetLastError());
@@ -235,7 +235,7 @@ int launch_stream_scratch(Ctx *c, int64_t m, const int32_t *d_edited, int32_t *t
     if (m > 0) {
         const int threads = 256;
         const int64_t g = (10 * m + threads - 1) / threads;
-        k_stream_claim<<<(unsigned)g, threads, 0, s>>>(d_edited, m, nullptr, c->tunit, c->cslot,
+        k_stream_claim<<<(unsigned)g, threads, 0, s>>>(d_edited, m, nullptr, c->T, c->tunit, c->cslot,
                                                        c->ccode, c->mask, c->owner, touched,
                                                        counters);
         STA_CUDA_TRY(cudaGetLastError());
