@@ -79,6 +79,10 @@ def lib(path=None):
         L.orc_element_x_grad_cs.restype = C.c_int
         L.orc_grad_all.argtypes = [_p, _p, _p, _p, _p, _p, _p, _p, _p]
         L.orc_grad_all.restype = C.c_int
+        L.orc_fx_exponents.argtypes = [_p, _p, _p]
+        L.orc_fx_rebuild.argtypes = [_p, _p, _p, _p, _f64, _p, _p]
+        L.orc_fx_update.argtypes = [_p, _p, _p, _p, _p, _i64, _f64, _p, _p]
+        L.orc_fx_update.restype = _i64
         _lib = L
     return _lib
 
@@ -193,6 +197,30 @@ class Pattern:
         assert mask.dtype == np.uint8 and val.dtype == np.float64
         r = lib().orc_additive_update(self._h, _ptr(_c(Ke, np.float64)), _ptr(mask),
                                       _ptr(edits), edits.shape[0], _ptr(val))
+        if r < 0:
+            raise ValueError(f"invalid edit at index {-r - 2}")
+
+    # exact additive streaming in fixed point (see orc_fx_exponents)
+    def fx_exponents(self, Ke) -> np.ndarray:
+        e = np.zeros(self.nnz, np.int32)
+        lib().orc_fx_exponents(self._h, _ptr(_c(Ke, np.float64)), _ptr(e))
+        return e
+
+    def fx_rebuild(self, Ke, e, mask, eps: float = 0.0):
+        """(S, val): exact integer sums and values over the active set."""
+        S = np.zeros(self.nnz, np.int64)
+        val = np.zeros(self.nnz)
+        lib().orc_fx_rebuild(self._h, _ptr(_c(Ke, np.float64)), _ptr(_c(e, np.int32)),
+                             _ptr(_c(mask, np.uint8)), float(eps), _ptr(S), _ptr(val))
+        return S, val
+
+    def fx_update(self, Ke, e, mask, edits, S, val, eps: float = 0.0) -> None:
+        """In place on mask, S and val (additive, O(|Delta|))."""
+        edits = _c(edits, np.int32).reshape(-1, 3)
+        assert mask.dtype == np.uint8 and S.dtype == np.int64 and val.dtype == np.float64
+        r = lib().orc_fx_update(self._h, _ptr(_c(Ke, np.float64)), _ptr(_c(e, np.int32)),
+                                _ptr(mask), _ptr(edits), edits.shape[0], float(eps), _ptr(S),
+                                _ptr(val))
         if r < 0:
             raise ValueError(f"invalid edit at index {-r - 2}")
 

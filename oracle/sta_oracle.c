@@ -486,6 +486,120 @@ int64_t orc_additive_update(const orc_pattern_t *p, const double *Ke, uint8_t *m
 }
 
 /* ------------------------------------------------------------------------------------- */
+/* Exact additive streaming in fixed point                                                  */
+/* ------------------------------------------------------------------------------------- */
+
+/*
+ * The paper's streaming_update (Sec. 3.4, Sec. 3.5: add or subtract the edited tetrahedra's
+ * element contributions, O(|Delta|)) is exact only up to rounding in floating point.  Reading
+ * that makes it exact: every CSR entry k gets a fixed binary exponent e_k from its superset
+ * contributions; every contribution c to k is quantised once, q = c * 2^-e_k rounded to the
+ * nearest integer (ties to even); the entry keeps the exact integer sum S_k over its active
+ * contributors and its value is that sum converted once, val_k = double(S_k) * 2^e_k, plus
+ * eps on the diagonal.  Integer addition is associative, so adding and subtracting q in any
+ * order gives the S_k of a rebuild.
+ *   E(x)   unbiased exponent field of x (floor(log2|x|) for normal x; -1023 for 0 / subnormal)
+ *   m_k    maximum of E over the entry's superset contributions
+ *   L_k    ceil(log2(kappa_k)), kappa_k = number of superset contributions to k
+ *   e_k    m_k + 1 + L_k - 62, limited to [-1022, 1023]; 0 when every contribution is 0
+ * so |q| < 2^(62 - L_k), |S_k| < 2^62, and |val_k - sum of active c| <= kappa_k 2^(e_k - 1)
+ * plus the rounding of the final conversion.
+ */
+static int exp_field(double x)
+{
+    uint64_t u;
+    memcpy(&u, &x, sizeof u);
+    return (int)((u >> 52) & 0x7ff) - 1023;
+}
+
+void orc_fx_exponents(const orc_pattern_t *p, const double *Ke, int32_t *e)
+{
+    int32_t *mk = malloc(sizeof(int32_t) * (p->nnz > 0 ? p->nnz : 1));
+    int64_t *kap = calloc(p->nnz > 0 ? p->nnz : 1, sizeof(int64_t));
+    for (int64_t k = 0; k < p->nnz; ++k) mk[k] = -1023;
+    for (int64_t t = 0; t < p->T; ++t)
+        for (int pq = 0; pq < 144; ++pq) {
+            int64_t k = p->scat[144 * t + pq];
+            int ex = exp_field(Ke[144 * t + pq]);
+            if (ex > mk[k]) mk[k] = ex;
+            kap[k] += 1;
+        }
+    for (int64_t k = 0; k < p->nnz; ++k) {
+        if (mk[k] == -1023) {
+            e[k] = 0;
+            continue;
+        }
+        int L = 0;
+        while (((int64_t)1 << L) < kap[k]) ++L;
+        int ek = mk[k] + 1 + L - 62;
+        e[k] = ek < -1022 ? -1022 : (ek > 1023 ? 1023 : ek);
+    }
+    free(mk);
+    free(kap);
+}
+
+static int64_t fx_quant(double c, int32_t e) { return llrint(ldexp(c, -e)); }
+
+static double fx_value(int64_t S, int32_t e) { return ldexp((double)S, e); }
+
+/* S and val from scratch over the active set (plus eps on the diagonal). */
+void orc_fx_rebuild(const orc_pattern_t *p, const double *Ke, const int32_t *e,
+                    const uint8_t *mask, double eps, int64_t *S, double *val)
+{
+    for (int64_t k = 0; k < p->nnz; ++k) S[k] = 0;
+    for (int64_t t = 0; t < p->T; ++t) {
+        if (!mask[t]) continue;
+        for (int pq = 0; pq < 144; ++pq) {
+            int64_t k = p->scat[144 * t + pq];
+            S[k] += fx_quant(Ke[144 * t + pq], e[k]);
+        }
+    }
+    for (int64_t r = 0; r < p->nrows; ++r)
+        for (int64_t k = p->row_ptr[r]; k < p->row_ptr[r + 1]; ++k) {
+            val[k] = fx_value(S[k], e[k]);
+            if (eps != 0.0 && p->col[k] == r) val[k] += eps;
+        }
+}
+
+/* One frame of the additive update on S (O(|Delta|)): each edited tetrahedron subtracts
+ * (deactivation) or adds (activation) its quantised contributions, edits in list order, a
+ * swap as its deactivation then its activation; then the values of its entries are
+ * converted again.  Same return convention as orc_local_recompute. */
+int64_t orc_fx_update(const orc_pattern_t *p, const double *Ke, const int32_t *e, uint8_t *mask,
+                      const orc_edit *ed, int64_t n, double eps, int64_t *S, double *val)
+{
+    int64_t bad = orc_validate_edits(p->T, mask, ed, n);
+    if (bad) return -(bad + 1);
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t off = -1, on = -1;
+        if (ed[i].op == 0) off = ed[i].tet;
+        if (ed[i].op == 1) on = ed[i].tet;
+        if (ed[i].op == 2) { off = ed[i].tet; on = ed[i].tet2; }
+        for (int side = 0; side < 2; ++side) {
+            int32_t t = side == 0 ? off : on;
+            if (t < 0) continue;
+            mask[t] = side == 0 ? 0 : 1;
+            for (int pq = 0; pq < 144; ++pq) {
+                int64_t k = p->scat[144 * (int64_t)t + pq];
+                int64_t q = fx_quant(Ke[144 * (int64_t)t + pq], e[k]);
+                S[k] += side == 0 ? -q : q;
+            }
+        }
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int side = 0; side < 2; ++side) {
+            int32_t t = side == 0 ? ed[i].tet : (ed[i].op == 2 ? ed[i].tet2 : -1);
+            if (t < 0) continue;
+            for (int pq = 0; pq < 144; ++pq) {  /* a local diagonal entry is a global one */
+                int64_t k = p->scat[144 * (int64_t)t + pq];
+                val[k] = fx_value(S[k], e[k]);
+                if (eps != 0.0 && pq / 12 == pq % 12) val[k] += eps;
+            }
+        }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------- */
 /* Gradient reference (adjoint form)                                                        */
 /* ------------------------------------------------------------------------------------- */
 

@@ -38,6 +38,12 @@ MUTATIONS = {
                                     [pins.test_local_recompute_equals_rebuild_every_frame]),
     "dnu_sign": ("- sb * E / (2.0 * onu * onu));", "+ sb * E / (2.0 * onu * onu));",
                  [pins.test_element_param_grad_vs_fd_and_linearity]),
+    "fx_removal_truncates": ("                S[k] += side == 0 ? -q : q;",
+                             "                S[k] += side == 0 ? -(int64_t)trunc(ldexp(Ke[144 * (int64_t)t + pq], -e[k])) : q;",
+                             [pins.test_fx_additive_stream_equals_fx_rebuild_every_frame]),
+    "fx_exponent_too_coarse": ("        int ek = mk[k] + 1 + L - 62;", "        int ek = mk[k] + 1 + L - 40;",
+                               [pins.test_fx_within_its_error_bound_of_the_fp64_fold,
+                                pins.test_fx_exact_when_contributions_are_small_integers]),
 }
 
 

@@ -406,3 +406,78 @@ def test_compliance_gradient_vs_central_fd(orc):
     h = 1e-6
     fd = (loss(wl.X + h * Dx, wl.E, wl.nu)[0] - loss(wl.X - h * Dx, wl.E, wl.nu)[0]) / (2 * h)
     assert abs(np.sum(dX * Dx) - fd) <= 1e-6 * abs(fd)
+
+
+# -------------------------------------------------------------------------------------------
+# Exact additive streaming in fixed point (orc_fx_*): the paper's streaming_update (Sec. 3.4,
+# Sec. 3.5) with integer sums, so that adding and subtracting element contributions in any
+# order equals a rebuild bit for bit.
+# -------------------------------------------------------------------------------------------
+
+def _fx_stream(orc, wl, eps=0.0):
+    P = orc.Pattern(wl.n_nodes, wl.tets)
+    Ke, bad = orc.element_all(wl.X, wl.tets, wl.E, wl.nu)
+    assert bad == 0
+    e = P.fx_exponents(Ke)
+    mask = wl.mask0.copy()
+    S, val = P.fx_rebuild(Ke, e, mask, eps)
+    for ed in wl.frames:
+        P.fx_update(Ke, e, mask, ed, S, val, eps)
+        S_r, val_r = P.fx_rebuild(Ke, e, mask, eps)
+        assert np.array_equal(S, S_r)
+        assert np.array_equal(val.view(np.uint64), val_r.view(np.uint64))
+    return P, Ke, e, mask, S, val
+
+
+def test_fx_additive_stream_equals_fx_rebuild_every_frame(orc):
+    _fx_stream(orc, W.plain_small(seed=2))
+    _fx_stream(orc, W.plain_small(seed=3), eps=1e-3)
+    _fx_stream(orc, W.prefractured_block(N=8, sites=6, frames=6))
+    _fx_stream(orc, W.refinement_hierarchy(N=5, radius=0.3, frames=6))
+
+
+def test_fx_within_its_error_bound_of_the_fp64_fold(orc):
+    # |val_fx - val_fold| <= kappa_k 2^(e_k - 1) + 2 ulp(val), and <= 1e-13 sum_k |c|
+    P, Ke, e, mask, S, val = _fx_stream(orc, W.prefractured_block(N=8, sites=6, frames=4))
+    fold = P.rebuild(Ke, mask)
+    absum = P.rebuild(np.abs(Ke), mask)
+    kappa = np.bincount(P.scat.reshape(-1), minlength=P.nnz)
+    err = np.abs(val - fold)
+    bound = kappa * np.ldexp(1.0, e - 1) + 2 * np.spacing(np.abs(fold)) + 2 * np.spacing(absum)
+    assert np.all(err <= bound)
+    assert np.all(err <= 1e-13 * absum + 1e-300)
+    assert np.all(np.abs(S) < 2 ** 62)
+
+
+def test_fx_exact_when_contributions_are_small_integers(orc):
+    # integer element contributions (|c| <= 2^10, at most 2^6 per entry): the fold is exact in
+    # FP64 and so must the fixed-point value be
+    wl = W.plain_small(seed=4)
+    P = orc.Pattern(wl.n_nodes, wl.tets)
+    rng = np.random.default_rng(5)
+    A = rng.integers(-1024, 1025, size=(wl.n_tets, 12, 12)).astype(np.float64)
+    Ke = (A + np.transpose(A, (0, 2, 1))).reshape(wl.n_tets, 144)
+    e = P.fx_exponents(Ke)
+    mask = wl.mask0.copy()
+    S, val = P.fx_rebuild(Ke, e, mask)
+    assert np.array_equal(val.view(np.uint64), P.rebuild(Ke, mask).view(np.uint64))
+    for ed in wl.frames[:6]:
+        P.fx_update(Ke, e, mask, ed, S, val)
+    assert np.array_equal(val.view(np.uint64), P.rebuild(Ke, mask).view(np.uint64))
+
+
+def test_fx_order_of_edits_does_not_matter(orc):
+    wl = W.plain_small(seed=6)
+    P = orc.Pattern(wl.n_nodes, wl.tets)
+    Ke, _ = orc.element_all(wl.X, wl.tets, wl.E, wl.nu)
+    e = P.fx_exponents(Ke)
+    m1, m2 = wl.mask0.copy(), wl.mask0.copy()
+    S1, v1 = P.fx_rebuild(Ke, e, m1)
+    S2, v2 = S1.copy(), v1.copy()
+    rng = np.random.default_rng(7)
+    for ed in wl.frames[:8]:
+        P.fx_update(Ke, e, m1, ed, S1, v1)
+        for i in rng.permutation(ed.shape[0]):  # one edit per call, shuffled
+            P.fx_update(Ke, e, m2, ed[i:i + 1], S2, v2)
+    assert np.array_equal(S1, S2)
+    assert np.array_equal(v1.view(np.uint64), v2.view(np.uint64))
