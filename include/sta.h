@@ -272,6 +272,29 @@ int sta_batch_apply_edits(sta_ctx *ctx, const int64_t *counts, const sta_edit *e
 int sta_graph_enable(sta_ctx *ctx, int64_t max_edited, void *stream);
 int sta_graph_disable(sta_ctx *ctx, void *stream);
 
+/*
+ * sta_set_policy -- how sta_apply_edits maintains the values, and what a rebuild computes.
+ *  STA_POLICY_REFOLD (default): every touched entry is re-folded from +0.0 over its active
+ *    contributions in ascending tetrahedron id (the local_recompute policy of Sec. 3.5 made
+ *    bitwise); values are the canonical FP64 fold.
+ *  STA_POLICY_FIXED: the streaming_update of Sec. 3.4 / 3.5 (add or subtract the edited
+ *    tetrahedra's contributions, O(|Delta|)) made exact in fixed point: each entry k has a
+ *    binary exponent e_k fixed by its superset contributions (2^-62 of the largest, times the
+ *    contributor count rounded up to a power of two), each contribution is quantised once to
+ *    the nearest integer multiple of 2^e_k, the context keeps the exact integer sum per entry
+ *    and a value is that sum converted once (+ eps on the diagonal).  Streaming equals the
+ *    fixed-point rebuild bit for bit; values are within about 2^-56 of each entry's largest
+ *    contribution of the FP64 fold.
+ * Switching computes what the policy needs (exponents and quantised contributions, about
+ * 8.5 bytes per nnz and 672 bytes per tetrahedron on first use) and rebuilds every value from
+ * the current mask.  Not allowed while graph mode is on (STA_ESTATE); graphs enabled afterwards
+ * capture the current policy.  sta_set_params / sta_recompute_elements recompute the
+ * fixed-point inputs under STA_POLICY_FIXED (values are not re-folded; call sta_refold).
+ */
+#define STA_POLICY_REFOLD 0
+#define STA_POLICY_FIXED 1
+int sta_set_policy(sta_ctx *ctx, int32_t policy, void *stream);
+
 /* Human-readable message of the last error on the calling thread. */
 const char *sta_last_error(void);
 const char *sta_status_string(int status);

@@ -29,9 +29,11 @@ EXPORTED = (
     "sta_recompute_elements", "sta_set_params", "sta_element_matrices", "sta_last_error",
     "sta_status_string", "sta_apply_edits_noalloc", "sta_adjoint", "sta_spmv", "sta_set_launch",
     "sta_batch_create", "sta_batch_size", "sta_batch_instance", "sta_batch_apply_edits",
-    "sta_graph_enable", "sta_graph_disable",
+    "sta_graph_enable", "sta_graph_disable", "sta_set_policy",
 )
 STA_NOALLOC_MAX_EDITED = 32768
+STA_POLICY_REFOLD = 0
+STA_POLICY_FIXED = 1
 
 
 class StaError(RuntimeError):
@@ -89,6 +91,7 @@ def load_library(path: Path | str | None = None):
     L.sta_batch_apply_edits.argtypes = [_p, _p, _p, _p]
     L.sta_graph_enable.argtypes = [_p, _i64, _p]
     L.sta_graph_disable.argtypes = [_p, _p]
+    L.sta_set_policy.argtypes = [_p, C.c_int32, _p]
     L.sta_last_error.restype = C.c_char_p
     L.sta_status_string.argtypes = [_int]
     L.sta_status_string.restype = C.c_char_p
@@ -305,6 +308,12 @@ def sta_graph_enable(h: int, max_edited: int, stream=None) -> None:
     _check(load_library().sta_graph_enable(h, int(max_edited), _stream_handle(stream)))
 
 
+def sta_set_policy(h: int, policy: int, stream=None) -> None:
+    """STA_POLICY_REFOLD (canonical FP64 fold) or STA_POLICY_FIXED (exact fixed-point additive
+    update); rebuilds every value under the new policy."""
+    _check(load_library().sta_set_policy(h, int(policy), _stream_handle(stream)))
+
+
 def sta_graph_disable(h: int, stream=None) -> None:
     _check(load_library().sta_graph_disable(h, _stream_handle(stream)))
 
@@ -423,6 +432,9 @@ class Assembler:
 
     def graph_enable(self, max_edited: int, stream=None):
         sta_graph_enable(self.h, max_edited, stream)
+
+    def set_policy(self, policy: int, stream=None):
+        sta_set_policy(self.h, policy, stream)
 
     def graph_disable(self, stream=None):
         sta_graph_disable(self.h, stream)

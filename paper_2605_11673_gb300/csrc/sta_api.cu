@@ -402,7 +402,21 @@ int sta_sizes(const sta_ctx *x, int64_t *n_nodes, int64_t *n_tets, int64_t *n_bl
 
 int sta_recompute_elements(sta_ctx *x, int active_only, void *stream) {
     if (!x) return fail(STA_EINVAL, "ctx is NULL");
-    return launch_elements(&x->c, active_only != 0, (cudaStream_t)stream);
+    STA_TRY(launch_elements(&x->c, active_only != 0, (cudaStream_t)stream));
+    if (x->c.policy == STA_POLICY_FIXED) STA_TRY(launch_fx_prepare(&x->c, (cudaStream_t)stream));
+    return STA_OK;
+}
+
+int sta_set_policy(sta_ctx *x, int32_t policy, void *stream) {
+    if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    if (policy != STA_POLICY_REFOLD && policy != STA_POLICY_FIXED)
+        return fail(STA_EINVAL, "policy must be STA_POLICY_REFOLD or STA_POLICY_FIXED");
+    Ctx *c = &x->c;
+    if (c->graph_on) return fail(STA_ESTATE, "disable graph mode before changing the policy");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (policy == STA_POLICY_FIXED) STA_TRY(launch_fx_prepare(c, s));
+    c->policy = policy;
+    return launch_rebuild(c, s);  // every value under the new policy, from the current mask
 }
 
 int sta_set_params(sta_ctx *x, const double *nodes, const double *young, const double *poisson,
@@ -442,6 +456,7 @@ int sta_set_params(sta_ctx *x, const double *nodes, const double *young, const d
     if (back[0] != 0)
         return fail(STA_EINVAL, std::to_string(back[0]) + " tetrahedra have det <= 0 (first: tet " +
                                     std::to_string(back[2]) + ")");
+    if (c->policy == STA_POLICY_FIXED) STA_TRY(launch_fx_prepare(c, s));
     return STA_OK;
 }
 

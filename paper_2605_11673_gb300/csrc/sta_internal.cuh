@@ -166,6 +166,11 @@ struct Ctx {
 
     // state
     double *Ke = nullptr;       // 84 T: element cache, diagonal runs then pair runs (KE_DIAG, KE_PAIR)
+    // update policy (STA_POLICY_*) and the fixed-point state (sta_fixed.cu), allocated on first use
+    int policy = STA_POLICY_REFOLD;
+    long long *fx_q = nullptr;  // 84 T: quantised contributions at the element-cache offsets
+    int16_t *fx_e = nullptr;    // nnz: exponent of each entry (keyed by its upper-block index)
+    long long *fx_s = nullptr;  // nnz: exact integer sum of each entry's active contributions
     uint8_t *mask = nullptr;    // T
     double *val = nullptr;      // nnz
     int32_t *owner = nullptr;   // nunits: streaming dedupe slot, INT32_MAX when free
@@ -229,6 +234,10 @@ int launch_adjoint(Ctx *c, const double *gval, double *dE, double *dnu, double *
 int launch_spmv(Ctx *c, const double *val, const double *x, double *y, cudaStream_t s);
 int launch_rebuild(Ctx *c, cudaStream_t s);                      // sta_assemble.cu
 int launch_stream_frame(Ctx *c, FrameHeader *frame, int64_t cap, cudaStream_t s);  // sta_stream.cu
+int launch_fx_prepare(Ctx *c, cudaStream_t s);                   // sta_fixed.cu
+int launch_fx_rebuild(Ctx *c, cudaStream_t s);
+int launch_fx_frame(Ctx *c, const int32_t *edited, int64_t m, const int64_t *m_dev, int64_t cap,
+                    int32_t *touched, unsigned long long *counters, cudaStream_t s);
 int launch_mask_bits(Ctx *c, cudaStream_t s);                    // codes <- mask
 int launch_stream_scratch(Ctx *c, int64_t m, const int32_t *d_edited, int32_t *touched,
                           unsigned long long *counters, cudaStream_t s);

@@ -184,6 +184,7 @@ k_fold_flat(FoldArgs A, const int4 *__restrict__ trec, int64_t ntiles) {
 // (block_threads 64, 128 or 256; blocks_per_sm 0 = occupancy maximum).
 int launch_rebuild(Ctx *c, cudaStream_t s) {
     if (c->ntiles == 0) return STA_OK;
+    if (c->policy == STA_POLICY_FIXED) return launch_fx_rebuild(c, s);
     const int threads = c->block_threads == 64 || c->block_threads == 256 ? c->block_threads : 128;
     const void *kern = threads == 64    ? (const void *)k_fold_flat<2>
                        : threads == 256 ? (const void *)k_fold_flat<8>

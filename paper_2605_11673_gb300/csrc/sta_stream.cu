@@ -213,6 +213,9 @@ int launch_mask_bits(Ctx *c, cudaStream_t s) {
 // it, grids are sized for `cap` edited tetrahedra (so the sequence can be captured once and
 // replayed for any frame up to `cap`).
 int launch_stream_frame(Ctx *c, FrameHeader *frame, int64_t cap, cudaStream_t s) {
+    if (c->policy == STA_POLICY_FIXED)
+        return launch_fx_frame(c, frame_edited(frame), 0, &frame->m, cap, c->touched,
+                               frame_counters(frame), s);
     const int threads = 256;
     int64_t g = (10 * cap + threads - 1) / threads;
     const int64_t gmax = (int64_t)c->num_sms * 16;
@@ -232,7 +235,9 @@ int launch_stream_frame(Ctx *c, FrameHeader *frame, int64_t cap, cudaStream_t s)
 int launch_stream_scratch(Ctx *c, int64_t m, const int32_t *d_edited, int32_t *touched,
                           unsigned long long *counters, cudaStream_t s) {
     STA_CUDA_TRY(cudaMemsetAsync(counters + 1, 0, 3 * sizeof(unsigned long long), s));
-    if (m > 0) {
+    if (m > 0 && c->policy == STA_POLICY_FIXED) {
+        STA_TRY(launch_fx_frame(c, d_edited, m, nullptr, m, touched, counters, s));
+    } else if (m > 0) {
         const int threads = 256;
         const int64_t g = (10 * m + threads - 1) / threads;
         k_stream_claim<<<(unsigned)g, threads, 0, s>>>(d_edited, m, nullptr, c->T, c->tunit, c->cslot,
