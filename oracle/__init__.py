@@ -6,7 +6,7 @@ its binding) never imports, links or runs it, and the two share no code.
 
 Functions follow STA-FEM (arXiv 2605.11673): Eq. 8 for the assembled operator, Sec. 3.3 for
 the rebuild-equality invariant, Sec. 3.5 for the full_rebuild / local_recompute /
-streaming_update policies.  See sta_oracle.c for the element formula and summation order.
+streaming_update policies, Eqs. 1-7 and Algorithm 1 for the graph-Laplacian proxy operator.  See sta_oracle.c for the element formula and summation order.
 """
 from __future__ import annotations
 
@@ -83,6 +83,14 @@ def lib(path=None):
         L.orc_fx_rebuild.argtypes = [_p, _p, _p, _p, _f64, _p, _p]
         L.orc_fx_update.argtypes = [_p, _p, _p, _p, _p, _i64, _f64, _p, _p]
         L.orc_fx_update.restype = _i64
+        L.orc_proxy_nnz.argtypes = [_p]
+        L.orc_proxy_nnz.restype = _i64
+        L.orc_proxy_pattern.argtypes = [_p, _p, _p]
+        L.orc_proxy_pattern.restype = None
+        L.orc_proxy_rebuild.argtypes = [_p, _p, _f64, _p, _p, _p]
+        L.orc_proxy_rebuild.restype = None
+        L.orc_proxy_update.argtypes = [_p, _p, _p, _i64, _f64, _p, _p, _p]
+        L.orc_proxy_update.restype = _i64
         _lib = L
     return _lib
 
@@ -223,6 +231,37 @@ class Pattern:
                                 _ptr(val))
         if r < 0:
             raise ValueError(f"invalid edit at index {-r - 2}")
+
+    # graph-Laplacian proxy operator (see orc_proxy_rebuild)
+    def proxy_pattern(self):
+        """(row_ptr (n + 1), col): the node-level superset pattern."""
+        nb = int(lib().orc_proxy_nnz(self._h))
+        ptr = np.zeros(self.n + 1, np.int32)
+        col = np.zeros(nb, np.int32)
+        lib().orc_proxy_pattern(self._h, _ptr(ptr), _ptr(col))
+        return ptr, col
+
+    def proxy_rebuild(self, mask, eps: float = 0.0):
+        """(mult, deg, val): edge multiplicities at both entries of each edge, node degrees,
+        and the values of A = L + eps I on the node-level pattern."""
+        nb = int(lib().orc_proxy_nnz(self._h))
+        mult = np.zeros(nb, np.int32)
+        deg = np.zeros(self.n, np.int32)
+        val = np.zeros(nb)
+        lib().orc_proxy_rebuild(self._h, _ptr(_c(mask, np.uint8)), float(eps), _ptr(mult),
+                                _ptr(deg), _ptr(val))
+        return mult, deg, val
+
+    def proxy_update(self, mask, edits, mult, deg, val, eps: float = 0.0) -> int:
+        """In place on mask, mult, deg and val.  Returns the distinct entries visited."""
+        edits = _c(edits, np.int32).reshape(-1, 3)
+        assert mask.dtype == np.uint8 and mult.dtype == np.int32 and deg.dtype == np.int32
+        assert val.dtype == np.float64
+        r = lib().orc_proxy_update(self._h, _ptr(mask), _ptr(edits), edits.shape[0],
+                                   float(eps), _ptr(mult), _ptr(deg), _ptr(val))
+        if r < 0:
+            raise ValueError(f"invalid edit at index {-r - 2}")
+        return int(r)
 
     def grad_all(self, X, E, nu, mask, grad_val):
         """Reference gradients (dE, dnu per tet, dX (n, 3)) for upstream dL/dval."""

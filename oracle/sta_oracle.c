@@ -208,6 +208,8 @@ typedef struct {
     int32_t *row_ptr; /* 3n + 1 */
     int32_t *col;     /* nnz */
     int32_t *scat;    /* T x 144 */
+    int64_t *nptr;    /* node-level pattern: row u = sorted neighbour set of u, n + 1 */
+    int32_t *ncol;    /* neighbour node of each node-level entry */
 } orc_pattern_t;
 
 static int cmp_i32(const void *a, const void *b)
@@ -221,6 +223,7 @@ void orc_pattern_free(orc_pattern_t *p)
     if (!p) return;
     free(p->tets); free(p->nt_ptr); free(p->nt_list); free(p->deg);
     free(p->row_ptr); free(p->col); free(p->scat);
+    free(p->nptr); free(p->ncol);
     free(p);
 }
 
@@ -299,6 +302,14 @@ orc_pattern_t *orc_pattern_create(int64_t n, int64_t T, const int32_t *tets)
                         p->scat[144 * t + 12 * (3 * a + i) + 3 * b + j] =
                             p->row_ptr[3 * tv[a] + i] + (int32_t)(3 * pos + j);
             }
+    }
+    /* node-level pattern (the proxy operator's): the neighbour sets themselves */
+    p->nptr = malloc(sizeof(int64_t) * (n + 1));
+    p->ncol = malloc(sizeof(int32_t) * (total_blocks > 0 ? total_blocks : 1));
+    p->nptr[0] = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        for (int64_t e = 0; e < p->deg[v]; ++e) p->ncol[p->nptr[v] + e] = nbr[v][e];
+        p->nptr[v + 1] = p->nptr[v] + p->deg[v];
     }
     for (int64_t v = 0; v < n; ++v) free(nbr[v]);
     free(nbr);
@@ -597,6 +608,124 @@ int64_t orc_fx_update(const orc_pattern_t *p, const double *Ke, const int32_t *e
             }
         }
     return 0;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* Graph-Laplacian proxy operator (Sec. 3.1 Eqs. 1-4; Sec. 3.2 Eqs. 5-7; Sec. 3.3;          */
+/* Algorithm 1)                                                                             */
+/* ------------------------------------------------------------------------------------- */
+
+/*
+ * A scalar n x n operator on the node-level superset pattern: row u holds the sorted
+ * neighbour set of u, u included (the node pairs whose 3x3 blocks make the elasticity CSR).
+ *   c_t(u, v) = number of active tetrahedra having {u, v} among their six edges   (Eq. 1)
+ *   a_t(u, v) = 1[c_t(u, v) > 0]                                                  (Eq. 2)
+ *   A_t(u, v) = -a_t(u, v) for u != v,  A_t(u, u) = sum_{w != u} a_t(u, w) + eps  (Eqs. 3, 4)
+ * Readings: a superset edge that is not active keeps its slot and holds +0.0 (the paper
+ * inserts and removes entries; a fixed slot holding +0.0 is the same matrix); an active one
+ * holds -1.0; the diagonal is (double) degree + eps, one IEEE addition; a node of no
+ * superset tetrahedron has an empty row (no eps entry), as in the elasticity pattern.  c_t is kept at
+ * both entries (u, v) and (v, u) of an edge, the degree per node.
+ */
+int64_t orc_proxy_nnz(const orc_pattern_t *p) { return p->nptr[p->n]; }
+
+void orc_proxy_pattern(const orc_pattern_t *p, int32_t *row_ptr, int32_t *col)
+{
+    for (int64_t v = 0; v <= p->n; ++v) row_ptr[v] = (int32_t)p->nptr[v];
+    memcpy(col, p->ncol, sizeof(int32_t) * p->nptr[p->n]);
+}
+
+/* node-level entry (u, v), by a linear scan of u's neighbour set; -1 if absent */
+static int64_t proxy_pos(const orc_pattern_t *p, int32_t u, int32_t v)
+{
+    for (int64_t k = p->nptr[u]; k < p->nptr[u + 1]; ++k)
+        if (p->ncol[k] == v) return k;
+    return -1;
+}
+
+/* full_rebuild of the proxy (Sec. 3.5): Eq. 1 by counting over the active tetrahedra, then
+ * Eqs. 2-4 entry by entry. */
+void orc_proxy_rebuild(const orc_pattern_t *p, const uint8_t *mask, double eps, int32_t *mult,
+                       int32_t *deg, double *val)
+{
+    const int64_t nb = p->nptr[p->n];
+    for (int64_t k = 0; k < nb; ++k) mult[k] = 0;
+    for (int64_t t = 0; t < p->T; ++t) {
+        if (!mask[t]) continue;
+        const int32_t *tv = p->tets + 4 * t;
+        for (int a = 0; a < 4; ++a)
+            for (int b = a + 1; b < 4; ++b) {
+                mult[proxy_pos(p, tv[a], tv[b])] += 1;
+                mult[proxy_pos(p, tv[b], tv[a])] += 1;
+            }
+    }
+    for (int64_t u = 0; u < p->n; ++u) {
+        deg[u] = 0;
+        for (int64_t k = p->nptr[u]; k < p->nptr[u + 1]; ++k) {
+            if (p->ncol[k] == u) continue;
+            int a = mult[k] > 0;
+            val[k] = a ? -1.0 : 0.0;
+            deg[u] += a;
+        }
+        int64_t kd = proxy_pos(p, (int32_t)u, (int32_t)u);
+        if (kd >= 0) val[kd] = (double)deg[u] + eps;  /* a node of no tetrahedron has no row */
+    }
+}
+
+/* streaming_update of the proxy (Sec. 3.2, Algorithm 1): the edits in list order (a swap as
+ * its deactivation then its activation), each edited tetrahedron adding +-1 to the
+ * multiplicity of its six edges (Eqs. 5-7); where a multiplicity moves between 0 and > 0,
+ * the edge's two off-diagonal entries are set (inserted: -1.0) or cleared (removed: +0.0)
+ * and the degrees of both end nodes and their diagonal entries follow.  mask, mult, deg and
+ * val are updated in place.  Returns the number of distinct entries the update visits (the
+ * two entries of each edge of an edited tetrahedron and the diagonal entry of each of their
+ * nodes), or -(1 + bad index) for an invalid edit list (nothing is changed then). */
+int64_t orc_proxy_update(const orc_pattern_t *p, uint8_t *mask, const orc_edit *ed, int64_t n,
+                         double eps, int32_t *mult, int32_t *deg, double *val)
+{
+    int64_t bad = orc_validate_edits(p->T, mask, ed, n);
+    if (bad) return -(bad + 1);
+    const int64_t nb = p->nptr[p->n];
+    uint8_t *seen = calloc(nb > 0 ? nb : 1, 1);
+    int64_t visited = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t off = -1, on = -1;
+        if (ed[i].op == 0) off = ed[i].tet;
+        if (ed[i].op == 1) on = ed[i].tet;
+        if (ed[i].op == 2) { off = ed[i].tet; on = ed[i].tet2; }
+        for (int side = 0; side < 2; ++side) {
+            int32_t t = side == 0 ? off : on;
+            if (t < 0) continue;
+            int32_t step = side == 0 ? -1 : 1;
+            mask[t] = side == 0 ? 0 : 1;
+            const int32_t *tv = p->tets + 4 * (int64_t)t;
+            for (int a = 0; a < 4; ++a) {
+                int64_t kd = proxy_pos(p, tv[a], tv[a]);
+                if (!seen[kd]) { seen[kd] = 1; ++visited; }
+            }
+            for (int a = 0; a < 4; ++a)
+                for (int b = a + 1; b < 4; ++b) {
+                    int32_t u = tv[a], v = tv[b];
+                    int64_t kuv = proxy_pos(p, u, v), kvu = proxy_pos(p, v, u);
+                    if (!seen[kuv]) { seen[kuv] = 1; ++visited; }
+                    if (!seen[kvu]) { seen[kvu] = 1; ++visited; }
+                    int32_t before = mult[kuv], after = before + step;
+                    mult[kuv] = after;
+                    mult[kvu] = after;
+                    if ((before == 0) != (after == 0)) {
+                        int32_t d = after > 0 ? 1 : -1;
+                        val[kuv] = after > 0 ? -1.0 : 0.0;
+                        val[kvu] = val[kuv];
+                        deg[u] += d;
+                        deg[v] += d;
+                        val[proxy_pos(p, u, u)] = (double)deg[u] + eps;
+                        val[proxy_pos(p, v, v)] = (double)deg[v] + eps;
+                    }
+                }
+        }
+    }
+    free(seen);
+    return visited;
 }
 
 /* ------------------------------------------------------------------------------------- */

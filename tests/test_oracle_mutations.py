@@ -44,6 +44,18 @@ MUTATIONS = {
     "fx_exponent_too_coarse": ("        int ek = mk[k] + 1 + L - 62;", "        int ek = mk[k] + 1 + L - 40;",
                                [pins.test_fx_within_its_error_bound_of_the_fp64_fold,
                                 pins.test_fx_exact_when_contributions_are_small_integers]),
+    "proxy_threshold_dropped": ("            val[k] = a ? -1.0 : 0.0;",
+                                "            val[k] = -(double)mult[k];",
+                                [pins.test_proxy_rebuild_vs_textbook_laplacian]),
+    "proxy_degree_counts_multiplicity": ("            deg[u] += a;", "            deg[u] += mult[k];",
+                                         [pins.test_proxy_rebuild_vs_textbook_laplacian,
+                                          pins.test_proxy_invariants_rows_symmetry_components]),
+    "proxy_update_misses_removal": ("                    if ((before == 0) != (after == 0)) {",
+                                    "                    if (before == 0 && after > 0) {",
+                                    [pins.test_proxy_stream_equals_rebuild_every_frame]),
+    "proxy_update_wrong_mirror": ("                        val[kvu] = val[kuv];",
+                                  "                        val[kvu] = -1.0;",
+                                  [pins.test_proxy_stream_equals_rebuild_every_frame]),
 }
 
 

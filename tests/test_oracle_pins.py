@@ -481,3 +481,106 @@ def test_fx_order_of_edits_does_not_matter(orc):
             P.fx_update(Ke, e, m2, ed[i:i + 1], S2, v2)
     assert np.array_equal(S1, S2)
     assert np.array_equal(v1.view(np.uint64), v2.view(np.uint64))
+
+
+# ---------------------------------------------------------------- graph-Laplacian proxy
+
+
+def _proxy_dense(P, val):
+    import scipy.sparse as sp
+    ptr, col = P.proxy_pattern()
+    return sp.csr_matrix((val, col, ptr), shape=(P.n, P.n)).toarray()
+
+
+def _active_edges(tets, mask):
+    """{(u, v): count} over the six edges of every active tetrahedron, both orientations."""
+    cnt = {}
+    for t in np.flatnonzero(mask):
+        q = [int(v) for v in tets[t]]
+        for a in range(4):
+            for b in range(a + 1, 4):
+                for e in ((q[a], q[b]), (q[b], q[a])):
+                    cnt[e] = cnt.get(e, 0) + 1
+    return cnt
+
+
+def test_proxy_rebuild_vs_textbook_laplacian(orc):
+    """Eqs. 1-4 against scipy's graph Laplacian of the active edge set (dense, small meshes),
+    the multiplicities against a count by brute force, the pattern against the node pairs."""
+    from scipy.sparse.csgraph import laplacian
+    rng = np.random.default_rng(21)
+    meshes = [(X.shape[0], tets) for X, tets in _tiny_meshes()]
+    wl = W.plain_small(seed=3, N=3)
+    meshes.append((wl.n_nodes, wl.tets))
+    for n, tets in meshes:
+        T = tets.shape[0]
+        P = orc.Pattern(n, tets)
+        ptr, col = P.proxy_pattern()
+        pairs = {(int(a), int(b)) for t in tets for a in t for b in t}
+        rows = np.repeat(np.arange(n), np.diff(ptr))
+        assert {(int(r), int(c)) for r, c in zip(rows, col)} == pairs
+        for mask in (np.ones(T, np.uint8), (rng.uniform(size=T) < 0.5).astype(np.uint8),
+                     np.zeros(T, np.uint8)):
+            for eps in (0.0, 1e-3, 0.75):
+                mult, deg, val = P.proxy_rebuild(mask, eps)
+                cnt = _active_edges(tets, mask)
+                assert [cnt.get((int(r), int(c)), 0) if r != c else 0
+                        for r, c in zip(rows, col)] == mult.tolist()
+                adj = np.zeros((n, n))
+                for (u, v) in cnt:
+                    adj[u, v] = 1.0
+                in_mesh = np.isin(np.arange(n), tets)   # a node of no tetrahedron: empty row
+                ref = laplacian(adj) + np.diag(np.where(in_mesh, eps, 0.0))
+                got = _proxy_dense(P, val)
+                assert np.array_equal(got, ref)                       # bitwise
+                assert np.array_equal(deg, adj.sum(axis=1).astype(np.int32))
+                assert not np.any(np.signbit(val) & (val == 0))       # no -0.0
+
+
+def test_proxy_invariants_rows_symmetry_components(orc):
+    """L 1 = 0 exactly (row sums = eps), symmetry, and the multiplicity of eigenvalue eps
+    equals the number of connected components of the active graph (isolated nodes too)."""
+    from scipy.sparse.csgraph import connected_components
+    import scipy.sparse as sp
+    for seed in range(3):
+        wl = W.plain_small(seed=seed, N=4, frames=6)
+        P = orc.Pattern(wl.n_nodes, wl.tets)
+        for mask in wl.masks()[::2]:
+            _, _, val = P.proxy_rebuild(mask, 0.25)
+            A = _proxy_dense(P, val)
+            assert np.array_equal(A, A.T)
+            assert np.all(A.sum(axis=1) == 0.25)
+            off = (A != 0) & ~np.eye(wl.n_nodes, dtype=bool)
+            ncomp, _ = connected_components(sp.csr_matrix(off.astype(float)), directed=False)
+            w = np.linalg.eigvalsh(A - 0.25 * np.eye(wl.n_nodes))
+            assert np.sum(np.abs(w) < 1e-9) == ncomp
+            assert w[0] > -1e-9
+
+
+def _proxy_stream(orc, wl, eps=0.0):
+    P = orc.Pattern(wl.n_nodes, wl.tets)
+    ptr, col = P.proxy_pattern()
+    mask = wl.mask0.copy()
+    mult, deg, val = P.proxy_rebuild(mask, eps)
+    for f, ed in enumerate(wl.frames):
+        visited = P.proxy_update(mask, ed, mult, deg, val, eps)
+        ref_mask = W.apply_edits_to_mask(wl.masks()[f], ed)
+        assert np.array_equal(mask, ref_mask)
+        rm, rd, rv = P.proxy_rebuild(mask, eps)
+        assert np.array_equal(mult, rm) and np.array_equal(deg, rd), f"frame {f}"
+        assert np.array_equal(val.view(np.uint64), rv.view(np.uint64)), f"frame {f}"
+        # visited entries: both entries of every edge and the diagonal of every node of an
+        # edited tetrahedron, counted by a set
+        edited = np.concatenate([ed[:, 1], ed[ed[:, 0] == 2, 2]])
+        ents = {(int(a), int(b)) for t in edited for a in wl.tets[t] for b in wl.tets[t]}
+        assert visited == len(ents)
+
+
+def test_proxy_stream_equals_rebuild_every_frame(orc):
+    """Sec. 3.3 invariant for the proxy's streaming rule (Sec. 3.2), bitwise, every frame."""
+    for seed in range(3):
+        _proxy_stream(orc, W.plain_small(seed=seed))
+    _proxy_stream(orc, W.plain_small(seed=5), eps=1e-3)
+    _proxy_stream(orc, W.prefractured_block(N=8, sites=6, frames=6), eps=0.5)
+    _proxy_stream(orc, W.refinement_hierarchy(N=5, radius=0.3, frames=6))
+    _proxy_stream(orc, W.edge_fan(seed=1, K=40, frames=6))
