@@ -295,6 +295,38 @@ int sta_graph_disable(sta_ctx *ctx, void *stream);
 #define STA_POLICY_FIXED 1
 int sta_set_policy(sta_ctx *ctx, int32_t policy, void *stream);
 
+/*
+ * Graph-Laplacian proxy operator (Sec. 3.1 Eqs. 1-4, Sec. 3.2 Eqs. 5-7, Sec. 3.3,
+ * Algorithm 1).  sta_proxy_create makes a context for the scalar n x n matrix
+ *     A_t = L_t + eps I,   L_t(u, v) = -a_t(u, v) (u != v),   L_t(u, u) = sum_{w != u} a_t(u, w),
+ *     a_t(u, v) = 1[c_t(u, v) > 0],   c_t(u, v) = #active tetrahedra with edge {u, v},
+ * over the same superset mesh and edit model as the elasticity operator.
+ *  - Layout: node-level CSR, n rows; row u holds every node sharing a SUPERSET tetrahedron
+ *    with u (u included), ascending.  Inactive edges keep their slot and hold +0.0, active
+ *    ones -1.0; the diagonal is (double) degree + eps.  A node of no tetrahedron has an empty
+ *    row.  sta_csr returns this CSR (n_rows = n, nnz = n_blocks of sta_sizes).
+ *  - State: the edge multiplicities c_t and node degrees, int32 (sta_proxy_state), the mask
+ *    and the values.  All of it is integer arithmetic, so values are exact.
+ *  - Calls: sta_full_rebuild (count c over the active set, then Eqs. 2-4), sta_refold (the
+ *    same from the current mask), sta_apply_edits / sta_apply_edits_noalloc (the streaming
+ *    rule: +-1 on the multiplicity of each edge of each edited tetrahedron, off-diagonal
+ *    entries set or cleared and the end nodes' degrees moved where a multiplicity moves
+ *    between 0 and > 0), sta_last_touched (entries the last frame visited: both entries of
+ *    each edge and the diagonal entry of each node of the edited tetrahedra), sta_graph_*,
+ *    sta_mask, sta_sizes, sta_spmv, sta_destroy.  The streamed state equals a rebuild on the
+ *    same mask bit for bit.  Calls of the elasticity operator (sta_set_params,
+ *    sta_recompute_elements, sta_element_matrices, sta_scatter_map, sta_adjoint,
+ *    sta_set_policy) return STA_ESTATE.
+ * Create: tets (n_tets x 4 int32, host) as for sta_create; every tetrahedron starts inactive
+ * (A = eps I on the nodes of the mesh).  Limits: n_tets < 2^27, nnz < 2^31.
+ */
+int sta_proxy_create(int64_t n_nodes, const int32_t *tets, int64_t n_tets, double eps,
+                     void *stream, sta_ctx **out);
+/* Device pointers (context-owned): mult[g] = c_t of the edge of block g for each upper block
+ * (col[g] > row node); 0 at every other block; degree[u] = sum_{w != u} a_t(u, w).
+ * STA_ESTATE for an elasticity context.  Either pointer argument may be NULL. */
+int sta_proxy_state(const sta_ctx *ctx, const int32_t **mult, const int32_t **degree);
+
 /* Human-readable message of the last error on the calling thread. */
 const char *sta_last_error(void);
 const char *sta_status_string(int status);

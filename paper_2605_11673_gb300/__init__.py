@@ -29,7 +29,8 @@ EXPORTED = (
     "sta_recompute_elements", "sta_set_params", "sta_element_matrices", "sta_last_error",
     "sta_status_string", "sta_apply_edits_noalloc", "sta_adjoint", "sta_spmv", "sta_set_launch",
     "sta_batch_create", "sta_batch_size", "sta_batch_instance", "sta_batch_apply_edits",
-    "sta_graph_enable", "sta_graph_disable", "sta_set_policy",
+    "sta_graph_enable", "sta_graph_disable", "sta_set_policy", "sta_proxy_create",
+    "sta_proxy_state",
 )
 STA_NOALLOC_MAX_EDITED = 32768
 STA_POLICY_REFOLD = 0
@@ -92,6 +93,8 @@ def load_library(path: Path | str | None = None):
     L.sta_graph_enable.argtypes = [_p, _i64, _p]
     L.sta_graph_disable.argtypes = [_p, _p]
     L.sta_set_policy.argtypes = [_p, C.c_int32, _p]
+    L.sta_proxy_create.argtypes = [_i64, _p, _i64, C.c_double, _p, _P(_p)]
+    L.sta_proxy_state.argtypes = [_p, _P(_p), _P(_p)]
     L.sta_last_error.restype = C.c_char_p
     L.sta_status_string.argtypes = [_int]
     L.sta_status_string.restype = C.c_char_p
@@ -170,6 +173,25 @@ def sta_create(nodes, tets, young, poisson, opt: sta_options | None = None, stre
     return h.value
 
 
+def sta_proxy_create(n_nodes: int, tets, eps: float = 0.0, stream=None) -> int:
+    """Context of the graph-Laplacian proxy operator A = L + eps I (see include/sta.h)."""
+    L = load_library()
+    tets = _host(tets, np.int32).reshape(-1, 4)
+    h = _p()
+    _check(L.sta_proxy_create(int(n_nodes), tets.ctypes.data, tets.shape[0], float(eps),
+                              _stream_handle(stream), C.byref(h)))
+    return h.value
+
+
+def sta_proxy_state(h: int, owner=None):
+    """(mult per block, degree per node) as zero-copy DeviceArrays."""
+    m, d = _p(), _p()
+    _check(load_library().sta_proxy_state(h, C.byref(m), C.byref(d)))
+    s = sta_sizes(h)
+    return (DeviceArray(m.value or 0, (s["n_blocks"],), "<i4", owner),
+            DeviceArray(d.value or 0, (s["n_nodes"],), "<i4", owner))
+
+
 def sta_destroy(h: int) -> None:
     _check(load_library().sta_destroy(h))
 
@@ -211,9 +233,12 @@ def sta_last_touched(h: int, stream=None) -> int:
 
 def sta_sizes(h: int) -> dict:
     n, T, nb, by = _i64(), _i64(), _i64(), _i64()
-    _check(load_library().sta_sizes(h, C.byref(n), C.byref(T), C.byref(nb), C.byref(by)))
-    return {"n_nodes": n.value, "n_tets": T.value, "n_blocks": nb.value, "nnz": 9 * nb.value,
-            "device_bytes": by.value}
+    L = load_library()
+    _check(L.sta_sizes(h, C.byref(n), C.byref(T), C.byref(nb), C.byref(by)))
+    nr, nz = _i64(), _i64()
+    _check(L.sta_csr(h, None, None, None, C.byref(nr), C.byref(nz)))
+    return {"n_nodes": n.value, "n_tets": T.value, "n_blocks": nb.value, "nnz": nz.value,
+            "n_rows": nr.value, "device_bytes": by.value}
 
 
 def sta_csr(h: int, owner=None):
@@ -465,3 +490,18 @@ class BatchAssembler(Assembler):
     def instance_csr(self, i: int):
         rp, col, val, _ = sta_batch_instance(self.h, i, self)
         return rp.torch(), col.torch(), val.torch()
+
+
+class ProxyAssembler(Assembler):
+    """Graph-Laplacian proxy operator A_t = L_t + eps I of one superset mesh (node-level CSR,
+    n rows).  Same edit, rebuild, graph and CSR calls as Assembler."""
+
+    def __init__(self, n_nodes: int, tets, eps: float = 0.0, stream=None):
+        self.h = sta_proxy_create(n_nodes, tets, eps, stream)
+        s = sta_sizes(self.h)
+        self.n_nodes, self.n_tets, self.nnz = s["n_nodes"], s["n_tets"], s["n_blocks"]
+        self.n_rows = self.n_nodes
+
+    def state(self):
+        """(mult, degree) torch tensors viewing the context's device memory."""
+        return tuple(a.torch() for a in sta_proxy_state(self.h, self))

@@ -170,6 +170,65 @@ int sta::create_impl(const double *nodes, int64_t n_nodes, const int32_t *tets, 
     return STA_OK;
 }
 
+extern "C" int sta_proxy_create(int64_t n_nodes, const int32_t *tets, int64_t n_tets, double eps,
+                                void *stream, sta_ctx **out) {
+    if (!out) return fail(STA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_nodes < 0 || n_tets < 0) return fail(STA_EINVAL, "negative size");
+    if (n_tets > 0 && !tets) return fail(STA_EINVAL, "NULL input array");
+    if (n_tets >= (1LL << 27)) return fail(STA_ERANGE, "n_tets must be < 2^27");
+    if (n_nodes + 1 > INT32_MAX) return fail(STA_ERANGE, "n_nodes + 1 exceeds int32");
+    for (int64_t t = 0; t < n_tets; ++t) {
+        const int32_t *q = tets + 4 * t;
+        for (int a = 0; a < 4; ++a) {
+            if (q[a] < 0 || q[a] >= n_nodes)
+                return fail(STA_EINVAL, "tet " + std::to_string(t) + ": node id out of range");
+            for (int b = 0; b < a; ++b)
+                if (q[a] == q[b])
+                    return fail(STA_EINVAL, "tet " + std::to_string(t) + ": repeated node");
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    sta_ctx *x = new sta_ctx();
+    Ctx *c = &x->c;
+    c->op = STA_OP_PROXY;
+    c->n = n_nodes;
+    c->T = n_tets;
+    c->eps = eps;
+    int rc = STA_OK;
+    auto bail = [&](int code) {
+        free_ctx(x);
+        return code;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+        return bail(fail(STA_ECUDA, "no CUDA device"));
+    if (cudaEventCreateWithFlags(&x->h2d_done, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(STA_ECUDA, "cudaEventCreate failed"));
+    if ((rc = dev_alloc(c, &c->tets, n_tets)) || (rc = dev_alloc(c, &c->counters, 4)))
+        return bail(rc);
+    if (cudaMemcpyAsync(c->tets, tets, sizeof(int4) * n_tets, cudaMemcpyHostToDevice, s))
+        return bail(fail(STA_ECUDA, "input copy failed"));
+    if ((rc = build_pattern(c, s))) return bail(rc);
+    if ((rc = dev_alloc(c, &c->mask, n_tets)) || (rc = dev_alloc(c, &c->val, c->nnz))) return bail(rc);
+    unsigned long long init[4] = {0ull, 0ull, ~0ull, 0ull};
+    if (cudaMemcpyAsync(c->counters, init, sizeof init, cudaMemcpyHostToDevice, s) ||
+        cudaMemsetAsync(c->mask, 0, (size_t)(n_tets > 0 ? n_tets : 1), s))
+        return bail(fail(STA_ECUDA, "init failed"));
+    if ((rc = launch_proxy_rebuild(c, s))) return bail(rc);  // all inactive: A = eps I
+    if (cudaStreamSynchronize(s) != cudaSuccess)
+        return bail(fail(STA_ECUDA, std::string("proxy create: ") +
+                                        cudaGetErrorString(cudaGetLastError())));
+    c->host_mask.assign((size_t)n_tets, 0);
+    c->seen.assign((size_t)n_tets, 0);
+    c->stamp.assign((size_t)n_tets, 0);
+    c->last_counters = c->counters;
+    if (cudaMallocHost((void **)&x->h_mask, (size_t)(n_tets > 0 ? n_tets : 1)) != cudaSuccess)
+        return bail(fail(STA_ENOMEM, "pinned mask buffer"));
+    *out = x;
+    return STA_OK;
+}
+
 extern "C" {
 
 int sta_destroy(sta_ctx *x) {
@@ -208,7 +267,7 @@ int sta_full_rebuild(sta_ctx *x, const uint8_t *mask, int mask_on_device, void *
         return STA_OK;
     }
     STA_TRY(launch_mask_bits(c, s));
-    return launch_rebuild(c, s);
+    return launch_values(c, s);
 }
 
 int sta_set_launch(sta_ctx *x, int32_t block_threads, int32_t blocks_per_sm) {
@@ -228,7 +287,7 @@ int sta_refold(sta_ctx *x, void *stream) {
         STA_CUDA_TRY(cudaGraphLaunch(x->c.g_refold, (cudaStream_t)stream));
         return STA_OK;
     }
-    return launch_rebuild(&x->c, (cudaStream_t)stream);
+    return launch_values(&x->c, (cudaStream_t)stream);
 }
 
 int sta_apply_edits(sta_ctx *x, const sta_edit *edits, int64_t n_edits, void *stream) {
@@ -380,6 +439,7 @@ int sta_csr(const sta_ctx *x, const int32_t **row_ptr, const int32_t **col, cons
 
 int sta_scatter_map(const sta_ctx *x, const int32_t **scat) {
     if (!x || !scat) return fail(STA_EINVAL, "NULL argument");
+    if (x->c.op != STA_OP_ELASTICITY) return fail(STA_ESTATE, "not an elasticity context");
     *scat = x->c.scat;
     return STA_OK;
 }
@@ -402,6 +462,7 @@ int sta_sizes(const sta_ctx *x, int64_t *n_nodes, int64_t *n_tets, int64_t *n_bl
 
 int sta_recompute_elements(sta_ctx *x, int active_only, void *stream) {
     if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    if (x->c.op != STA_OP_ELASTICITY) return fail(STA_ESTATE, "not an elasticity context");
     STA_TRY(launch_elements(&x->c, active_only != 0, (cudaStream_t)stream));
     if (x->c.policy == STA_POLICY_FIXED) STA_TRY(launch_fx_prepare(&x->c, (cudaStream_t)stream));
     return STA_OK;
@@ -409,6 +470,7 @@ int sta_recompute_elements(sta_ctx *x, int active_only, void *stream) {
 
 int sta_set_policy(sta_ctx *x, int32_t policy, void *stream) {
     if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    if (x->c.op != STA_OP_ELASTICITY) return fail(STA_ESTATE, "not an elasticity context");
     if (policy != STA_POLICY_REFOLD && policy != STA_POLICY_FIXED)
         return fail(STA_EINVAL, "policy must be STA_POLICY_REFOLD or STA_POLICY_FIXED");
     Ctx *c = &x->c;
@@ -422,6 +484,7 @@ int sta_set_policy(sta_ctx *x, int32_t policy, void *stream) {
 int sta_set_params(sta_ctx *x, const double *nodes, const double *young, const double *poisson,
                    int on_device, void *stream) {
     if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    if (x->c.op != STA_OP_ELASTICITY) return fail(STA_ESTATE, "not an elasticity context");
     Ctx *c = &x->c;
     cudaStream_t s = (cudaStream_t)stream;
     if (nodes) {
@@ -464,6 +527,7 @@ int sta_adjoint(sta_ctx *x, const double *grad_val, double *dE, double *dnu, dou
                 void *stream) {
     if (!x) return fail(STA_EINVAL, "ctx is NULL");
     const Ctx *c = &x->c;
+    if (x->c.op != STA_OP_ELASTICITY) return fail(STA_ESTATE, "not an elasticity context");
     if ((c->nnz > 0 && !grad_val) || (c->T > 0 && (!dE || !dnu)) || (c->n > 0 && !dX))
         return fail(STA_EINVAL, "NULL argument");
     return launch_adjoint(&x->c, grad_val, dE, dnu, dX, (cudaStream_t)stream);
@@ -477,6 +541,7 @@ int sta_spmv(sta_ctx *x, const double *val, const double *xv, double *y, void *s
 
 int sta_element_matrices(sta_ctx *x, const int32_t *tet_ids, int64_t n, double *out, void *stream) {
     if (!x || n < 0 || (n > 0 && (!tet_ids || !out))) return fail(STA_EINVAL, "bad argument");
+    if (x->c.op != STA_OP_ELASTICITY) return fail(STA_ESTATE, "not an elasticity context");
     return launch_expand_elements(&x->c, tet_ids, n, out, (cudaStream_t)stream);
 }
 

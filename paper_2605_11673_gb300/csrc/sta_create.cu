@@ -211,7 +211,8 @@ __global__ void k_col(int64_t nblocks, const int32_t *block_node, const int32_t 
 }
 
 // tblk[16 t + 4 la + lb] = block of (v_la, v_lb); scat[144 t + 12 (3la+i) + 3lb + j] = CSR
-// index of (3 v_la + i, 3 v_lb + j).  Position of v_lb in v_la's sorted list by bisection.
+// index of (3 v_la + i, 3 v_lb + j) (skipped when scat is NULL).  Position of v_lb in v_la's
+// sorted list by bisection.
 __global__ void k_tet_maps(const int4 *tets, int64_t T, const int32_t *adj_ptr,
                            const int32_t *adj, int32_t *tblk, int32_t *scat) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
@@ -227,6 +228,7 @@ __global__ void k_tet_maps(const int4 *tets, int64_t T, const int32_t *adj_ptr,
                     if (adj[s + mid] < v[lb]) lo = mid + 1; else hi = mid;
                 }
                 tblk[16 * t + 4 * la + lb] = s + lo;
+                if (!scat) continue;  // proxy operator: blocks only
                 for (int i = 0; i < 3; ++i)
                     for (int j = 0; j < 3; ++j)
                         scat[144 * t + 12 * (3 * la + i) + 3 * lb + j] =
@@ -483,6 +485,23 @@ int build_pattern(Ctx *c, cudaStream_t s) {
                                  cudaMemcpyDeviceToHost, s));
     STA_CUDA_TRY(cudaStreamSynchronize(s));
     STA_CUDA_TRY(cudaGetLastError());
+    if (c->op == STA_OP_PROXY) {  // node-level pattern, slot blocks and mirrors only
+        if (nblocks > INT32_MAX)
+            return fail(STA_ERANGE, "nnz = " + std::to_string(nblocks) + " exceeds int32");
+        c->nblocks = nblocks;
+        int32_t *tblk = nullptr;
+        STA_TRY(sc.get(&tblk, 16 * T));
+        STA_TRY(dev_alloc(c, &c->adj_ptr, n + 1));
+        STA_TRY(dev_alloc(c, &c->adj, nblocks));
+        STA_TRY(dev_alloc(c, &c->block_node, nblocks));
+        k_adj_fill<<<grid_for(n + 1), TPB, 0, s>>>(n, nt_ptr, scratch, adj_ptr64, c->adj_ptr,
+                                                   c->adj, c->block_node);
+        k_tet_maps<<<grid_for(T), TPB, 0, s>>>(c->tets, T, c->adj_ptr, c->adj, tblk, nullptr);
+        STA_TRY(build_proxy_maps(c, tblk, s));
+        STA_CUDA_TRY(cudaGetLastError());
+        STA_CUDA_TRY(cudaStreamSynchronize(s));  // the scratch is freed on return
+        return STA_OK;
+    }
     if (9 * nblocks > INT32_MAX)
         return fail(STA_ERANGE, "nnz = " + std::to_string(9 * nblocks) + " exceeds int32");
     c->nblocks = nblocks;

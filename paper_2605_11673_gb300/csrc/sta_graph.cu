@@ -82,11 +82,11 @@ extern "C" int sta_graph_enable(sta_ctx *x, int64_t max_edited, void *stream) {
              return launch_stream_frame(c, c->d_gframe, c->gcap, s);
          }, &c->g_stream)))
         return bail(rc);
-    if ((rc = capture(cs, [&](cudaStream_t s) { return launch_rebuild(c, s); }, &c->g_refold)))
+    if ((rc = capture(cs, [&](cudaStream_t s) { return launch_values(c, s); }, &c->g_refold)))
         return bail(rc);
     if ((rc = capture(cs, [&](cudaStream_t s) {
              int r = launch_mask_bits(c, s);
-             return r != STA_OK ? r : launch_rebuild(c, s);
+             return r != STA_OK ? r : launch_values(c, s);
          }, &c->g_rebuild)))
         return bail(rc);
     cudaStreamDestroy(cs);

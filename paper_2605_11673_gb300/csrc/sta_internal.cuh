@@ -124,7 +124,13 @@ inline size_t frame_bytes(int64_t m) { return sizeof(FrameHeader) + sizeof(int32
 // ------------------------------------------------------------------------------------
 // Context
 // ------------------------------------------------------------------------------------
+// Operator of a context: the elasticity operator (sta_create, sta_batch_create) or the
+// graph-Laplacian proxy (sta_proxy_create).
+constexpr int STA_OP_ELASTICITY = 0;
+constexpr int STA_OP_PROXY = 1;
+
 struct Ctx {
+    int op = STA_OP_ELASTICITY;
     int64_t n = 0, T = 0, nblocks = 0, nnz = 0, nrows = 0;
     double eps = 0.0;
     int block_threads = 256;
@@ -186,6 +192,15 @@ struct Ctx {
     std::vector<uint8_t> stamp;   // host: edit-list duplicate check, stamp_gen = "seen"; one
     uint8_t stamp_gen = 0;        // byte per tet keeps it and the mask mirror cache-resident
 
+    // graph-Laplacian proxy operator (sta_proxy.cu); its CSR is the node-level pattern
+    // (row_ptr = adj_ptr, col = adj, nrows = n, nnz = nblocks)
+    int32_t *ptblk = nullptr;   // T x 10: block of tet t's unit slot s (diagonal; upper edge block)
+    int32_t *pmir = nullptr;    // nblocks: block (b, a) of block (a, b)
+    int32_t *pdiag = nullptr;   // n: diagonal block of each node, -1 for a node of no tetrahedron
+    int32_t *pmult = nullptr;   // nblocks + n: edge multiplicity at the upper block, then degrees
+    uint32_t *pflag = nullptr;  // nblocks: claim flags of the frame's touched blocks
+    int32_t *plist = nullptr;   // nblocks: the frame's touched blocks
+
     // CUDA-graph mode (sta_graph_enable): captured frame sequences and fixed staging
     bool graph_on = false;
     cudaGraphExec_t g_stream = nullptr, g_refold = nullptr, g_rebuild = nullptr;
@@ -239,6 +254,11 @@ int launch_fx_rebuild(Ctx *c, cudaStream_t s);
 int launch_fx_frame(Ctx *c, const int32_t *edited, int64_t m, const int64_t *m_dev, int64_t cap,
                     int32_t *touched, unsigned long long *counters, cudaStream_t s);
 int launch_mask_bits(Ctx *c, cudaStream_t s);                    // codes <- mask
+int launch_values(Ctx *c, cudaStream_t s);  // the operator's rebuild (elasticity or proxy)
+int build_proxy_maps(Ctx *c, const int32_t *tblk, cudaStream_t s);  // sta_proxy.cu
+int launch_proxy_rebuild(Ctx *c, cudaStream_t s);
+int launch_proxy_frame(Ctx *c, const int32_t *edited, int64_t m, const int64_t *m_dev,
+                       int64_t cap, int32_t *list, unsigned long long *counters, cudaStream_t s);
 int launch_stream_scratch(Ctx *c, int64_t m, const int32_t *d_edited, int32_t *touched,
                           unsigned long long *counters, cudaStream_t s);
 

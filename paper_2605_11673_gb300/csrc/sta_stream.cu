@@ -198,7 +198,7 @@ int launch_fold_list(Ctx *c, const int32_t *list, const unsigned long long *coun
 }
 
 int launch_mask_bits(Ctx *c, cudaStream_t s) {
-    if (c->T == 0) return STA_OK;
+    if (c->T == 0 || c->op == STA_OP_PROXY) return STA_OK;  // the proxy reads the mask itself
     const int64_t n = 10 * c->T;
     int64_t grid = (n + 255) / 256;
     const int64_t cap = (int64_t)c->num_sms * 8;
@@ -208,11 +208,19 @@ int launch_mask_bits(Ctx *c, cudaStream_t s) {
     return STA_OK;
 }
 
+// Every value from the current mask: the operator's full rebuild.
+int launch_values(Ctx *c, cudaStream_t s) {
+    return c->op == STA_OP_PROXY ? launch_proxy_rebuild(c, s) : launch_rebuild(c, s);
+}
+
 // One streaming frame: claim kernel, then the fold of the touched units.  `frame` is a device
 // frame block (FrameHeader + edited list) already holding the frame; the count is read from
 // it, grids are sized for `cap` edited tetrahedra (so the sequence can be captured once and
 // replayed for any frame up to `cap`).
 int launch_stream_frame(Ctx *c, FrameHeader *frame, int64_t cap, cudaStream_t s) {
+    if (c->op == STA_OP_PROXY)
+        return launch_proxy_frame(c, frame_edited(frame), 0, &frame->m, cap, c->plist,
+                                  frame_counters(frame), s);
     if (c->policy == STA_POLICY_FIXED)
         return launch_fx_frame(c, frame_edited(frame), 0, &frame->m, cap, c->touched,
                                frame_counters(frame), s);
@@ -235,7 +243,9 @@ int launch_stream_frame(Ctx *c, FrameHeader *frame, int64_t cap, cudaStream_t s)
 int launch_stream_scratch(Ctx *c, int64_t m, const int32_t *d_edited, int32_t *touched,
                           unsigned long long *counters, cudaStream_t s) {
     STA_CUDA_TRY(cudaMemsetAsync(counters + 1, 0, 3 * sizeof(unsigned long long), s));
-    if (m > 0 && c->policy == STA_POLICY_FIXED) {
+    if (m > 0 && c->op == STA_OP_PROXY) {
+        STA_TRY(launch_proxy_frame(c, d_edited, m, nullptr, m, touched, counters, s));
+    } else if (m > 0 && c->policy == STA_POLICY_FIXED) {
         STA_TRY(launch_fx_frame(c, d_edited, m, nullptr, m, touched, counters, s));
     } else if (m > 0) {
         const int threads = 256;
