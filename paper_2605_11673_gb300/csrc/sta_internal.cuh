@@ -196,6 +196,7 @@ struct Ctx {
     // (row_ptr = adj_ptr, col = adj, nrows = n, nnz = nblocks)
     int32_t *ptblk = nullptr;   // T x 10: block of tet t's unit slot s (diagonal; upper edge block)
     int32_t *pmir = nullptr;    // nblocks: block (b, a) of block (a, b)
+    int32_t *pup = nullptr;     // nblocks: upper block of the block's edge, -1 on the diagonal
     int32_t *pdiag = nullptr;   // n: diagonal block of each node, -1 for a node of no tetrahedron
     int32_t *pmult = nullptr;   // nblocks + n: edge multiplicity at the upper block, then degrees
     uint32_t *pflag = nullptr;  // nblocks: claim flags of the frame's touched blocks

@@ -44,17 +44,19 @@ __global__ void k_proxy_slots(const int4 *__restrict__ tets, int64_t T,
     }
 }
 
-// pmir[g]: the block (b, a) of block g = (a, b) (a diagonal block is its own); pdiag[a]: the
+// pmir[g]: the block (b, a) of block g = (a, b) (a diagonal block is its own); pup[g]: the
+// upper block of g's edge (g itself or its mirror), -1 for a diagonal block; pdiag[a]: the
 // diagonal block of node a (left at -1 for a node of no tetrahedron).
 __global__ void k_proxy_block_maps(int64_t nblocks, const int32_t *__restrict__ block_node,
                                    const int32_t *__restrict__ adj,
                                    const int32_t *__restrict__ adj_ptr, int32_t *__restrict__ pmir,
-                                   int32_t *__restrict__ pdiag) {
+                                   int32_t *__restrict__ pup, int32_t *__restrict__ pdiag) {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nblocks;
          g += (int64_t)gridDim.x * blockDim.x) {
         const int32_t a = block_node[g], b = adj[g];
         if (a == b) {
             pmir[g] = (int32_t)g;
+            pup[g] = -1;
             pdiag[a] = (int32_t)g;
             continue;
         }
@@ -64,18 +66,22 @@ __global__ void k_proxy_block_maps(int64_t nblocks, const int32_t *__restrict__ 
             if (adj[mid] < a) lo = mid + 1; else hi = mid;
         }
         pmir[g] = lo;
+        pup[g] = b > a ? (int32_t)g : lo;
     }
 }
 
-// Eq. 1 over the active set: +1 on the multiplicity of each of the six edges.
+// Eq. 1 over the active set: +1 on the multiplicity of each of the six edges.  The edge
+// blocks are loaded together with the mask byte (not after it), so one memory round trip
+// serves each tetrahedron.
 __global__ void k_proxy_count(const uint8_t *__restrict__ mask, const int32_t *__restrict__ ptblk,
                               int64_t T, int32_t *__restrict__ mult) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
          t += (int64_t)gridDim.x * blockDim.x) {
-        if (!mask[t]) continue;
         // the six edge blocks: ints 10 t + 4 .. 10 t + 9, an 8-byte aligned run
         const int2 *e = reinterpret_cast<const int2 *>(ptblk + 10 * t + 4);
-        const int2 e0 = e[0], e1 = e[1], e2 = e[2];
+        const uint8_t on = __ldg(mask + t);
+        const int2 e0 = __ldg(e), e1 = __ldg(e + 1), e2 = __ldg(e + 2);
+        if (!on) continue;
         atomicAdd(&mult[e0.x], 1);
         atomicAdd(&mult[e0.y], 1);
         atomicAdd(&mult[e1.x], 1);
@@ -88,9 +94,8 @@ __global__ void k_proxy_count(const uint8_t *__restrict__ mask, const int32_t *_
 // Eqs. 2-3 for every off-diagonal block: -a_t, and the degree of the row's node (Eq. 3's
 // diagonal sum) as a count of the active entries, added once per node and warp.
 __global__ void k_proxy_offdiag(int64_t nblocks, const int32_t *__restrict__ block_node,
-                                const int32_t *__restrict__ adj, const int32_t *__restrict__ pmir,
-                                const int32_t *__restrict__ mult, int32_t *__restrict__ deg,
-                                double *__restrict__ val) {
+                                const int32_t *__restrict__ pup, const int32_t *__restrict__ mult,
+                                int32_t *__restrict__ deg, double *__restrict__ val) {
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < nblocks;
@@ -100,9 +105,8 @@ __global__ void k_proxy_offdiag(int64_t nblocks, const int32_t *__restrict__ blo
         bool on = false;
         if (g < nblocks) {
             a = block_node[g];
-            const int32_t b = adj[g];
-            if (a != b) {
-                const int32_t up = b > a ? (int32_t)g : pmir[g];
+            const int32_t up = pup[g];
+            if (up >= 0) {
                 on = mult[up] > 0;
                 val[g] = on ? -1.0 : 0.0;
             }
@@ -204,6 +208,7 @@ int build_proxy_maps(Ctx *c, const int32_t *tblk, cudaStream_t s) {
     const int64_t n = c->n, T = c->T, nb = c->nblocks;
     STA_TRY(dev_alloc(c, &c->ptblk, 10 * T));
     STA_TRY(dev_alloc(c, &c->pmir, nb));
+    STA_TRY(dev_alloc(c, &c->pup, nb));
     STA_TRY(dev_alloc(c, &c->pdiag, n));
     STA_TRY(dev_alloc(c, &c->pmult, nb + n));
     STA_TRY(dev_alloc(c, &c->pflag, nb));
@@ -214,7 +219,8 @@ int build_proxy_maps(Ctx *c, const int32_t *tblk, cudaStream_t s) {
     if (T > 0) k_proxy_slots<<<px_grid(c, T, 16), PX_TPB, 0, s>>>(c->tets, T, tblk, c->ptblk);
     if (nb > 0)
         k_proxy_block_maps<<<px_grid(c, nb, 16), PX_TPB, 0, s>>>(nb, c->block_node, c->adj,
-                                                                 c->adj_ptr, c->pmir, c->pdiag);
+                                                                 c->adj_ptr, c->pmir, c->pup,
+                                                                 c->pdiag);
     STA_CUDA_TRY(cudaGetLastError());
     // the node-level pattern is the proxy's CSR (sta_csr, sta_spmv)
     c->row_ptr = c->adj_ptr;
@@ -230,8 +236,8 @@ int launch_proxy_rebuild(Ctx *c, cudaStream_t s) {
     STA_CUDA_TRY(cudaMemsetAsync(c->pmult, 0, sizeof(int32_t) * (size_t)(nb + n > 0 ? nb + n : 1), s));
     if (T > 0) k_proxy_count<<<px_grid(c, T), PX_TPB, 0, s>>>(c->mask, c->ptblk, T, c->pmult);
     if (nb > 0)
-        k_proxy_offdiag<<<px_grid(c, nb), PX_TPB, 0, s>>>(nb, c->block_node, c->adj, c->pmir,
-                                                          c->pmult, deg, c->val);
+        k_proxy_offdiag<<<px_grid(c, nb), PX_TPB, 0, s>>>(nb, c->block_node, c->pup, c->pmult,
+                                                          deg, c->val);
     if (n > 0) k_proxy_diag<<<px_grid(c, n), PX_TPB, 0, s>>>(n, c->pdiag, deg, c->eps, c->val);
     STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;

@@ -10,10 +10,11 @@
             <workload> <out.json> [command]
         DRAM bytes per launch of the first matching launch, recorded with the hash of the
         rebuild kernel's source (bench.py reports the traffic only while that hash matches)
-    python -m paper_2605_11673_gb300.ncu_summary run <prefractured|refinement> [--stream]
-        the program to capture: one context on the workload, sta_full_rebuild of the initial
-        mask, 3 sta_refold calls after 256 MiB L2 flushes, and (--stream) the 24-frame edit
-        stream through sta_apply_edits without CUDA graphs, each frame after a flush
+    python -m paper_2605_11673_gb300.ncu_summary run <prefractured|refinement> [--stream] [--proxy]
+        the program to capture: one context on the workload (--proxy: the graph-Laplacian
+        proxy operator), sta_full_rebuild of the initial mask, 3 sta_refold calls after
+        256 MiB L2 flushes, and (--stream) the 24-frame edit stream through sta_apply_edits
+        without CUDA graphs, each frame after a flush
 """
 from __future__ import annotations
 
@@ -119,13 +120,14 @@ def traffic(rep: str, kernel: str, workload: str, out_json: str, command: str = 
     return rec
 
 
-def run(workload: str, stream: bool = False) -> None:
+def run(workload: str, stream: bool = False, proxy: bool = False) -> None:
     import torch
     import paper_2605_11673_gb300 as P
     sys.path.insert(0, str(Path(__file__).resolve().parent.parent))
     import workloads as W
     wl = {"prefractured": W.prefractured_block, "refinement": W.refinement_hierarchy}[workload]()
-    asm = P.Assembler(wl.X, wl.tets, wl.E, wl.nu)
+    asm = (P.ProxyAssembler(wl.n_nodes, wl.tets, eps=1e-3) if proxy
+           else P.Assembler(wl.X, wl.tets, wl.E, wl.nu))
     asm.full_rebuild(wl.mask0)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(3):
@@ -143,7 +145,7 @@ def run(workload: str, stream: bool = False) -> None:
 if __name__ == "__main__":
     cmd, args = sys.argv[1], sys.argv[2:]
     if cmd == "run":
-        run(args[0], "--stream" in args)
+        run(args[0], "--stream" in args, "--proxy" in args)
     elif cmd == "launches":
         print(launches(args[0]))
     elif cmd == "full":

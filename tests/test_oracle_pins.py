@@ -584,3 +584,19 @@ def test_proxy_stream_equals_rebuild_every_frame(orc):
     _proxy_stream(orc, W.prefractured_block(N=8, sites=6, frames=6), eps=0.5)
     _proxy_stream(orc, W.refinement_hierarchy(N=5, radius=0.3, frames=6))
     _proxy_stream(orc, W.edge_fan(seed=1, K=40, frames=6))
+
+
+def test_slab_cycles_workload_is_a_valid_repeated_edit_stream(orc):
+    """Sec. 6.5 workload: the same slab deleted and reinserted, the mask back at mask0 every
+    two frames, the slab growing with its half-width."""
+    sizes = []
+    for hw in (0.01, 0.02, 0.04, 0.08):
+        wl = W.slab_cycles(N=8, half_width=hw, frames=6)
+        masks = wl.masks()
+        for f, ed in enumerate(wl.frames):
+            assert orc.validate_edits(wl.n_tets, masks[f], ed) == 0
+        for f in range(0, len(masks), 2):
+            assert (masks[f] == wl.mask0).all()
+        assert set(wl.frames[0][:, 1]) == set(wl.frames[1][:, 1])
+        sizes.append(wl.meta["slab_tets"])
+    assert sizes == sorted(sizes) and sizes[0] > 0

@@ -304,6 +304,30 @@ def _red_children(tets: np.ndarray, mid) -> np.ndarray:
     return np.stack([np.stack(k, -1) for k in kids], 1)
 
 
+def slab_cycles(seed: int = 0, N: int = 12, half_width: float = 0.04, frames: int = 8) -> Workload:
+    """Spatiotemporal edit locality (Sec. 6.4 locality sweep, Sec. 6.5 repeated edits): the
+    unit cube, N^3 hexes x 6 (N = 12: 10,368 tets, the size of the paper's smallest model),
+    jitter +-0.15h, E lognormal (median 1e5, sigma 0.3), nu = 0.3, all active at start.  The
+    slab: the tets whose centroid lies within half_width of a plane through a seeded point of
+    [0.35, 0.65]^3 with a seeded unit normal (the paper's "adaptively chosen" slab placement
+    is not specified).  Even frames delete the slab's tets, odd frames reinsert them, so the
+    same region is edited frame after frame and the mask returns to mask0 every 2 frames."""
+    rng = rng_for(7, seed)
+    X, tets, gi = kuhn_cube(N, 0.15, rng)
+    T = tets.shape[0]
+    p0 = rng.uniform(0.35, 0.65, 3)
+    nrm = rng.standard_normal(3)
+    nrm /= np.linalg.norm(nrm)
+    cen = X[tets].mean(axis=1)
+    slab = np.flatnonzero(np.abs((cen - p0) @ nrm) <= half_width)
+    mask0 = np.ones(T, np.uint8)
+    fr = [make_edits(off=slab) if f % 2 == 0 else make_edits(on=slab) for f in range(frames)]
+    return Workload(f"slab_cycles_N{N}_hw{half_width}", X, tets, lognormal_E(rng, T),
+                    np.full(T, 0.3), mask0, fr,
+                    {"N": N, "half_width": half_width, "slab_tets": int(slab.size),
+                     "grid_index": gi})
+
+
 def refinement_hierarchy(seed: int = 0, N: int = 30, radius: float = 0.15, frames: int = 24
                          ) -> Workload:
     """Refinement hierarchy: N^3 hexes x 6 coarse tets (no jitter), each with its 8
