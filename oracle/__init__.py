@@ -6,7 +6,8 @@ its binding) never imports, links or runs it, and the two share no code.
 
 Functions follow STA-FEM (arXiv 2605.11673): Eq. 8 for the assembled operator, Sec. 3.3 for
 the rebuild-equality invariant, Sec. 3.5 for the full_rebuild / local_recompute /
-streaming_update policies, Eqs. 1-7 and Algorithm 1 for the graph-Laplacian proxy operator.  See sta_oracle.c for the element formula and summation order.
+streaming_update policies, Eqs. 1-7 and Algorithm 1 for the graph-Laplacian proxy operator,
+Eq. 9 (Sec. 6.2) for the implicit-Euler step with the lumped mass.  See sta_oracle.c for the element formula and summation order.
 """
 from __future__ import annotations
 
@@ -91,6 +92,8 @@ def lib(path=None):
         L.orc_proxy_rebuild.restype = None
         L.orc_proxy_update.argtypes = [_p, _p, _p, _i64, _f64, _p, _p, _p]
         L.orc_proxy_update.restype = _i64
+        L.orc_lumped_mass.argtypes = [_p, _p, _f64, _p, _p]
+        L.orc_lumped_mass.restype = None
         _lib = L
     return _lib
 
@@ -263,6 +266,13 @@ class Pattern:
             raise ValueError(f"invalid edit at index {-r - 2}")
         return int(r)
 
+    def lumped_mass(self, X, rho: float, mask) -> np.ndarray:
+        """Nodal lumped mass (n,) of the active set (see orc_lumped_mass)."""
+        m = np.zeros(self.n)
+        lib().orc_lumped_mass(self._h, _ptr(_c(X, np.float64)), float(rho),
+                              _ptr(_c(mask, np.uint8)), _ptr(m))
+        return m
+
     def grad_all(self, X, E, nu, mask, grad_val):
         """Reference gradients (dE, dnu per tet, dX (n, 3)) for upstream dL/dval."""
         X = _c(X, np.float64)
@@ -282,6 +292,32 @@ class Pattern:
         """scipy CSR matrix with this pattern and the given values."""
         import scipy.sparse as sp
         return sp.csr_matrix((val, self.col, self.row_ptr), shape=(self.nrows, self.nrows))
+
+
+def dyn_free(mass, clamped):
+    """DOFs the implicit-Euler step solves for: nodes not clamped and with mass (3 per node)."""
+    return np.repeat((~np.asarray(clamped, bool)) & (np.asarray(mass) > 0), 3)
+
+
+def implicit_euler_step(K, mass, u, v, f, h: float, clamped):
+    """One step of Sec. 6.2, Eq. 9:  (M + h^2 K) u1 = M (u + h v) + h^2 f  on the free DOFs
+    (dyn_free), by a sparse direct solve (scipy spsolve), v1 = (u1 - u) / h there; a clamped
+    DOF stays 0 and a DOF of a node without mass keeps its displacement with velocity 0.
+    K: the assembled operator (scipy sparse, 3n x 3n); mass: nodal lumped mass (n,);
+    b_i = m_i (u_i + h v_i) + (h h) f_i."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    m3 = np.repeat(np.asarray(mass, np.float64), 3)
+    free = dyn_free(mass, clamped)
+    idx = np.flatnonzero(free)
+    A = (sp.diags(m3) + (h * h) * K.tocsr())[idx][:, idx].tocsc()
+    b = m3 * (u + h * v) + (h * h) * f
+    u1 = np.where(np.repeat(np.asarray(clamped, bool), 3), 0.0, u).astype(np.float64)
+    v1 = np.zeros_like(u1)
+    if idx.size:
+        u1[idx] = spla.spsolve(A, b[idx])
+        v1[idx] = (u1[idx] - u[idx]) / h
+    return u1, v1
 
 
 def validate_edits(T: int, mask, edits) -> int:

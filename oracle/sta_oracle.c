@@ -729,6 +729,46 @@ int64_t orc_proxy_update(const orc_pattern_t *p, uint8_t *mask, const orc_edit *
 }
 
 /* ------------------------------------------------------------------------------------- */
+/* Lumped mass of the implicit-Euler loop (Sec. 6.2, Eq. 9)                                 */
+/* ------------------------------------------------------------------------------------- */
+
+/*
+ * M_t of Eq. 9, the "maintained lumped mass matrix" (the paper gives no formula).  Reading:
+ * row-sum lumping of the consistent P1 mass, so every active tetrahedron gives a quarter of
+ * its mass to each of its four nodes, for each of the node's three DOFs:
+ *     m_v = sum over active tau containing v, in ascending tau, of (rho * V_tau) * 0.25,
+ * folded from +0.0 (the summation-order reading of the stiffness); V_tau = det / 6 with det
+ * evaluated as in orc_element (d_k = x_k - x_0, c_1 = d_2 x d_3 with the fma order there,
+ * det = fma(d_1.z, c_1.z, fma(d_1.y, c_1.y, d_1.x c_1.x))).  A node of no active tetrahedron
+ * has mass +0.0.
+ */
+static double tet_volume(const double *X, const int32_t *tv)
+{
+    double d[3][3];
+    for (int k = 1; k <= 3; ++k)
+        for (int m = 0; m < 3; ++m) d[k - 1][m] = X[3 * (int64_t)tv[k] + m] - X[3 * (int64_t)tv[0] + m];
+    double c0 = fma(d[1][1], d[2][2], -(d[1][2] * d[2][1]));
+    double c1 = fma(d[1][2], d[2][0], -(d[1][0] * d[2][2]));
+    double c2 = fma(d[1][0], d[2][1], -(d[1][1] * d[2][0]));
+    double det = fma(d[0][2], c2, fma(d[0][1], c1, d[0][0] * c0));
+    return det / 6.0;
+}
+
+void orc_lumped_mass(const orc_pattern_t *p, const double *X, double rho, const uint8_t *mask,
+                     double *mass)
+{
+    for (int64_t v = 0; v < p->n; ++v) {
+        double m = 0.0;
+        for (int64_t q = p->nt_ptr[v]; q < p->nt_ptr[v + 1]; ++q) {
+            int64_t t = p->nt_list[q];
+            if (!mask[t]) continue;
+            m += (rho * tet_volume(X, p->tets + 4 * t)) * 0.25;
+        }
+        mass[v] = m;
+    }
+}
+
+/* ------------------------------------------------------------------------------------- */
 /* Gradient reference (adjoint form)                                                        */
 /* ------------------------------------------------------------------------------------- */
 

@@ -56,6 +56,12 @@ MUTATIONS = {
     "proxy_update_wrong_mirror": ("                        val[kvu] = val[kuv];",
                                   "                        val[kvu] = -1.0;",
                                   [pins.test_proxy_stream_equals_rebuild_every_frame]),
+    "mass_half_not_quarter": ("            m += (rho * tet_volume(X, p->tets + 4 * t)) * 0.25;",
+                              "            m += (rho * tet_volume(X, p->tets + 4 * t)) * 0.5;",
+                              [pins.test_lumped_mass_vs_volumes]),
+    "mass_volume_cross_sign": ("    double c1 = fma(d[1][2], d[2][0], -(d[1][0] * d[2][2]));",
+                               "    double c1 = fma(d[1][0], d[2][2], -(d[1][2] * d[2][0]));",
+                               [pins.test_lumped_mass_vs_volumes]),
 }
 
 

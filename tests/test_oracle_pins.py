@@ -600,3 +600,78 @@ def test_slab_cycles_workload_is_a_valid_repeated_edit_stream(orc):
         assert set(wl.frames[0][:, 1]) == set(wl.frames[1][:, 1])
         sizes.append(wl.meta["slab_tets"])
     assert sizes == sorted(sizes) and sizes[0] > 0
+
+
+# ---------------------------------------------------------------- implicit-Euler loop (Eq. 9)
+
+
+def test_lumped_mass_vs_volumes(orc):
+    """m_v = sum of rho V / 4 over the active tets at v: total = rho * active volume (numpy
+    determinants, computed independently), node by node, the unit right tet exactly, and +0.0
+    for nodes without an active tet."""
+    rng = np.random.default_rng(31)
+    wl = W.plain_small(seed=2, N=4, frames=4)
+    P = orc.Pattern(wl.n_nodes, wl.tets)
+    for mask in wl.masks()[::2] + [np.zeros(wl.n_tets, np.uint8)]:
+        rho = float(rng.uniform(1.0, 2000.0))
+        m = P.lumped_mass(wl.X, rho, mask)
+        act = np.flatnonzero(mask)
+        x = wl.X[wl.tets[act]]
+        vol = np.linalg.det(x[:, 1:] - x[:, :1]) / 6.0
+        ref = np.zeros(wl.n_nodes)
+        np.add.at(ref, wl.tets[act].reshape(-1), np.repeat(rho * vol / 4.0, 4))
+        assert np.allclose(m, ref, rtol=1e-13, atol=0.0)
+        assert abs(m.sum() - rho * vol.sum()) <= 1e-12 * max(1.0, rho * vol.sum())
+        untouched = ~np.isin(np.arange(wl.n_nodes), wl.tets[act])
+        assert np.all(m[untouched] == 0.0) and not np.any(np.signbit(m))
+    X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [5, 5, 5]], float)
+    P1 = orc.Pattern(5, np.array([[0, 1, 2, 3]], np.int32))
+    assert P1.lumped_mass(X, 24.0, np.ones(1, np.uint8)).tolist() == [1.0, 1.0, 1.0, 1.0, 0.0]
+
+
+def test_implicit_euler_step_closed_forms(orc):
+    """Eq. 9 step: with K = 0 it is u + h v + h^2 f / m; for large h it tends to the static
+    solve K_ff u = f_f; a single free node against numpy's dense solve; clamped DOFs stay 0
+    and massless ones keep their displacement with zero velocity."""
+    import scipy.sparse as sp
+    wl = W.adjoint_block(N=4)
+    n = wl.n_nodes
+    Ke, bad = orc.element_all(wl.X, wl.tets, wl.E, wl.nu)
+    P = orc.Pattern(n, wl.tets)
+    mask = wl.mask0.copy()
+    K = P.csr(P.rebuild(Ke, mask))
+    mass = P.lumped_mass(wl.X, 1000.0, mask)
+    clamped = wl.meta["clamped_nodes"]
+    rng = np.random.default_rng(5)
+    u, v, f = (rng.standard_normal(3 * n) for _ in range(3))
+    h = 1e-2
+    free = orc.dyn_free(mass, clamped)
+    u1, v1 = orc.implicit_euler_step(sp.csr_matrix(K.shape), mass, u, v, f, h, clamped)
+    m3 = np.repeat(mass, 3)
+    ref = u + h * v + h * h * f / np.where(m3 > 0, m3, 1.0)
+    assert np.allclose(u1[free], ref[free], rtol=1e-13, atol=1e-15)
+    assert np.all(u1[np.repeat(clamped, 3)] == 0.0) and np.all(v1[~free] == 0.0)
+    assert np.allclose(v1[free], (u1[free] - u[free]) / h, rtol=1e-15)
+    # static limit: (M / h^2 + K) u1 = M (u + h v) / h^2 + f -> K u = f as h grows
+    f0 = wl.meta["load"]
+    us = orc.solve_free(K, f0, free)
+    ul, _ = orc.implicit_euler_step(K, mass, np.zeros(3 * n), np.zeros(3 * n), f0, 1e6, clamped)
+    assert np.linalg.norm(ul - us) <= 1e-6 * np.linalg.norm(us)
+    # at rest with no load it stays at rest
+    z, zv = orc.implicit_euler_step(K, mass, np.zeros(3 * n), np.zeros(3 * n), np.zeros(3 * n),
+                                    h, clamped)
+    assert not np.any(z) and not np.any(zv)
+    # one tet, three nodes clamped: a 3x3 system for the free node
+    X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0.2, 0.3, 1.1], [4, 4, 4]], float)
+    tets = np.array([[0, 1, 2, 3]], np.int32)
+    K1, _ = orc.element_all(X, tets, np.array([3e4]), np.array([0.3]))
+    P1 = orc.Pattern(5, tets)
+    Kc = P1.csr(P1.rebuild(K1, np.ones(1, np.uint8)))
+    m1 = P1.lumped_mass(X, 500.0, np.ones(1, np.uint8))
+    cl = np.array([1, 1, 1, 0, 0], bool)
+    u0, v0, f1 = (rng.standard_normal(15) for _ in range(3))
+    got, _ = orc.implicit_euler_step(Kc, m1, u0, v0, f1, 0.05, cl)
+    A = m1[3] * np.eye(3) + 0.05 ** 2 * K1[0].reshape(12, 12)[9:, 9:]
+    want = np.linalg.solve(A, m1[3] * (u0[9:12] + 0.05 * v0[9:12]) + 0.05 ** 2 * f1[9:12])
+    assert np.allclose(got[9:12], want, rtol=1e-12)
+    assert np.all(got[:9] == 0.0) and np.array_equal(got[12:], u0[12:])   # node 4: no mass
