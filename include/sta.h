@@ -327,6 +327,37 @@ int sta_proxy_create(int64_t n_nodes, const int32_t *tets, int64_t n_tets, doubl
  * STA_ESTATE for an elasticity context.  Either pointer argument may be NULL. */
 int sta_proxy_state(const sta_ctx *ctx, const int32_t **mult, const int32_t **degree);
 
+/*
+ * Implicit-Euler dynamic loop on the maintained operator (Sec. 6.2, Eq. 9): each step solves
+ *     (M_t + h^2 K_t) u_{t+1} = M_t (u_t + h v_t) + h^2 f,   v_{t+1} = (u_{t+1} - u_t) / h,
+ * with K_t the context's current values (eps included) and M_t a lumped mass maintained with
+ * the mask.  Elasticity contexts only (STA_ESTATE otherwise).
+ *  - Lumped mass (the paper gives no formula): each active tetrahedron gives (rho V) / 4 to
+ *    each of its four nodes (all three DOFs), V = det / 6 in the element matrix's fixed order,
+ *    folded per node from +0.0 in ascending tetrahedron id; after every sta_apply_edits (the
+ *    nodes of the edited tetrahedra are re-folded), sta_full_rebuild, sta_refold and
+ *    sta_set_params it equals a from-scratch evaluation bit for bit.  A node of no active
+ *    tetrahedron has mass +0.0.
+ *  - Free DOFs: those of nodes that are not clamped and have mass.  A clamped DOF is held at
+ *    0; a DOF of a node without mass keeps its displacement, with velocity 0.
+ *  - Solve: Jacobi-preconditioned CG from x = u_t until ||r|| <= tol ||b|| or max_iter
+ *    iterations, deterministic (fixed-order reductions).
+ * sta_dyn_setup: rho, h > 0; f (3n, host, NULL = 0) and clamped (n, host, NULL = none) are
+ * copied; u = v = 0; computes the per-tetrahedron quarter masses and the lumped mass of the
+ * current mask.  Not allowed in graph mode (STA_ESTATE); graphs enabled afterwards include
+ * the mass update.  May be called again to change rho, h, f or clamped (resets u and v).
+ * sta_dyn_step: one step; synchronises `stream`; *iters = CG iterations, *rel_res =
+ * ||r|| / ||b|| at exit (0 when b = 0); either may be NULL.  Reaching max_iter is not an error.
+ * sta_dyn_state: device pointers (context-owned): u, v (3n) and the lumped mass (n).
+ * sta_dyn_set_state: overwrite u and/or v (3n each, host or device; NULL = keep).
+ */
+int sta_dyn_setup(sta_ctx *ctx, double rho, double h, const double *f, const uint8_t *clamped,
+                  void *stream);
+int sta_dyn_step(sta_ctx *ctx, double tol, int32_t max_iter, int32_t *iters, double *rel_res,
+                 void *stream);
+int sta_dyn_state(const sta_ctx *ctx, const double **u, const double **v, const double **mass);
+int sta_dyn_set_state(sta_ctx *ctx, const double *u, const double *v, int on_device, void *stream);
+
 /* Human-readable message of the last error on the calling thread. */
 const char *sta_last_error(void);
 const char *sta_status_string(int status);

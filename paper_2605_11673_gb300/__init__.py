@@ -30,7 +30,7 @@ EXPORTED = (
     "sta_status_string", "sta_apply_edits_noalloc", "sta_adjoint", "sta_spmv", "sta_set_launch",
     "sta_batch_create", "sta_batch_size", "sta_batch_instance", "sta_batch_apply_edits",
     "sta_graph_enable", "sta_graph_disable", "sta_set_policy", "sta_proxy_create",
-    "sta_proxy_state",
+    "sta_proxy_state", "sta_dyn_setup", "sta_dyn_step", "sta_dyn_state", "sta_dyn_set_state",
 )
 STA_NOALLOC_MAX_EDITED = 32768
 STA_POLICY_REFOLD = 0
@@ -95,6 +95,10 @@ def load_library(path: Path | str | None = None):
     L.sta_set_policy.argtypes = [_p, C.c_int32, _p]
     L.sta_proxy_create.argtypes = [_i64, _p, _i64, C.c_double, _p, _P(_p)]
     L.sta_proxy_state.argtypes = [_p, _P(_p), _P(_p)]
+    L.sta_dyn_setup.argtypes = [_p, C.c_double, C.c_double, _p, _p, _p]
+    L.sta_dyn_step.argtypes = [_p, C.c_double, C.c_int32, _P(C.c_int32), _P(C.c_double), _p]
+    L.sta_dyn_state.argtypes = [_p, _P(_p), _P(_p), _P(_p)]
+    L.sta_dyn_set_state.argtypes = [_p, _p, _p, _int, _p]
     L.sta_last_error.restype = C.c_char_p
     L.sta_status_string.argtypes = [_int]
     L.sta_status_string.restype = C.c_char_p
@@ -190,6 +194,43 @@ def sta_proxy_state(h: int, owner=None):
     s = sta_sizes(h)
     return (DeviceArray(m.value or 0, (s["n_blocks"],), "<i4", owner),
             DeviceArray(d.value or 0, (s["n_nodes"],), "<i4", owner))
+
+
+def sta_dyn_setup(h: int, rho: float, dt: float, f=None, clamped=None, stream=None) -> None:
+    """Implicit-Euler loop (include/sta.h): density, time step, load (3n), clamped nodes (n)."""
+    fp = _host(f, np.float64).reshape(-1) if f is not None else None
+    cp = _host(clamped, np.uint8).reshape(-1) if clamped is not None else None
+    _check(load_library().sta_dyn_setup(h, float(rho), float(dt),
+                                        fp.ctypes.data if fp is not None else None,
+                                        cp.ctypes.data if cp is not None else None,
+                                        _stream_handle(stream)))
+
+
+def sta_dyn_step(h: int, tol: float = 1e-10, max_iter: int = 1000, stream=None):
+    """One step; returns (CG iterations, relative residual)."""
+    it, rr = C.c_int32(), C.c_double()
+    _check(load_library().sta_dyn_step(h, float(tol), int(max_iter), C.byref(it), C.byref(rr),
+                                       _stream_handle(stream)))
+    return int(it.value), float(rr.value)
+
+
+def sta_dyn_state(h: int, owner=None):
+    """(u, v, mass) as zero-copy DeviceArrays."""
+    u, v, m = _p(), _p(), _p()
+    _check(load_library().sta_dyn_state(h, C.byref(u), C.byref(v), C.byref(m)))
+    n = sta_sizes(h)["n_nodes"]
+    return (DeviceArray(u.value or 0, (3 * n,), "<f8", owner),
+            DeviceArray(v.value or 0, (3 * n,), "<f8", owner),
+            DeviceArray(m.value or 0, (n,), "<f8", owner))
+
+
+def sta_dyn_set_state(h: int, u=None, v=None, stream=None) -> None:
+    """Overwrite u and/or v from host arrays."""
+    up = _host(u, np.float64).reshape(-1) if u is not None else None
+    vp = _host(v, np.float64).reshape(-1) if v is not None else None
+    _check(load_library().sta_dyn_set_state(h, up.ctypes.data if up is not None else None,
+                                            vp.ctypes.data if vp is not None else None, 0,
+                                            _stream_handle(stream)))
 
 
 def sta_destroy(h: int) -> None:
@@ -463,6 +504,19 @@ class Assembler:
 
     def graph_disable(self, stream=None):
         sta_graph_disable(self.h, stream)
+
+    def dyn_setup(self, rho: float, dt: float, f=None, clamped=None, stream=None):
+        sta_dyn_setup(self.h, rho, dt, f, clamped, stream)
+
+    def dyn_step(self, tol: float = 1e-10, max_iter: int = 1000, stream=None):
+        return sta_dyn_step(self.h, tol, max_iter, stream)
+
+    def dyn_state(self):
+        """(u, v, mass) torch tensors viewing the context's device memory."""
+        return tuple(a.torch() for a in sta_dyn_state(self.h, self))
+
+    def dyn_set_state(self, u=None, v=None, stream=None):
+        sta_dyn_set_state(self.h, u, v, stream)
 
 
 class BatchAssembler(Assembler):

@@ -40,6 +40,7 @@ static void free_ctx(sta_ctx *x) {
     if (x->c.d_frame) cudaFree(x->c.d_frame);
     if (x->h_mask) cudaFreeHost(x->h_mask);
     if (x->h2d_done) cudaEventDestroy(x->h2d_done);
+    if (x->c.g_cg) cudaGraphExecDestroy(x->c.g_cg);
     graph_release(&x->c);
     delete x;
 }
@@ -520,6 +521,10 @@ int sta_set_params(sta_ctx *x, const double *nodes, const double *young, const d
         return fail(STA_EINVAL, std::to_string(back[0]) + " tetrahedra have det <= 0 (first: tet " +
                                     std::to_string(back[2]) + ")");
     if (c->policy == STA_POLICY_FIXED) STA_TRY(launch_fx_prepare(c, s));
+    if (nodes) {  // the tetrahedra's volumes, hence the lumped mass, follow the positions
+        STA_TRY(launch_dyn_qmass(c, s));
+        STA_TRY(launch_dyn_mass_all(c, s));
+    }
     return STA_OK;
 }
 

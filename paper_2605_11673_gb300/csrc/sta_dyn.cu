@@ -1,0 +1,502 @@
+// Implicit-Euler dynamic loop on the maintained operator (STA-FEM Sec. 6.2, Eq. 9):
+//     (M_t + h^2 K_t) u_{t+1} = M_t (u_t + h v_t) + h^2 f,   v_{t+1} = (u_{t+1} - u_t) / h,
+// K_t the context's maintained values (eps included), M_t a maintained lumped mass.
+//
+// Lumped mass (the paper gives no formula): row-sum lumping of the consistent P1 mass, each
+// active tetrahedron gives (rho V) / 4 to each of its nodes (every DOF of the node), folded per
+// node from +0.0 in ascending tetrahedron id -- the canonical order of the stiffness, so the
+// maintained mass equals a rebuild bit for bit.  V = det / 6 with det in the element matrix's
+// fixed order.  The per-tet quarter masses are computed once (sta_dyn_setup, sta_set_params);
+// a streaming frame re-folds the nodes of its edited tetrahedra after the mask update; a
+// rebuild re-folds every node.
+//
+// Solve: conjugate gradients with the Jacobi preconditioner (the paper's solver: CG with
+// diagonal preconditioning), on the free DOFs -- not clamped, of a node with mass; a clamped
+// DOF stays 0, a DOF of a node without mass keeps its displacement with velocity 0.  Start:
+// x = u_t.  Stop: ||r|| <= tol ||b|| or max_iter.  A x = m x + h^2 (K x) is applied without
+// forming the matrix, one warp per node over its three rows (they share their columns).
+// Every dot product is a fixed-order reduction (warp tree, warps in order, CTAs in order by the
+// last CTA to arrive), so a solve is deterministic for a given context.  Iterations run in
+// captured chunks of CG_CHUNK (3 launches each); the host reads the state between chunks.
+#include <cmath>
+
+#include "sta_internal.cuh"
+
+namespace sta {
+namespace {
+
+constexpr int DYN_TPB = 256;
+constexpr int DYN_WARPS = DYN_TPB / 32;
+constexpr int CG_CHUNK = 8;
+
+// Device state of one step's solve.
+struct CgState {
+    double rz, pq, rr, bb, alpha, beta, tol2, pad0;
+    int32_t iters, max_iter, done, pad1;
+    unsigned int arrive[4];  // last-CTA counters: spmv, r0, update, spare
+};
+
+// -------------------------------------------------------------------------------- mass
+
+__global__ void k_dyn_qmass(const double4_32a *__restrict__ X, const int4 *__restrict__ tets,
+                            int64_t T, double rho, double *__restrict__ qmass) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int4 q = tets[t];
+        const double4_32a x0 = X[q.x], x1 = X[q.y], x2 = X[q.z], x3 = X[q.w];
+        const double d1x = x1.x - x0.x, d1y = x1.y - x0.y, d1z = x1.z - x0.z;
+        const double d2x = x2.x - x0.x, d2y = x2.y - x0.y, d2z = x2.z - x0.z;
+        const double d3x = x3.x - x0.x, d3y = x3.y - x0.y, d3z = x3.z - x0.z;
+        // c_1 = d_2 x d_3, det = d_1 . c_1 (the element matrix's order)
+        const double cx = __fma_rn(d2y, d3z, -(d2z * d3y));
+        const double cy = __fma_rn(d2z, d3x, -(d2x * d3z));
+        const double cz = __fma_rn(d2x, d3y, -(d2y * d3x));
+        const double det = __fma_rn(d1z, cz, __fma_rn(d1y, cy, d1x * cx));
+        qmass[t] = (rho * (det / 6.0)) * 0.25;
+    }
+}
+
+__device__ __forceinline__ double node_mass(int32_t a, const int32_t *__restrict__ nt_ptr,
+                                            const int32_t *__restrict__ nt_list,
+                                            const uint8_t *__restrict__ mask,
+                                            const double *__restrict__ qmass) {
+    double m = 0.0;
+    for (int32_t q = nt_ptr[a]; q < nt_ptr[a + 1]; ++q) {
+        const int32_t t = nt_list[q];
+        if (mask[t]) m += qmass[t];
+    }
+    return m;
+}
+
+__global__ void k_dyn_mass_all(int64_t n, const int32_t *__restrict__ nt_ptr,
+                               const int32_t *__restrict__ nt_list, const uint8_t *__restrict__ mask,
+                               const double *__restrict__ qmass, double *__restrict__ mass) {
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n;
+         a += (int64_t)gridDim.x * blockDim.x)
+        mass[a] = node_mass((int32_t)a, nt_ptr, nt_list, mask, qmass);
+}
+
+// The nodes of the frame's edited tetrahedra, after the mask update.  A node shared by several
+// edited tetrahedra is re-folded by each of them; all read the same mask and write the same
+// value.
+__global__ void k_dyn_mass_edited(const int32_t *__restrict__ edited, int64_t m,
+                                  const int64_t *__restrict__ m_dev, const int4 *__restrict__ tets,
+                                  const int32_t *__restrict__ nt_ptr,
+                                  const int32_t *__restrict__ nt_list,
+                                  const uint8_t *__restrict__ mask,
+                                  const double *__restrict__ qmass, double *__restrict__ mass) {
+    const int64_t items = 4 * (m_dev ? *m_dev : m);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < items;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = (uint32_t)edited[i >> 2] & 0x7fffffffu;
+        const int4 q = tets[t];
+        const int j = (int)(i & 3);
+        const int32_t a = j == 0 ? q.x : (j == 1 ? q.y : (j == 2 ? q.z : q.w));
+        mass[a] = node_mass(a, nt_ptr, nt_list, mask, qmass);
+    }
+}
+
+// -------------------------------------------------------------------------------- CG
+
+// Sum over the CTA in a fixed order; the result is valid in thread 0.
+__device__ __forceinline__ double cta_sum(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    __syncthreads();
+    return t;
+}
+
+// Thread 0 has stored this CTA's partials; true (in every thread) in the last CTA to arrive,
+// once all partials are visible.  The last CTA resets the counter for the next use.
+__device__ __forceinline__ bool last_cta(unsigned int *arrive) {
+    __shared__ bool last;
+    __threadfence();
+    if (threadIdx.x == 0) last = atomicAdd(arrive, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+__device__ __forceinline__ double sum_parts(const double *part, int n) {
+    double t = 0.0;
+    for (int i = 0; i < n; ++i) t += __ldcg(part + i);
+    return t;
+}
+
+__device__ __forceinline__ bool cg_stopped(const CgState *st) {
+    return st->done || st->iters >= st->max_iter;
+}
+
+// b, x0 = u, Jacobi inverse diagonal and the free flags, per DOF.
+__global__ void k_cg_init(int64_t n3, const int32_t *__restrict__ adj_ptr,
+                          const int32_t *__restrict__ adj, const int32_t *__restrict__ row_ptr,
+                          const double *__restrict__ val, const double *__restrict__ mass,
+                          const uint8_t *__restrict__ clamped, const double *__restrict__ u,
+                          const double *__restrict__ v, const double *__restrict__ f, double h,
+                          double *__restrict__ x, double *__restrict__ b,
+                          double *__restrict__ dinv, uint8_t *__restrict__ fr) {
+    const double h2 = h * h;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = (int32_t)(i / 3), k = (int32_t)(i - 3 * (int64_t)a);
+        const double m = mass[a];
+        const bool free = !clamped[a] && m > 0.0;
+        fr[i] = free ? 1 : 0;
+        if (!free) {
+            x[i] = 0.0;
+            b[i] = 0.0;
+            dinv[i] = 0.0;
+            continue;
+        }
+        int32_t lo = adj_ptr[a], hi = adj_ptr[a + 1];  // the diagonal block of node a
+        while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (adj[mid] < a) lo = mid + 1; else hi = mid;
+        }
+        const double kii = val[row_ptr[i] + 3 * (lo - adj_ptr[a]) + k];
+        x[i] = u[i];
+        b[i] = m * (u[i] + h * v[i]) + h2 * f[i];
+        dinv[i] = 1.0 / (m + h2 * kii);
+    }
+}
+
+// q = A x on the free DOFs (0 elsewhere), one warp per node over its three rows.  With
+// `dots`, the last CTA forms p.q and alpha = rz / pq.
+__global__ void __launch_bounds__(DYN_TPB)
+k_cg_spmv(int64_t n, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+          const double *__restrict__ val, const double *__restrict__ mass, double h2,
+          const uint8_t *__restrict__ fr, const double *__restrict__ xin,
+          double *__restrict__ qout, double *__restrict__ part, CgState *st, bool dots) {
+    __shared__ double sh[DYN_WARPS];
+    if (dots && cg_stopped(st)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double pq = 0.0;
+    for (int64_t a = warp; a < n; a += nwarps) {
+        const int32_t r0 = row_ptr[3 * a], r1 = row_ptr[3 * a + 1], r2 = row_ptr[3 * a + 2];
+        const int32_t len = r1 - r0;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+        for (int32_t k = lane; k < len; k += 32) {
+            const double xj = xin[col[r0 + k]];
+            s0 = __fma_rn(val[r0 + k], xj, s0);
+            s1 = __fma_rn(val[r1 + k], xj, s1);
+            s2 = __fma_rn(val[r2 + k], xj, s2);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        double c = 0.0;
+        if (lane < 3) {
+            const int64_t i = 3 * a + lane;
+            const double s = lane == 0 ? s0 : (lane == 1 ? s1 : s2);
+            const double q = fr[i] ? __fma_rn(mass[a], xin[i], h2 * s) : 0.0;
+            qout[i] = q;
+            c = xin[i] * q;
+        }
+        const double c1 = __shfl_sync(0xffffffffu, c, 1), c2 = __shfl_sync(0xffffffffu, c, 2);
+        if (lane == 0) pq += (c + c1) + c2;
+    }
+    if (!dots) return;
+    const double t = cta_sum(lane == 0 ? pq : 0.0, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+    if (last_cta(&st->arrive[0]) && threadIdx.x == 0) {
+        const double s = sum_parts(part, gridDim.x);
+        st->pq = s;
+        if (s > 0.0) st->alpha = st->rz / s;
+        else st->done = 1;  // breakdown: p = 0 (already converged) or A not positive definite
+        st->arrive[0] = 0u;
+    }
+}
+
+// r = b - q, z = D^-1 r, p = z; rz, rr, bb; the convergence test.
+__global__ void __launch_bounds__(DYN_TPB)
+k_cg_r0(int64_t n3, const double *__restrict__ b, const double *__restrict__ q,
+        const double *__restrict__ dinv, double *__restrict__ r, double *__restrict__ z,
+        double *__restrict__ p, double *__restrict__ part, CgState *st) {
+    __shared__ double sh[DYN_WARPS];
+    double rz = 0.0, rr = 0.0, bb = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double ri = b[i] - q[i], zi = dinv[i] * ri;
+        r[i] = ri;
+        z[i] = zi;
+        p[i] = zi;
+        rz = __fma_rn(ri, zi, rz);
+        rr = __fma_rn(ri, ri, rr);
+        bb = __fma_rn(b[i], b[i], bb);
+    }
+    const double a0 = cta_sum(rz, sh), a1 = cta_sum(rr, sh), a2 = cta_sum(bb, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = a0;
+        part[gridDim.x + blockIdx.x] = a1;
+        part[2 * gridDim.x + blockIdx.x] = a2;
+    }
+    if (last_cta(&st->arrive[1]) && threadIdx.x == 0) {
+        st->rz = sum_parts(part, gridDim.x);
+        st->rr = sum_parts(part + gridDim.x, gridDim.x);
+        st->bb = sum_parts(part + 2 * gridDim.x, gridDim.x);
+        st->iters = 0;
+        st->done = st->rr <= st->tol2 * st->bb ? 1 : 0;
+        st->arrive[1] = 0u;
+    }
+}
+
+// x += alpha p, r -= alpha q, z = D^-1 r; rz, rr; beta, the iteration count, the test.
+__global__ void __launch_bounds__(DYN_TPB)
+k_cg_update(int64_t n3, double *__restrict__ x, double *__restrict__ r, double *__restrict__ z,
+            const double *__restrict__ p, const double *__restrict__ q,
+            const double *__restrict__ dinv, double *__restrict__ part, CgState *st) {
+    __shared__ double sh[DYN_WARPS];
+    if (cg_stopped(st)) return;
+    const double alpha = st->alpha;
+    double rz = 0.0, rr = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] = __fma_rn(alpha, p[i], x[i]);
+        const double ri = __fma_rn(-alpha, q[i], r[i]), zi = dinv[i] * ri;
+        r[i] = ri;
+        z[i] = zi;
+        rz = __fma_rn(ri, zi, rz);
+        rr = __fma_rn(ri, ri, rr);
+    }
+    const double a0 = cta_sum(rz, sh), a1 = cta_sum(rr, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = a0;
+        part[gridDim.x + blockIdx.x] = a1;
+    }
+    if (last_cta(&st->arrive[2]) && threadIdx.x == 0) {
+        const double rzn = sum_parts(part, gridDim.x);
+        st->rr = sum_parts(part + gridDim.x, gridDim.x);
+        st->beta = st->rz != 0.0 ? rzn / st->rz : 0.0;
+        st->rz = rzn;
+        st->iters += 1;
+        if (st->rr <= st->tol2 * st->bb) st->done = 1;
+        st->arrive[2] = 0u;
+    }
+}
+
+// p = z + beta p.
+__global__ void k_cg_pupdate(int64_t n3, double *__restrict__ p, const double *__restrict__ z,
+                             const CgState *st) {
+    if (st->done || st->iters >= st->max_iter) return;
+    const double beta = st->beta;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = __fma_rn(beta, p[i], z[i]);
+}
+
+// u, v from the solution.
+__global__ void k_dyn_advance(int64_t n3, double *__restrict__ u, double *__restrict__ v,
+                              const double *__restrict__ x, const uint8_t *__restrict__ fr,
+                              const uint8_t *__restrict__ clamped, double h) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (fr[i]) {
+            v[i] = (x[i] - u[i]) / h;
+            u[i] = x[i];
+        } else {
+            v[i] = 0.0;
+            if (clamped[i / 3]) u[i] = 0.0;
+        }
+    }
+}
+
+unsigned dyn_grid(const Ctx *c, int64_t items, int per_sm = 4) {
+    int64_t g = (items + DYN_TPB - 1) / DYN_TPB;
+    const int64_t cap = (int64_t)c->num_sms * per_sm;
+    if (g > cap) g = cap;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ launchers
+
+int launch_dyn_mass_all(Ctx *c, cudaStream_t s) {
+    if (!c->dyn || c->n == 0) return STA_OK;
+    k_dyn_mass_all<<<dyn_grid(c, c->n), DYN_TPB, 0, s>>>(c->n, c->nt_ptr, c->nt_list, c->mask,
+                                                         c->qmass, c->mass);
+    STA_CUDA_TRY(cudaGetLastError());
+    return STA_OK;
+}
+
+int launch_dyn_mass_edited(Ctx *c, const int32_t *edited, int64_t m, const int64_t *m_dev,
+                           int64_t cap, cudaStream_t s) {
+    if (!c->dyn) return STA_OK;
+    k_dyn_mass_edited<<<dyn_grid(c, 4 * (cap > 0 ? cap : 1), 8), DYN_TPB, 0, s>>>(
+        edited, m, m_dev, c->tets, c->nt_ptr, c->nt_list, c->mask, c->qmass, c->mass);
+    STA_CUDA_TRY(cudaGetLastError());
+    return STA_OK;
+}
+
+int launch_dyn_qmass(Ctx *c, cudaStream_t s) {
+    if (!c->dyn || c->T == 0) return STA_OK;
+    k_dyn_qmass<<<dyn_grid(c, c->T, 8), DYN_TPB, 0, s>>>(c->X, c->tets, c->T, c->dyn_rho, c->qmass);
+    STA_CUDA_TRY(cudaGetLastError());
+    return STA_OK;
+}
+
+namespace {
+
+// One chunk of CG_CHUNK iterations (3 launches each), launched or captured on s.
+int cg_chunk(Ctx *c, cudaStream_t s) {
+    const int64_t n3 = 3 * c->n;
+    const unsigned gv = c->cg_grid;
+    double *x = c->cg, *b = x + n3, *r = b + n3, *z = r + n3, *p = z + n3, *q = p + n3;
+    double *dinv = q + n3;
+    CgState *st = reinterpret_cast<CgState *>(c->cg_state);
+    for (int it = 0; it < CG_CHUNK; ++it) {
+        k_cg_spmv<<<gv, DYN_TPB, 0, s>>>(c->n, c->row_ptr, c->col, c->val, c->mass,
+                                        c->dyn_h * c->dyn_h, c->cg_free, p, q, c->cg_part, st, true);
+        k_cg_update<<<gv, DYN_TPB, 0, s>>>(n3, x, r, z, p, q, dinv, c->cg_part, st);
+        k_cg_pupdate<<<gv, DYN_TPB, 0, s>>>(n3, p, z, st);
+    }
+    STA_CUDA_TRY(cudaGetLastError());
+    return STA_OK;
+}
+
+}  // namespace
+
+int launch_dyn_step(Ctx *c, double tol, int32_t max_iter, int32_t *iters, double *rel_res,
+                    cudaStream_t s) {
+    const int64_t n3 = 3 * c->n;
+    const unsigned gv = c->cg_grid;
+    double *x = c->cg, *b = x + n3, *r = b + n3, *z = r + n3, *p = z + n3, *q = p + n3;
+    double *dinv = q + n3;
+    CgState *st = reinterpret_cast<CgState *>(c->cg_state);
+    CgState h0 = {};
+    h0.tol2 = tol * tol;
+    h0.max_iter = max_iter;
+    STA_CUDA_TRY(cudaMemcpyAsync(st, &h0, sizeof h0, cudaMemcpyHostToDevice, s));
+    if (n3 > 0) {
+        k_cg_init<<<gv, DYN_TPB, 0, s>>>(n3, c->adj_ptr, c->adj, c->row_ptr, c->val, c->mass,
+                                         c->clamped, c->du, c->dv, c->df, c->dyn_h, x, b, dinv,
+                                         c->cg_free);
+        k_cg_spmv<<<gv, DYN_TPB, 0, s>>>(c->n, c->row_ptr, c->col, c->val, c->mass,
+                                        c->dyn_h * c->dyn_h, c->cg_free, x, q, c->cg_part, st, false);
+        k_cg_r0<<<gv, DYN_TPB, 0, s>>>(n3, b, q, dinv, r, z, p, c->cg_part, st);
+        STA_CUDA_TRY(cudaGetLastError());
+    }
+    if (!c->g_cg) {  // capture the chunk once (the context's buffers never move)
+        cudaStream_t cs = nullptr;
+        STA_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        int rc = e == cudaSuccess ? cg_chunk(c, cs) : STA_ECUDA;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (rc == STA_OK && e == cudaSuccess && e2 == cudaSuccess)
+            e2 = cudaGraphInstantiate(&c->g_cg, g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        if (rc != STA_OK || e != cudaSuccess || e2 != cudaSuccess) {
+            c->g_cg = nullptr;
+            return fail(STA_ECUDA, "CG chunk capture failed");
+        }
+    }
+    CgState hs = {};
+    for (;;) {
+        if (n3 > 0) {
+            STA_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof hs, cudaMemcpyDeviceToHost, s));
+            STA_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+        if (n3 == 0 || hs.done || hs.iters >= max_iter) break;
+        STA_CUDA_TRY(cudaGraphLaunch(c->g_cg, s));
+    }
+    if (n3 > 0) {
+        k_dyn_advance<<<gv, DYN_TPB, 0, s>>>(n3, c->du, c->dv, x, c->cg_free, c->clamped, c->dyn_h);
+        STA_CUDA_TRY(cudaGetLastError());
+        STA_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    if (iters) *iters = hs.iters;
+    if (rel_res) *rel_res = hs.bb > 0.0 ? std::sqrt(hs.rr / hs.bb) : 0.0;
+    return STA_OK;
+}
+
+}  // namespace sta
+
+using namespace sta;
+
+extern "C" int sta_dyn_setup(sta_ctx *x, double rho, double h, const double *f,
+                             const uint8_t *clamped, void *stream) {
+    if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    Ctx *c = &x->c;
+    if (c->op != STA_OP_ELASTICITY) return fail(STA_ESTATE, "not an elasticity context");
+    if (c->graph_on) return fail(STA_ESTATE, "disable graph mode before setting up the dynamics");
+    if (!(rho > 0.0) || !(h > 0.0) || !std::isfinite(rho) || !std::isfinite(h))
+        return fail(STA_EINVAL, "rho and h must be positive and finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = c->n, n3 = 3 * n;
+    if (!c->qmass) {
+        c->cg_grid = (int)dyn_grid(c, n3 > 0 ? n3 : 1);
+        STA_TRY(dev_alloc(c, &c->qmass, c->T));
+        STA_TRY(dev_alloc(c, &c->mass, n));
+        STA_TRY(dev_alloc(c, &c->du, n3));
+        STA_TRY(dev_alloc(c, &c->dv, n3));
+        STA_TRY(dev_alloc(c, &c->df, n3));
+        STA_TRY(dev_alloc(c, &c->clamped, n));
+        STA_TRY(dev_alloc(c, &c->cg, 7 * n3));
+        STA_TRY(dev_alloc(c, &c->cg_free, n3));
+        STA_TRY(dev_alloc(c, &c->cg_part, 3 * (int64_t)c->cg_grid));
+        STA_TRY(dev_alloc(c, &c->cg_state, (int64_t)sizeof(CgState)));
+    }
+    std::vector<double> hf(n3 > 0 ? n3 : 1, 0.0);
+    std::vector<uint8_t> hc(n > 0 ? n : 1, 0);
+    if (f) std::copy(f, f + n3, hf.begin());
+    if (clamped)
+        for (int64_t a = 0; a < n; ++a) hc[a] = clamped[a] ? 1 : 0;
+    STA_CUDA_TRY(cudaMemcpyAsync(c->df, hf.data(), sizeof(double) * n3, cudaMemcpyHostToDevice, s));
+    STA_CUDA_TRY(cudaMemcpyAsync(c->clamped, hc.data(), (size_t)n, cudaMemcpyHostToDevice, s));
+    STA_CUDA_TRY(cudaMemsetAsync(c->du, 0, sizeof(double) * (size_t)(n3 > 0 ? n3 : 1), s));
+    STA_CUDA_TRY(cudaMemsetAsync(c->dv, 0, sizeof(double) * (size_t)(n3 > 0 ? n3 : 1), s));
+    if (c->g_cg) {  // the captured CG chunk holds h^2: capture again on the next step
+        cudaGraphExecDestroy(c->g_cg);
+        c->g_cg = nullptr;
+    }
+    c->dyn = true;
+    c->dyn_rho = rho;
+    c->dyn_h = h;
+    STA_TRY(launch_dyn_qmass(c, s));
+    STA_TRY(launch_dyn_mass_all(c, s));
+    STA_CUDA_TRY(cudaStreamSynchronize(s));  // the host vectors go out of scope
+    return STA_OK;
+}
+
+extern "C" int sta_dyn_step(sta_ctx *x, double tol, int32_t max_iter, int32_t *iters,
+                            double *rel_res, void *stream) {
+    if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    Ctx *c = &x->c;
+    if (!c->dyn) return fail(STA_ESTATE, "call sta_dyn_setup first");
+    if (!(tol >= 0.0) || max_iter < 0) return fail(STA_EINVAL, "tol and max_iter must be >= 0");
+    return launch_dyn_step(c, tol, max_iter, iters, rel_res, (cudaStream_t)stream);
+}
+
+extern "C" int sta_dyn_state(const sta_ctx *x, const double **u, const double **v,
+                             const double **mass) {
+    if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    if (!x->c.dyn) return fail(STA_ESTATE, "call sta_dyn_setup first");
+    if (u) *u = x->c.du;
+    if (v) *v = x->c.dv;
+    if (mass) *mass = x->c.mass;
+    return STA_OK;
+}
+
+extern "C" int sta_dyn_set_state(sta_ctx *x, const double *u, const double *v, int on_device,
+                                 void *stream) {
+    if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    Ctx *c = &x->c;
+    if (!c->dyn) return fail(STA_ESTATE, "call sta_dyn_setup first");
+    const size_t bytes = sizeof(double) * 3 * (size_t)c->n;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (u) STA_CUDA_TRY(cudaMemcpyAsync(c->du, u, bytes, kind, s));
+    if (v) STA_CUDA_TRY(cudaMemcpyAsync(c->dv, v, bytes, kind, s));
+    if (!on_device) STA_CUDA_TRY(cudaStreamSynchronize(s));
+    return STA_OK;
+}

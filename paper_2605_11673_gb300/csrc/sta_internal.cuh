@@ -202,6 +202,20 @@ struct Ctx {
     uint32_t *pflag = nullptr;  // nblocks: claim flags of the frame's touched blocks
     int32_t *plist = nullptr;   // nblocks: the frame's touched blocks
 
+    // implicit-Euler loop (sta_dyn.cu), allocated by the first sta_dyn_setup
+    bool dyn = false;
+    double dyn_rho = 0.0, dyn_h = 0.0;
+    double *qmass = nullptr;    // T: (rho V) / 4 of each tetrahedron
+    double *mass = nullptr;     // n: lumped mass per node, maintained with the mask
+    double *du = nullptr, *dv = nullptr, *df = nullptr;  // 3n: displacement, velocity, load
+    uint8_t *clamped = nullptr; // n
+    double *cg = nullptr;       // 7 x 3n: x, b, r, z, p, q, D^-1
+    uint8_t *cg_free = nullptr; // 3n: DOF solved for
+    double *cg_part = nullptr;  // 3 x cg_grid: per-CTA partial sums
+    unsigned char *cg_state = nullptr;  // the solve's device scalars
+    int cg_grid = 0;
+    cudaGraphExec_t g_cg = nullptr;     // one captured chunk of CG iterations
+
     // CUDA-graph mode (sta_graph_enable): captured frame sequences and fixed staging
     bool graph_on = false;
     cudaGraphExec_t g_stream = nullptr, g_refold = nullptr, g_rebuild = nullptr;
@@ -256,6 +270,12 @@ int launch_fx_frame(Ctx *c, const int32_t *edited, int64_t m, const int64_t *m_d
                     int32_t *touched, unsigned long long *counters, cudaStream_t s);
 int launch_mask_bits(Ctx *c, cudaStream_t s);                    // codes <- mask
 int launch_values(Ctx *c, cudaStream_t s);  // the operator's rebuild (elasticity or proxy)
+int launch_dyn_qmass(Ctx *c, cudaStream_t s);     // sta_dyn.cu (no-ops unless set up)
+int launch_dyn_mass_all(Ctx *c, cudaStream_t s);
+int launch_dyn_mass_edited(Ctx *c, const int32_t *edited, int64_t m, const int64_t *m_dev,
+                           int64_t cap, cudaStream_t s);
+int launch_dyn_step(Ctx *c, double tol, int32_t max_iter, int32_t *iters, double *rel_res,
+                    cudaStream_t s);
 int build_proxy_maps(Ctx *c, const int32_t *tblk, cudaStream_t s);  // sta_proxy.cu
 int launch_proxy_rebuild(Ctx *c, cudaStream_t s);
 int launch_proxy_frame(Ctx *c, const int32_t *edited, int64_t m, const int64_t *m_dev,

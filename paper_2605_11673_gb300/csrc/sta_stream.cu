@@ -210,7 +210,9 @@ int launch_mask_bits(Ctx *c, cudaStream_t s) {
 
 // Every value from the current mask: the operator's full rebuild.
 int launch_values(Ctx *c, cudaStream_t s) {
-    return c->op == STA_OP_PROXY ? launch_proxy_rebuild(c, s) : launch_rebuild(c, s);
+    if (c->op == STA_OP_PROXY) return launch_proxy_rebuild(c, s);
+    STA_TRY(launch_rebuild(c, s));
+    return launch_dyn_mass_all(c, s);  // the lumped mass, when the dynamics are set up
 }
 
 // One streaming frame: claim kernel, then the fold of the touched units.  `frame` is a device
@@ -221,9 +223,11 @@ int launch_stream_frame(Ctx *c, FrameHeader *frame, int64_t cap, cudaStream_t s)
     if (c->op == STA_OP_PROXY)
         return launch_proxy_frame(c, frame_edited(frame), 0, &frame->m, cap, c->plist,
                                   frame_counters(frame), s);
-    if (c->policy == STA_POLICY_FIXED)
-        return launch_fx_frame(c, frame_edited(frame), 0, &frame->m, cap, c->touched,
-                               frame_counters(frame), s);
+    if (c->policy == STA_POLICY_FIXED) {
+        STA_TRY(launch_fx_frame(c, frame_edited(frame), 0, &frame->m, cap, c->touched,
+                                frame_counters(frame), s));
+        return launch_dyn_mass_edited(c, frame_edited(frame), 0, &frame->m, cap, s);
+    }
     const int threads = 256;
     int64_t g = (10 * cap + threads - 1) / threads;
     const int64_t gmax = (int64_t)c->num_sms * 16;
@@ -233,7 +237,8 @@ int launch_stream_frame(Ctx *c, FrameHeader *frame, int64_t cap, cudaStream_t s)
                                                    c->cslot, c->ccode, c->mask, c->owner,
                                                    c->touched, cnt);
     STA_CUDA_TRY(cudaGetLastError());
-    return launch_fold_list(c, c->touched, cnt + 1, 10 * (cap > 0 ? cap : 1), s);
+    STA_TRY(launch_fold_list(c, c->touched, cnt + 1, 10 * (cap > 0 ? cap : 1), s));
+    return launch_dyn_mass_edited(c, frame_edited(frame), 0, &frame->m, cap, s);
 }
 
 // Streaming update with caller-chosen scratch (the allocation-free entry point): the same two
@@ -256,6 +261,7 @@ int launch_stream_scratch(Ctx *c, int64_t m, const int32_t *d_edited, int32_t *t
         STA_CUDA_TRY(cudaGetLastError());
         STA_TRY(launch_fold_list(c, touched, counters + 1, 10 * m, s));
     }
+    if (m > 0) STA_TRY(launch_dyn_mass_edited(c, d_edited, m, nullptr, m, s));
     // touched units and touched entries, for sta_last_touched
     STA_CUDA_TRY(cudaMemcpyAsync(c->counters + 1, counters + 1, 3 * sizeof(unsigned long long),
                                  cudaMemcpyDeviceToDevice, s));

@@ -1,0 +1,162 @@
+"""Implicit-Euler loop (Sec. 6.2, Eq. 9) through the C-ABI (GPU only).
+
+Bar: the maintained lumped mass is bit-exact against the oracle's fold (orc_lumped_mass) after
+every call that changes the mask; each step's solution agrees with the oracle's step (a sparse
+direct solve of the same system, from the same state) to the CG tolerance scaled by the
+system's conditioning, and its residual under the oracle's matrix is within the tolerance."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sta():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_11673_gb300 as P
+    P.load_library()
+    return P
+
+
+def _bits(a):
+    return np.ascontiguousarray(a, dtype=np.float64).view(np.uint64)
+
+
+def _mass_check(asm, P, X, rho, mask, what):
+    got = asm.dyn_state()[2].cpu().numpy()
+    ref = P.lumped_mass(X, rho, mask)
+    assert np.array_equal(_bits(got), _bits(ref)), f"{what}: lumped mass differs"
+
+
+@pytest.mark.parametrize("mode", ["plain", "fixed", "graph", "noalloc"])
+def test_lumped_mass_maintained_bitwise(sta, orc, mode):
+    wl = W.adjoint_block(N=6)
+    P = orc.Pattern(wl.n_nodes, wl.tets)
+    asm = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu)
+    rho = 750.0
+    asm.dyn_setup(rho, 1e-2, wl.meta["load"], wl.meta["clamped_nodes"])
+    _mass_check(asm, P, wl.X, rho, np.zeros(wl.n_tets, np.uint8), "setup, nothing active")
+    mask = wl.mask0.copy()
+    asm.full_rebuild(mask)
+    _mass_check(asm, P, wl.X, rho, mask, "full rebuild")
+    if mode == "fixed":
+        asm.set_policy(sta.STA_POLICY_FIXED)
+    if mode == "graph":
+        asm.graph_enable(max(int(f.shape[0]) for f in wl.frames) or 1)
+    for f, ed in enumerate(wl.frames):
+        if mode == "noalloc":
+            sta.sta_apply_edits_noalloc(asm.h, ed)
+        else:
+            asm.apply_edits(ed)
+        mask = W.apply_edits_to_mask(mask, ed)
+        _mass_check(asm, P, wl.X, rho, mask, f"frame {f}")
+    asm.refold()
+    _mass_check(asm, P, wl.X, rho, mask, "refold")
+    if mode == "graph":
+        asm.graph_disable()
+    # moved nodes: volumes and masses follow sta_set_params
+    X2 = wl.X * 1.1 + 0.01
+    asm.set_params(X=X2)
+    _mass_check(asm, P, X2, rho, mask, "set_params")
+    asm.close()
+
+
+def _oracle_matrix(orc, P, Ke, mask, eps=0.0):
+    return P.csr(P.rebuild(Ke, mask, eps))
+
+
+def test_steps_vs_direct_solve(sta, orc):
+    import scipy.sparse as sp
+    wl = W.adjoint_block(N=6)
+    P = orc.Pattern(wl.n_nodes, wl.tets)
+    Ke, bad = orc.element_all(wl.X, wl.tets, wl.E, wl.nu)
+    assert bad == 0
+    rho, h, tol = 1000.0, 2e-3, 1e-12
+    f0, clamped = wl.meta["load"], wl.meta["clamped_nodes"]
+    asm = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu)
+    asm.full_rebuild(wl.mask0)
+    asm.dyn_setup(rho, h, f0, clamped)
+    mask = wl.mask0.copy()
+    iters_seen = []
+    for f in range(8):
+        if f > 0:
+            ed = wl.frames[f - 1]
+            asm.apply_edits(ed)
+            mask = W.apply_edits_to_mask(mask, ed)
+        u, v, m = (a.cpu().numpy().copy() for a in asm.dyn_state())
+        it, rel = asm.dyn_step(tol=tol, max_iter=5000)
+        iters_seen.append(it)
+        assert rel <= tol and it < 5000, f"step {f}: {it} iterations, rel {rel}"
+        u1, v1, _ = (a.cpu().numpy() for a in asm.dyn_state())
+        K = _oracle_matrix(orc, P, Ke, mask)
+        mo = P.lumped_mass(wl.X, rho, mask)
+        assert np.array_equal(_bits(m), _bits(mo))
+        ru, rv = orc.implicit_euler_step(K, mo, u, v, f0, h, clamped)
+        # residual under the oracle's matrix, on the free DOFs
+        free = orc.dyn_free(mo, clamped)
+        A = (sp.diags(np.repeat(mo, 3)) + h * h * K).tocsr()
+        b = np.repeat(mo, 3) * (u + h * v) + h * h * f0
+        res = (A @ u1 - b)[free]
+        assert np.linalg.norm(res) <= 10 * tol * np.linalg.norm(b[free])
+        # the solution: CG tolerance times a conditioning allowance
+        assert np.linalg.norm(u1 - ru) <= 1e-8 * np.linalg.norm(ru), f"step {f}: u"
+        assert np.linalg.norm(v1 - rv) <= 1e-6 * max(np.linalg.norm(rv), 1e-30), f"step {f}: v"
+        assert np.all(u1[np.repeat(clamped, 3)] == 0.0)
+        assert np.all(v1[~free] == 0.0)
+    assert max(iters_seen) > 0
+    asm.close()
+
+
+def test_dynamics_edge_cases_and_determinism(sta, orc):
+    wl = W.adjoint_block(N=4)
+    f0, clamped = wl.meta["load"], wl.meta["clamped_nodes"]
+
+    def make():
+        a = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu)
+        a.full_rebuild(wl.mask0)
+        return a
+
+    a = make()
+    with pytest.raises(sta.StaError) as ei:
+        a.dyn_step()
+    assert ei.value.status == sta.STA_ESTATE
+    # at rest and unloaded: nothing to solve
+    a.dyn_setup(500.0, 1e-2, None, clamped)
+    it, rel = a.dyn_step()
+    assert it == 0 and rel == 0.0
+    assert not a.dyn_state()[0].cpu().numpy().any()
+    # max_iter = 0: u is kept, v of the free DOFs is 0
+    a.dyn_setup(500.0, 1e-2, f0, clamped)
+    u0 = np.random.default_rng(1).standard_normal(3 * wl.n_nodes)
+    a.dyn_set_state(u=u0)
+    it, rel = a.dyn_step(max_iter=0)
+    u, v, m = (t.cpu().numpy() for t in a.dyn_state())
+    free = orc.dyn_free(m, clamped)
+    assert it == 0 and rel > 0
+    assert np.array_equal(u[free], u0[free]) and not v.any()
+    assert np.all(u[np.repeat(clamped, 3)] == 0.0)
+    # two contexts, same inputs: bit-identical trajectories
+    b = make()
+    a.dyn_setup(500.0, 1e-2, f0, clamped)
+    b.dyn_setup(500.0, 1e-2, f0, clamped)
+    for ed in wl.frames[:3]:
+        for x in (a, b):
+            x.apply_edits(ed)
+            x.dyn_step(tol=1e-10)
+    ua, ub = a.dyn_state()[0].cpu().numpy(), b.dyn_state()[0].cpu().numpy()
+    assert np.array_equal(_bits(ua), _bits(ub))
+    # graph mode forbids setup; the proxy has no dynamics
+    a.graph_enable(64)
+    with pytest.raises(sta.StaError):
+        a.dyn_setup(500.0, 1e-2)
+    a.graph_disable()
+    px = sta.ProxyAssembler(wl.n_nodes, wl.tets)
+    with pytest.raises(sta.StaError):
+        sta.sta_dyn_setup(px.h, 1.0, 1.0)
+    px.close()
+    a.close()
+    b.close()
