@@ -14,11 +14,13 @@
 // diagonal preconditioning), on the free DOFs -- not clamped, of a node with mass; a clamped
 // DOF stays 0, a DOF of a node without mass keeps its displacement with velocity 0.  Start:
 // x = u_t.  Stop: ||r|| <= tol ||b|| or max_iter.  A x = m x + h^2 (K x) is applied without
-// forming the matrix, one warp per node over its three rows (they share their columns).
+// forming the matrix, one thread per node over its three rows (they share their columns).
 // Every dot product is a fixed-order reduction (warp tree, warps in order, CTAs in order by the
 // last CTA to arrive), so a solve is deterministic for a given context.  Iterations run in
 // captured chunks of CG_CHUNK (3 launches each); the host reads the state between chunks.
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "sta_internal.cuh"
 
@@ -121,10 +123,12 @@ __device__ __forceinline__ bool last_cta(unsigned int *arrive) {
     return last;
 }
 
-__device__ __forceinline__ double sum_parts(const double *part, int n) {
+// In the last CTA (every thread calls it): the sum of the n per-CTA partials, each thread over
+// a fixed stride of them, then the CTA tree; valid in thread 0.
+__device__ __forceinline__ double sum_parts(const double *part, int n, double *sh) {
     double t = 0.0;
-    for (int i = 0; i < n; ++i) t += __ldcg(part + i);
-    return t;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) t += __ldcg(part + i);
+    return cta_sum(t, sh);
 }
 
 __device__ __forceinline__ bool cg_stopped(const CgState *st) {
@@ -164,54 +168,86 @@ __global__ void k_cg_init(int64_t n3, const int32_t *__restrict__ adj_ptr,
     }
 }
 
-// q = A x on the free DOFs (0 elsewhere), one warp per node over its three rows.  With
-// `dots`, the last CTA forms p.q and alpha = rz / pq.
+// q = A x on the free DOFs (0 elsewhere), four lanes per node over its three rows (they share
+// their columns): lane j of the quad takes the entries j, j + 4, ... of each row, ascending,
+// and the quad adds its four partial sums as (s0 + s1) + (s2 + s3).  GB300 issues an FP64
+// instruction for a whole warp whatever its active lanes, and the FP64 pipe is the scarce unit
+// here, so every lane works on its own entries and the only cross-lane adds are the two quad
+// levels.  The nodes are taken in the order `perm` (ascending row length), so that the eight
+// nodes of a warp have rows of nearly one length.  With `dots`, the last CTA forms p.q and
+// alpha = rz / pq.
 __global__ void __launch_bounds__(DYN_TPB)
-k_cg_spmv(int64_t n, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-          const double *__restrict__ val, const double *__restrict__ mass, double h2,
-          const uint8_t *__restrict__ fr, const double *__restrict__ xin,
-          double *__restrict__ qout, double *__restrict__ part, CgState *st, bool dots) {
+k_cg_spmv(int64_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ row_ptr,
+          const int32_t *__restrict__ col, const double *__restrict__ val,
+          const double *__restrict__ mass, double h2, const uint8_t *__restrict__ fr,
+          const double *__restrict__ xin, double *__restrict__ qout, double *__restrict__ part,
+          CgState *st, bool dots) {
     __shared__ double sh[DYN_WARPS];
     if (dots && cg_stopped(st)) return;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, qd = lane & 3;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double pq = 0.0;
-    for (int64_t a = warp; a < n; a += nwarps) {
-        const int32_t r0 = row_ptr[3 * a], r1 = row_ptr[3 * a + 1], r2 = row_ptr[3 * a + 2];
-        const int32_t len = r1 - r0;
+    for (int64_t base = 8 * warp; base < n; base += 8 * nwarps) {  // warp-uniform
+        const int64_t j = base + (lane >> 2);
         double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-        for (int32_t k = lane; k < len; k += 32) {
-            const double xj = xin[col[r0 + k]];
-            s0 = __fma_rn(val[r0 + k], xj, s0);
-            s1 = __fma_rn(val[r1 + k], xj, s1);
-            s2 = __fma_rn(val[r2 + k], xj, s2);
+        int64_t a = -1;
+        if (j < n) {
+            a = perm[j];
+            const int32_t r0 = row_ptr[3 * a], len = (row_ptr[3 * a + 3] - r0) / 3;
+            const int32_t r1 = r0 + len, r2 = r1 + len;
+            int32_t k = qd;
+            for (; k + 12 < len; k += 16) {
+                int32_t cj[4];
+                double v0[4], v1[4], v2[4], xj[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    cj[u] = col[r0 + k + 4 * u];
+                    v0[u] = val[r0 + k + 4 * u];
+                    v1[u] = val[r1 + k + 4 * u];
+                    v2[u] = val[r2 + k + 4 * u];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) xj[u] = xin[cj[u]];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    s0 = __fma_rn(v0[u], xj[u], s0);
+                    s1 = __fma_rn(v1[u], xj[u], s1);
+                    s2 = __fma_rn(v2[u], xj[u], s2);
+                }
+            }
+            for (; k < len; k += 4) {
+                const double xj = xin[col[r0 + k]];
+                s0 = __fma_rn(val[r0 + k], xj, s0);
+                s1 = __fma_rn(val[r1 + k], xj, s1);
+                s2 = __fma_rn(val[r2 + k], xj, s2);
+            }
         }
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = 1; o <= 2; o <<= 1) {
             s0 += __shfl_xor_sync(0xffffffffu, s0, o);
             s1 += __shfl_xor_sync(0xffffffffu, s1, o);
             s2 += __shfl_xor_sync(0xffffffffu, s2, o);
         }
-        double c = 0.0;
-        if (lane < 3) {
-            const int64_t i = 3 * a + lane;
-            const double s = lane == 0 ? s0 : (lane == 1 ? s1 : s2);
-            const double q = fr[i] ? __fma_rn(mass[a], xin[i], h2 * s) : 0.0;
-            qout[i] = q;
-            c = xin[i] * q;
+        if (a >= 0 && qd < 3) {
+            const int64_t d = 3 * a + qd;
+            const double xd = xin[d];
+            const double sd = qd == 0 ? s0 : (qd == 1 ? s1 : s2);
+            const double q = fr[d] ? __fma_rn(mass[a], xd, h2 * sd) : 0.0;
+            qout[d] = q;
+            pq = __fma_rn(xd, q, pq);
         }
-        const double c1 = __shfl_sync(0xffffffffu, c, 1), c2 = __shfl_sync(0xffffffffu, c, 2);
-        if (lane == 0) pq += (c + c1) + c2;
     }
     if (!dots) return;
-    const double t = cta_sum(lane == 0 ? pq : 0.0, sh);
+    const double t = cta_sum(pq, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
-    if (last_cta(&st->arrive[0]) && threadIdx.x == 0) {
-        const double s = sum_parts(part, gridDim.x);
-        st->pq = s;
-        if (s > 0.0) st->alpha = st->rz / s;
-        else st->done = 1;  // breakdown: p = 0 (already converged) or A not positive definite
-        st->arrive[0] = 0u;
+    if (last_cta(&st->arrive[0])) {
+        const double s = sum_parts(part, gridDim.x, sh);
+        if (threadIdx.x == 0) {
+            st->pq = s;
+            if (s > 0.0) st->alpha = st->rz / s;
+            else st->done = 1;  // breakdown: p = 0 (already converged) or A not positive definite
+            st->arrive[0] = 0u;
+        }
     }
 }
 
@@ -238,13 +274,18 @@ k_cg_r0(int64_t n3, const double *__restrict__ b, const double *__restrict__ q,
         part[gridDim.x + blockIdx.x] = a1;
         part[2 * gridDim.x + blockIdx.x] = a2;
     }
-    if (last_cta(&st->arrive[1]) && threadIdx.x == 0) {
-        st->rz = sum_parts(part, gridDim.x);
-        st->rr = sum_parts(part + gridDim.x, gridDim.x);
-        st->bb = sum_parts(part + 2 * gridDim.x, gridDim.x);
-        st->iters = 0;
-        st->done = st->rr <= st->tol2 * st->bb ? 1 : 0;
-        st->arrive[1] = 0u;
+    if (last_cta(&st->arrive[1])) {
+        const double s0 = sum_parts(part, gridDim.x, sh);
+        const double s1 = sum_parts(part + gridDim.x, gridDim.x, sh);
+        const double s2 = sum_parts(part + 2 * gridDim.x, gridDim.x, sh);
+        if (threadIdx.x == 0) {
+            st->rz = s0;
+            st->rr = s1;
+            st->bb = s2;
+            st->iters = 0;
+            st->done = s1 <= st->tol2 * s2 ? 1 : 0;
+            st->arrive[1] = 0u;
+        }
     }
 }
 
@@ -271,14 +312,17 @@ k_cg_update(int64_t n3, double *__restrict__ x, double *__restrict__ r, double *
         part[blockIdx.x] = a0;
         part[gridDim.x + blockIdx.x] = a1;
     }
-    if (last_cta(&st->arrive[2]) && threadIdx.x == 0) {
-        const double rzn = sum_parts(part, gridDim.x);
-        st->rr = sum_parts(part + gridDim.x, gridDim.x);
-        st->beta = st->rz != 0.0 ? rzn / st->rz : 0.0;
-        st->rz = rzn;
-        st->iters += 1;
-        if (st->rr <= st->tol2 * st->bb) st->done = 1;
-        st->arrive[2] = 0u;
+    if (last_cta(&st->arrive[2])) {
+        const double rzn = sum_parts(part, gridDim.x, sh);
+        const double rrn = sum_parts(part + gridDim.x, gridDim.x, sh);
+        if (threadIdx.x == 0) {
+            st->rr = rrn;
+            st->beta = st->rz != 0.0 ? rzn / st->rz : 0.0;
+            st->rz = rzn;
+            st->iters += 1;
+            if (rrn <= st->tol2 * st->bb) st->done = 1;
+            st->arrive[2] = 0u;
+        }
     }
 }
 
@@ -353,7 +397,7 @@ int cg_chunk(Ctx *c, cudaStream_t s) {
     double *dinv = q + n3;
     CgState *st = reinterpret_cast<CgState *>(c->cg_state);
     for (int it = 0; it < CG_CHUNK; ++it) {
-        k_cg_spmv<<<gv, DYN_TPB, 0, s>>>(c->n, c->row_ptr, c->col, c->val, c->mass,
+        k_cg_spmv<<<gv, DYN_TPB, 0, s>>>(c->n, c->dyn_perm, c->row_ptr, c->col, c->val, c->mass,
                                         c->dyn_h * c->dyn_h, c->cg_free, p, q, c->cg_part, st, true);
         k_cg_update<<<gv, DYN_TPB, 0, s>>>(n3, x, r, z, p, q, dinv, c->cg_part, st);
         k_cg_pupdate<<<gv, DYN_TPB, 0, s>>>(n3, p, z, st);
@@ -379,7 +423,7 @@ int launch_dyn_step(Ctx *c, double tol, int32_t max_iter, int32_t *iters, double
         k_cg_init<<<gv, DYN_TPB, 0, s>>>(n3, c->adj_ptr, c->adj, c->row_ptr, c->val, c->mass,
                                          c->clamped, c->du, c->dv, c->df, c->dyn_h, x, b, dinv,
                                          c->cg_free);
-        k_cg_spmv<<<gv, DYN_TPB, 0, s>>>(c->n, c->row_ptr, c->col, c->val, c->mass,
+        k_cg_spmv<<<gv, DYN_TPB, 0, s>>>(c->n, c->dyn_perm, c->row_ptr, c->col, c->val, c->mass,
                                         c->dyn_h * c->dyn_h, c->cg_free, x, q, c->cg_part, st, false);
         k_cg_r0<<<gv, DYN_TPB, 0, s>>>(n3, b, q, dinv, r, z, p, c->cg_part, st);
         STA_CUDA_TRY(cudaGetLastError());
@@ -445,6 +489,17 @@ extern "C" int sta_dyn_setup(sta_ctx *x, double rho, double h, const double *f,
         STA_TRY(dev_alloc(c, &c->cg_free, n3));
         STA_TRY(dev_alloc(c, &c->cg_part, 3 * (int64_t)c->cg_grid));
         STA_TRY(dev_alloc(c, &c->cg_state, (int64_t)sizeof(CgState)));
+        // the SpMV's node order: ascending row length (ties by node id)
+        STA_TRY(dev_alloc(c, &c->dyn_perm, n));
+        std::vector<int32_t> rp(3 * n + 1), perm(n);
+        STA_CUDA_TRY(cudaMemcpy(rp.data(), c->row_ptr, sizeof(int32_t) * (3 * n + 1),
+                                cudaMemcpyDeviceToHost));
+        for (int64_t a = 0; a < n; ++a) perm[a] = (int32_t)a;
+        std::stable_sort(perm.begin(), perm.end(), [&](int32_t p, int32_t q) {
+            return rp[3 * p + 3] - rp[3 * p] < rp[3 * q + 3] - rp[3 * q];
+        });
+        STA_CUDA_TRY(cudaMemcpy(c->dyn_perm, perm.data(), sizeof(int32_t) * n,
+                                cudaMemcpyHostToDevice));
     }
     std::vector<double> hf(n3 > 0 ? n3 : 1, 0.0);
     std::vector<uint8_t> hc(n > 0 ? n : 1, 0);
