@@ -17,8 +17,8 @@ namespace {
 //
 // Each tile needs two dependent loads before its first add (tile record -> unit records and
 // codes), so the persistent warps run them as a software pipeline: while tile w folds, the
-// first code chunk of tile w+W, the unit records of tile w+2W and the tile record of tile w+3W
-// are in flight (W = warps in the grid).  Operands, order and operations are those of
+// first three code chunks of tile w+W (96 codes: most tiles' whole range), the unit records of
+// tile w+2W and the tile record of tile w+3W are in flight (W = warps in the grid).  Operands, order and operations are those of
 // fold_direct and k_fold_entries.
 // ------------------------------------------------------------------------------------------
 constexpr int FLAT_CAP = 448;  // staged active codes per tile; a larger tile folds from the list
@@ -71,6 +71,8 @@ k_fold_flat(FoldArgs A, const int4 *__restrict__ trec, int64_t ntiles) {
     int4 bm1 = L1.valid ? __ldg(A.bmeta + L1.u) : Z4;
     int32_t cr0 = r0.z, cr1 = r0.w;  // the tile's code range
     int32_t code0 = cr0 + lane < cr1 ? __ldg(A.ccode + cr0 + lane) : 0;
+    int32_t code0b = cr0 + 32 + lane < cr1 ? __ldg(A.ccode + cr0 + 32 + lane) : 0;
+    int32_t code0c = cr0 + 64 + lane < cr1 ? __ldg(A.ccode + cr0 + 64 + lane) : 0;
     int32_t nr0 = r1.z, nr1 = r1.w;
 
     for (; w < ntiles; w += W) {  // warp-uniform
@@ -79,15 +81,20 @@ k_fold_flat(FoldArgs A, const int4 *__restrict__ trec, int64_t ntiles) {
         // stage 1: unit records of w + 2W
         const FlatLane L2 = flat_lane(r2, lane);
         const int4 bm2 = L2.valid ? __ldg(A.bmeta + L2.u) : Z4;
-        // stage 2: first code chunk and mirror records of w + W
+        // stage 2: first three code chunks and mirror records of w + W
         const int32_t code1 = nr0 + lane < nr1 ? __ldg(A.ccode + nr0 + lane) : 0;
+        const int32_t code1b = nr0 + 32 + lane < nr1 ? __ldg(A.ccode + nr0 + 32 + lane) : 0;
+        const int32_t code1c = nr0 + 64 + lane < nr1 ? __ldg(A.ccode + nr0 + 64 + lane) : 0;
         const int2 mir1 = L1.valid && !L1.dgl ? __ldg(A.bmirror + L1.u) : make_int2(0, 0);
 
         // stage 3: tile w -- compact its active codes
         int base = 0, lo = 0, hi = 0;
         for (int32_t c0 = cr0; c0 < cr1; c0 += 32) {  // warp-uniform
             const int32_t c = c0 + lane;
-            const int32_t code = c0 == cr0 ? code0 : (c < cr1 ? __ldg(A.ccode + c) : 0);
+            const int32_t code = c0 == cr0        ? code0
+                                 : c0 == cr0 + 32 ? code0b
+                                 : c0 == cr0 + 64 ? code0c
+                                                  : (c < cr1 ? __ldg(A.ccode + c) : 0);
             const unsigned m = __ballot_sync(FULL, code < 0);
             const int pos = base + __popc(m & below);
             if (code < 0 && pos < FLAT_CAP) scode[pos] = (int32_t)word_offset((uint32_t)code);
@@ -170,6 +177,8 @@ k_fold_flat(FoldArgs A, const int4 *__restrict__ trec, int64_t ntiles) {
         cr0 = nr0;
         cr1 = nr1;
         code0 = code1;
+        code0b = code1b;
+        code0c = code1c;
         L1 = L2;
         bm1 = bm2;
         nr0 = r2.z;
