@@ -26,9 +26,6 @@ namespace {
 __device__ __forceinline__ int exp_field(double x) {
     return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
 }
-__device__ __forceinline__ double pow2i(int x) {  // 2^x for x in [-1022, 1023], exact
-    return __longlong_as_double((long long)(x + 1023) << 52);
-}
 __device__ __forceinline__ int ceil_log2(int64_t k) {  // k >= 1
     int L = 0;
     while (((int64_t)1 << L) < k) ++L;
@@ -110,34 +107,6 @@ __device__ __forceinline__ void fx_write(const FoldArgs &A, const int16_t *__res
     } else {
         A.val[k] = v;
         A.val[mir.x + (q % 3) * mir.y + q / 3] = v;
-    }
-}
-
-// Fixed-point rebuild: one thread per fold entry (tiles of the rebuild); S_k = the integer sum
-// over the unit's active contributors, stored, and converted.
-__global__ void k_fx_rebuild(FoldArgs A, const int4 *__restrict__ trec, int64_t ntiles,
-                             const long long *__restrict__ Kq, const int16_t *__restrict__ e,
-                             long long *__restrict__ S) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t w = warp; w < ntiles; w += W) {
-        const int4 r = __ldg(trec + w);
-        const bool dgl = (r.y >> 4) & 1;
-        if (lane >= (r.y >> 5)) continue;
-        const int per = dgl ? FOLD_TASKS_DIAG : FOLD_TASKS_PAIR;
-        const int ei = (r.y & 15) + lane;
-        const int32_t u = r.x + ei / per;
-        const int q = ei % per;
-        const int4 bm = __ldg(A.bmeta + u);
-        const int2 mir = dgl ? make_int2(0, 0) : __ldg(A.bmirror + u);
-        long long acc = 0;
-        for (int32_t c = bm.z; c < bm.w; ++c) {
-            const int32_t code = __ldg(A.ccode + c);
-            if (code < 0) acc += __ldg(Kq + word_offset((uint32_t)code) + q);
-        }
-        S[unit_key(bm, dgl, q)] = acc;
-        fx_write(A, e, bm, mir, dgl, q, acc);
     }
 }
 
@@ -239,15 +208,6 @@ int launch_fx_prepare(Ctx *c, cudaStream_t s) {
     STA_CUDA_TRY(cudaMemsetAsync(c->fx_q, 0, sizeof(long long) * KE_STRIDE * c->T, s));
     k_fx_quantize<<<grid_cap(c, 10 * c->T, 256), 256, 0, s>>>(c->T, c->tunit, c->bmeta, c->Ke,
                                                              c->fx_e, c->fx_q);
-    STA_CUDA_TRY(cudaGetLastError());
-    return STA_OK;
-}
-
-int launch_fx_rebuild(Ctx *c, cudaStream_t s) {
-    if (c->ntiles == 0) return STA_OK;
-    const int threads = 128;
-    k_fx_rebuild<<<grid_cap(c, c->ntiles * 32, threads), threads, 0, s>>>(
-        fold_args(c), c->ftile, c->ntiles, c->fx_q, c->fx_e, c->fx_s);
     STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;
 }

@@ -34,6 +34,11 @@ struct FoldArgs {
 };
 
 // +0.0 + v without an FP64 operation: identical except that -0.0 becomes +0.0.
+// 2^x for x in [-1022, 1023], exact (the fixed-point scale of an entry)
+__device__ __forceinline__ double pow2i(int x) {
+    return __longlong_as_double((long long)(x + 1023) << 52);
+}
+
 __device__ __forceinline__ double plus_zero(double v) {
     long long bits = __double_as_longlong(v);
     return __longlong_as_double(bits == (long long)0x8000000000000000ULL ? 0LL : bits);

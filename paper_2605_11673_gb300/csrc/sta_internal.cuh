@@ -266,7 +266,6 @@ int launch_spmv(Ctx *c, const double *val, const double *x, double *y, cudaStrea
 int launch_rebuild(Ctx *c, cudaStream_t s);                      // sta_assemble.cu
 int launch_stream_frame(Ctx *c, FrameHeader *frame, int64_t cap, cudaStream_t s);  // sta_stream.cu
 int launch_fx_prepare(Ctx *c, cudaStream_t s);                   // sta_fixed.cu
-int launch_fx_rebuild(Ctx *c, cudaStream_t s);
 int launch_fx_frame(Ctx *c, const int32_t *edited, int64_t m, const int64_t *m_dev, int64_t cap,
                     int32_t *touched, unsigned long long *counters, cudaStream_t s);
 int launch_mask_bits(Ctx *c, cudaStream_t s);                    // codes <- mask

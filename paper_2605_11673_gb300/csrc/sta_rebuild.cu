@@ -1,6 +1,9 @@
 // Full rebuild (a2 of Algorithm 1; the full_rebuild policy of Sec. 3.5): every value of the
 // superset pattern folded from the element cache over the active mask, one lane per fold
-// entry (k_fold_flat).  Fold definition and shared device code: sta_fold.cuh.
+// entry (k_fold_flat), in FP64 or, under STA_POLICY_FIXED, as the fixed-point integer sum.
+// Fold definition and shared device code: sta_fold.cuh.
+#include <type_traits>
+
 #include "sta_fold.cuh"
 
 namespace sta {
@@ -47,9 +50,24 @@ __device__ __forceinline__ int4 flat_rec(const int4 *__restrict__ trec, int64_t 
     return w < ntiles ? __ldg(trec + w) : make_int4(0, 0, 0, 0);  // no valid lane, no codes
 }
 
-template <int WARPS>  // warps per CTA: 2, 4 or 8 (at most 64 registers a thread)
+// Fixed-point operands of the fold (policy STA_POLICY_FIXED, sta_fixed.cu): the quantised
+// contributions at the element-cache offsets, the exponent of each entry and the integer sums,
+// keyed by the value index of the entry's upper block.
+struct FxArgs {
+    const long long *Kq;
+    const int16_t *e;
+    long long *S;
+};
+
+// FX = false: the canonical FP64 fold.  FX = true: the same tiles, compaction and operand
+// order over the quantised contributions with int64 adds (integer pipe), then S_k stored and
+// converted once, val = double(S_k) 2^e_k (+ eps on the diagonal).
+template <int WARPS, bool FX>  // warps per CTA: 2, 4 or 8 (at most 64 registers a thread)
 __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS)
-k_fold_flat(FoldArgs A, const int4 *__restrict__ trec, int64_t ntiles) {
+k_fold_flat(FoldArgs A, const int4 *__restrict__ trec, int64_t ntiles, FxArgs X) {
+    using V = typename std::conditional<FX, long long, double>::type;
+    const V *__restrict__ src;
+    if constexpr (FX) src = X.Kq; else src = A.Ke;
     __shared__ int32_t sbuf[WARPS][FLAT_CAP];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -109,24 +127,31 @@ k_fold_flat(FoldArgs A, const int4 *__restrict__ trec, int64_t ntiles) {
         const int n = L.valid ? hi - lo : 0;
         const bool dgl = L.dgl;
         const int q = L.q;
-        double acc = 0.0;
+        // 6-run entry q = (i, j), i <= j, of a diagonal unit; 3x3 row-major of a pair unit
+        const int ei = dgl ? (q < 3 ? 0 : (q < 5 ? 1 : 2)) : q / 3;
+        const int ej = dgl ? (q < 3 ? q : (q < 5 ? q - 2 : 2)) : q % 3;
+        const int32_t key = bm0.x + ei * (bm0.y >> 1) + ej;
+        int ex = 0;  // the entry's fixed-point exponent, loaded before the fold
+        if constexpr (FX) ex = L.valid ? (int)__ldg(X.e + key) : 0;
+        V acc = V(0);
         if (base <= FLAT_CAP) {
             const int maxn = __reduce_max_sync(FULL, n);
             // staged entries are element-cache offsets of the contributors' runs
             const uint32_t *sc = reinterpret_cast<const uint32_t *>(scode) + lo;
             // every guard on maxn is warp-uniform: a tile issues no operand work past its
             // longest fold (a tile of units without active contributors issues none at all)
-#define STA_LD(j) ((j) < n ? __ldg(A.Ke + sc[(j)] + q) : 0.0)
+#define STA_LD(j) ((j) < n ? __ldg(src + sc[(j)] + q) : V(0))
             if (maxn > 0) {
-                acc = plus_zero(STA_LD(0));  // the first contribution: +0.0 + v, no FP64 add
-                double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+                if constexpr (FX) acc = STA_LD(0);
+                else acc = plus_zero(STA_LD(0));  // the first contribution: +0.0 + v, no FP64 add
+                V v0 = V(0), v1 = V(0), v2 = V(0), v3 = V(0);
                 if (maxn > 1) v0 = STA_LD(1);
                 if (maxn > 2) v1 = STA_LD(2);
                 if (maxn > 3) v2 = STA_LD(3);
                 if (maxn > 4) v3 = STA_LD(4);
                 int j = 1;
                 for (; j + 4 <= maxn; j += 4) {  // next 4 operands in flight
-                    double x0 = 0.0, x1 = 0.0, x2 = 0.0, x3 = 0.0;
+                    V x0 = V(0), x1 = V(0), x2 = V(0), x3 = V(0);
                     if (j + 4 < maxn) x0 = STA_LD(j + 4);
                     if (j + 5 < maxn) x1 = STA_LD(j + 5);
                     if (j + 6 < maxn) x2 = STA_LD(j + 6);
@@ -150,23 +175,27 @@ k_fold_flat(FoldArgs A, const int4 *__restrict__ trec, int64_t ntiles) {
             for (int32_t c = bm0.z; c < bm0.w; ++c) {
                 const int32_t code = __ldg(A.ccode + c);
                 if (code >= 0) continue;
-                const double v = __ldg(A.Ke + word_offset((uint32_t)code) + q);
-                acc = j == 0 ? plus_zero(v) : acc + v;
+                const V v = __ldg(src + word_offset((uint32_t)code) + q);
+                if constexpr (FX) acc += v;
+                else acc = j == 0 ? plus_zero(v) : acc + v;
                 ++j;
             }
         }
         if (L.valid) {
-            const int rs = bm0.y >> 1;
-            if (dgl) {  // 6-run entry q = (i, j), i <= j, mirrored; eps on the diagonal
-                const int i = q < 3 ? 0 : (q < 5 ? 1 : 2), j = q < 3 ? q : (q < 5 ? q - 2 : 2);
-                double a = acc;
-                if (i == j && has_eps) a += A.eps;
-                A.val[bm0.x + i * rs + j] = a;
-                if (i != j) A.val[bm0.x + j * rs + i] = a;
+            double a;
+            if constexpr (FX) {
+                X.S[key] = acc;
+                a = __ll2double_rn(acc) * pow2i(ex);
             } else {
-                const int qi = q / 3, qj = q % 3;
-                A.val[bm0.x + qi * rs + qj] = acc;
-                A.val[mir0.x + qj * mir0.y + qi] = acc;
+                a = acc;
+            }
+            if (dgl) {  // mirrored inside the block; eps on the diagonal
+                if (ei == ej && has_eps) a += A.eps;
+                A.val[key] = a;
+                if (ei != ej) A.val[bm0.x + ej * (bm0.y >> 1) + ei] = a;
+            } else {
+                A.val[key] = a;
+                A.val[mir0.x + ej * mir0.y + ei] = a;
             }
         }
         __syncwarp();
@@ -193,18 +222,27 @@ k_fold_flat(FoldArgs A, const int4 *__restrict__ trec, int64_t ntiles) {
 // (block_threads 64, 128 or 256; blocks_per_sm 0 = occupancy maximum).
 int launch_rebuild(Ctx *c, cudaStream_t s) {
     if (c->ntiles == 0) return STA_OK;
-    if (c->policy == STA_POLICY_FIXED) return launch_fx_rebuild(c, s);
+    const bool fx = c->policy == STA_POLICY_FIXED;
+    const FxArgs X{c->fx_q, c->fx_e, c->fx_s};
     const int threads = c->block_threads == 64 || c->block_threads == 256 ? c->block_threads : 128;
-    const void *kern = threads == 64    ? (const void *)k_fold_flat<2>
-                       : threads == 256 ? (const void *)k_fold_flat<8>
-                                        : (const void *)k_fold_flat<4>;
+    const void *kern = threads == 64    ? (fx ? (const void *)k_fold_flat<2, true>
+                                              : (const void *)k_fold_flat<2, false>)
+                       : threads == 256 ? (fx ? (const void *)k_fold_flat<8, true>
+                                              : (const void *)k_fold_flat<8, false>)
+                                        : (fx ? (const void *)k_fold_flat<4, true>
+                                              : (const void *)k_fold_flat<4, false>);
     const int grid = persistent_grid(c, kern, threads, c->ntiles * 32, true);
-    if (threads == 64)
-        k_fold_flat<2><<<grid, threads, 0, s>>>(fold_args(c), c->ftile, c->ntiles);
-    else if (threads == 256)
-        k_fold_flat<8><<<grid, threads, 0, s>>>(fold_args(c), c->ftile, c->ntiles);
-    else
-        k_fold_flat<4><<<grid, threads, 0, s>>>(fold_args(c), c->ftile, c->ntiles);
+    const FoldArgs A = fold_args(c);
+    if (threads == 64) {
+        if (fx) k_fold_flat<2, true><<<grid, threads, 0, s>>>(A, c->ftile, c->ntiles, X);
+        else k_fold_flat<2, false><<<grid, threads, 0, s>>>(A, c->ftile, c->ntiles, X);
+    } else if (threads == 256) {
+        if (fx) k_fold_flat<8, true><<<grid, threads, 0, s>>>(A, c->ftile, c->ntiles, X);
+        else k_fold_flat<8, false><<<grid, threads, 0, s>>>(A, c->ftile, c->ntiles, X);
+    } else {
+        if (fx) k_fold_flat<4, true><<<grid, threads, 0, s>>>(A, c->ftile, c->ntiles, X);
+        else k_fold_flat<4, false><<<grid, threads, 0, s>>>(A, c->ftile, c->ntiles, X);
+    }
     STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;
 }
