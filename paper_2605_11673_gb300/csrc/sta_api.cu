@@ -161,9 +161,8 @@ int sta::create_impl(const double *nodes, int64_t n_nodes, const int32_t *tets, 
         return bail(fail(STA_EINVAL, std::to_string(back[0]) +
                                          " tetrahedra have det <= 0 (first: tet " +
                                          std::to_string(back[2]) + ")"));
-    c->host_mask.assign((size_t)n_tets, 0);
+    c->tstate.assign((size_t)n_tets, 0);
     c->seen.assign((size_t)n_tets, 0);
-    c->stamp.assign((size_t)n_tets, 0);
     c->last_counters = c->counters;
     if (cudaMallocHost((void **)&x->h_mask, (size_t)(n_tets > 0 ? n_tets : 1)) != cudaSuccess)
         return bail(fail(STA_ENOMEM, "pinned mask buffer"));
@@ -220,9 +219,8 @@ extern "C" int sta_proxy_create(int64_t n_nodes, const int32_t *tets, int64_t n_
     if (cudaStreamSynchronize(s) != cudaSuccess)
         return bail(fail(STA_ECUDA, std::string("proxy create: ") +
                                         cudaGetErrorString(cudaGetLastError())));
-    c->host_mask.assign((size_t)n_tets, 0);
+    c->tstate.assign((size_t)n_tets, 0);
     c->seen.assign((size_t)n_tets, 0);
-    c->stamp.assign((size_t)n_tets, 0);
     c->last_counters = c->counters;
     if (cudaMallocHost((void **)&x->h_mask, (size_t)(n_tets > 0 ? n_tets : 1)) != cudaSuccess)
         return bail(fail(STA_ENOMEM, "pinned mask buffer"));
@@ -246,17 +244,17 @@ int sta_full_rebuild(sta_ctx *x, const uint8_t *mask, int mask_on_device, void *
     cudaStream_t s = (cudaStream_t)stream;
     if (c->T > 0) {
         if (mask_on_device) {
+            std::vector<uint8_t> hm((size_t)c->T);
             STA_CUDA_TRY(cudaMemcpyAsync(c->mask, mask, (size_t)c->T, cudaMemcpyDeviceToDevice, s));
-            STA_CUDA_TRY(cudaMemcpyAsync(c->host_mask.data(), mask, (size_t)c->T,
-                                         cudaMemcpyDeviceToHost, s));
+            STA_CUDA_TRY(cudaMemcpyAsync(hm.data(), mask, (size_t)c->T, cudaMemcpyDeviceToHost, s));
             STA_CUDA_TRY(cudaStreamSynchronize(s));
-            for (auto &b : c->host_mask) b = b ? 1 : 0;
+            for (int64_t t = 0; t < c->T; ++t) ts_set_active(c, t, hm[t] != 0);
         } else {
             STA_TRY(wait_staging(x));
             for (int64_t t = 0; t < c->T; ++t) {
-                uint8_t b = mask[t] ? 1 : 0;
-                c->host_mask[t] = b;
-                x->h_mask[t] = b;
+                const bool on = mask[t] != 0;
+                ts_set_active(c, t, on);
+                x->h_mask[t] = on ? 1 : 0;
             }
             STA_CUDA_TRY(cudaMemcpyAsync(c->mask, x->h_mask, (size_t)c->T, cudaMemcpyHostToDevice, s));
             STA_CUDA_TRY(cudaEventRecord(x->h2d_done, s));
@@ -341,60 +339,51 @@ int sta_apply_edits(sta_ctx *x, const sta_edit *edits, int64_t n_edits, void *st
 
     // one pass: validate each edit against the host mirror of the mask, stage it and apply it
     // to the mirror; on a bad edit, undo the mirror changes made so far and change nothing
-    if (++c->stamp_gen == 0) {  // stamps wrapped (every 255 calls): clear them
-        std::fill(c->stamp.begin(), c->stamp.end(), (uint8_t)0);
+    if (++c->stamp_gen > TS_STAMP) {  // stamps wrapped (every 127 calls): clear them
+        for (auto &b : c->tstate) b &= TS_ACTIVE;
         c->stamp_gen = 1;
     }
     const uint8_t gen = c->stamp_gen;
-    uint8_t *stamp = c->stamp.data();
-    uint8_t *hm = c->host_mask.data();
+    uint8_t *ts = c->tstate.data();
     int32_t *stage = frame_edited(h);
     int64_t k = 0, e = 0;
     const char *why = nullptr;
     for (; e < n_edits; ++e) {
         if (e + 16 < n_edits) {  // the per-tet state is accessed at random: fetch it ahead
             const sta_edit &F = edits[e + 16];
-            if (F.tet >= 0 && F.tet < c->T) {
-                __builtin_prefetch(stamp + F.tet, 1);
-                __builtin_prefetch(hm + F.tet, 1);
-            }
-            if (F.op == STA_SWAP && F.tet2 >= 0 && F.tet2 < c->T) {
-                __builtin_prefetch(stamp + F.tet2, 1);
-                __builtin_prefetch(hm + F.tet2, 1);
-            }
+            if (F.tet >= 0 && F.tet < c->T) __builtin_prefetch(ts + F.tet, 1);
+            if (F.op == STA_SWAP && F.tet2 >= 0 && F.tet2 < c->T) __builtin_prefetch(ts + F.tet2, 1);
         }
         const sta_edit &E = edits[e];
         if (E.op < 0 || E.op > 2) { why = "bad op"; break; }
         if (E.tet < 0 || E.tet >= c->T) { why = "tet out of range"; break; }
-        if (stamp[E.tet] == gen) { why = "tet named twice"; break; }
+        const uint8_t s1 = ts[E.tet];
+        if ((s1 & TS_STAMP) == gen) { why = "tet named twice"; break; }
         if (E.op == STA_DEACTIVATE) {
-            if (!hm[E.tet]) { why = "deactivating an inactive tet"; break; }
-            stamp[E.tet] = gen;
+            if (!(s1 & TS_ACTIVE)) { why = "deactivating an inactive tet"; break; }
+            ts[E.tet] = gen;
             stage[k++] = E.tet;
-            hm[E.tet] = 0;
         } else if (E.op == STA_ACTIVATE) {
-            if (hm[E.tet]) { why = "activating an active tet"; break; }
-            stamp[E.tet] = gen;
+            if (s1 & TS_ACTIVE) { why = "activating an active tet"; break; }
+            ts[E.tet] = (uint8_t)(TS_ACTIVE | gen);
             stage[k++] = (int32_t)((uint32_t)E.tet | 0x80000000u);
-            hm[E.tet] = 1;
         } else {
             if (E.tet2 < 0 || E.tet2 >= c->T) { why = "tet2 out of range"; break; }
-            if (E.tet2 == E.tet || stamp[E.tet2] == gen) { why = "tet2 named twice"; break; }
-            if (!hm[E.tet] || hm[E.tet2]) { why = "swap needs an active tet and an inactive tet2"; break; }
-            stamp[E.tet] = gen;
-            stamp[E.tet2] = gen;
+            const uint8_t s2 = ts[E.tet2];
+            if (E.tet2 == E.tet || (s2 & TS_STAMP) == gen) { why = "tet2 named twice"; break; }
+            if (!(s1 & TS_ACTIVE) || (s2 & TS_ACTIVE)) { why = "swap needs an active tet and an inactive tet2"; break; }
+            ts[E.tet] = gen;
+            ts[E.tet2] = (uint8_t)(TS_ACTIVE | gen);
             stage[k++] = E.tet;
             stage[k++] = (int32_t)((uint32_t)E.tet2 | 0x80000000u);
-            hm[E.tet] = 0;
-            hm[E.tet2] = 1;
         }
     }
     if (why) {
         for (int64_t r = 0; r < e; ++r) {  // undo (each tet appears once, so this is exact)
             const sta_edit &E = edits[r];
-            if (E.op == STA_DEACTIVATE) hm[E.tet] = 1;
-            else if (E.op == STA_ACTIVATE) hm[E.tet] = 0;
-            else { hm[E.tet] = 1; hm[E.tet2] = 0; }
+            if (E.op == STA_DEACTIVATE) ts_set_active(c, E.tet, true);
+            else if (E.op == STA_ACTIVATE) ts_set_active(c, E.tet, false);
+            else { ts_set_active(c, E.tet, true); ts_set_active(c, E.tet2, false); }
         }
         return fail(STA_EINVAL, "edit " + std::to_string(e) + ": " + why);
     }

@@ -189,8 +189,7 @@ struct Ctx {
     int64_t edit_cap = 0;         // edited tetrahedra a frame block holds
     int64_t last_edited = 0;
     unsigned long long *last_counters = nullptr;  // device counters of the last frame
-    std::vector<uint8_t> stamp;   // host: edit-list duplicate check, stamp_gen = "seen"; one
-    uint8_t stamp_gen = 0;        // byte per tet keeps it and the mask mirror cache-resident
+    uint8_t stamp_gen = 0;        // the sta_apply_edits call's stamp (1 .. 127), see tstate
 
     // graph-Laplacian proxy operator (sta_proxy.cu); its CSR is the node-level pattern
     // (row_ptr = adj_ptr, col = adj, nrows = n, nnz = nblocks)
@@ -231,11 +230,21 @@ struct Ctx {
     int32_t *local_rp = nullptr;   // sum_i (3 n_i + 1): instance i at 3 node_off[i] + i
     int32_t *local_col = nullptr;  // nnz: column minus the instance's first DOF
 
-    std::vector<uint8_t> host_mask;
+    // host mirror of every tetrahedron, one byte: bit 7 = active (the mask), bits 0..6 = the
+    // stamp of the last sta_apply_edits call that named it (duplicate check); one random
+    // access per edited tetrahedron serves both checks
+    std::vector<uint8_t> tstate;
     std::vector<uint8_t> seen;  // per-tet scratch for edit validation (all zero at rest)
     int64_t device_bytes = 0;
     std::vector<void *> allocations;
 };
+
+constexpr uint8_t TS_ACTIVE = 0x80;
+constexpr uint8_t TS_STAMP = 0x7f;
+inline bool ts_active(const Ctx *c, int64_t t) { return (c->tstate[t] & TS_ACTIVE) != 0; }
+inline void ts_set_active(Ctx *c, int64_t t, bool on) {
+    c->tstate[t] = (uint8_t)((c->tstate[t] & TS_STAMP) | (on ? TS_ACTIVE : 0));
+}
 
 template <typename T> int dev_alloc(Ctx *c, T **p, int64_t count) {
     size_t bytes = sizeof(T) * (size_t)(count > 0 ? count : 1);

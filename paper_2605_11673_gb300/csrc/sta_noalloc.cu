@@ -60,13 +60,13 @@ extern "C" int sta_apply_edits_noalloc(sta_ctx *x, const sta_edit *edits, int64_
         if (E.tet < 0 || E.tet >= c->T) { bad = e; why = "tet out of range"; break; }
         if (c->seen[E.tet]) { bad = e; why = "tet named twice"; break; }
         c->seen[E.tet] = 1;
-        if (E.op == STA_DEACTIVATE && !c->host_mask[E.tet]) { bad = e; why = "deactivating an inactive tet"; break; }
-        if (E.op == STA_ACTIVATE && c->host_mask[E.tet]) { bad = e; why = "activating an active tet"; break; }
+        if (E.op == STA_DEACTIVATE && !ts_active(c, E.tet)) { bad = e; why = "deactivating an inactive tet"; break; }
+        if (E.op == STA_ACTIVATE && ts_active(c, E.tet)) { bad = e; why = "activating an active tet"; break; }
         if (E.op == STA_SWAP) {
             if (E.tet2 < 0 || E.tet2 >= c->T) { bad = e; why = "tet2 out of range"; break; }
             if (c->seen[E.tet2]) { bad = e; why = "tet2 named twice"; break; }
             c->seen[E.tet2] = 1;
-            if (!c->host_mask[E.tet] || c->host_mask[E.tet2]) { bad = e; why = "swap needs an active tet and an inactive tet2"; break; }
+            if (!ts_active(c, E.tet) || ts_active(c, E.tet2)) { bad = e; why = "swap needs an active tet and an inactive tet2"; break; }
             ++m;
         }
         ++m;
@@ -86,15 +86,15 @@ extern "C" int sta_apply_edits_noalloc(sta_ctx *x, const sta_edit *edits, int64_
         const sta_edit &E = edits[e];
         if (E.op == STA_DEACTIVATE) {
             g_host_stage[k++] = E.tet;
-            c->host_mask[E.tet] = 0;
+            ts_set_active(c, E.tet, false);
         } else if (E.op == STA_ACTIVATE) {
             g_host_stage[k++] = (int32_t)((uint32_t)E.tet | 0x80000000u);
-            c->host_mask[E.tet] = 1;
+            ts_set_active(c, E.tet, true);
         } else {
             g_host_stage[k++] = E.tet;
             g_host_stage[k++] = (int32_t)((uint32_t)E.tet2 | 0x80000000u);
-            c->host_mask[E.tet] = 0;
-            c->host_mask[E.tet2] = 1;
+            ts_set_active(c, E.tet, false);
+            ts_set_active(c, E.tet2, true);
         }
     }
     cudaStream_t s = (cudaStream_t)stream;
