@@ -348,6 +348,9 @@ int sta_proxy_state(const sta_ctx *ctx, const int32_t **mult, const int32_t **de
  * the mass update.  May be called again to change rho, h, f or clamped (resets u and v).
  * sta_dyn_step: one step; synchronises `stream`; *iters = CG iterations, *rel_res =
  * ||r|| / ||b|| at exit (0 when b = 0); either may be NULL.  Reaching max_iter is not an error.
+ * sta_dyn_apply: y = (M_t + h^2 K_t) x on the free DOFs, 0 elsewhere (x read on the free DOFs
+ * only); x and y are device arrays of 3n doubles, y must not overlap x; asynchronous on
+ * `stream`.  The operator the step's CG applies, for a caller's own solver.
  * sta_dyn_state: device pointers (context-owned): u, v (3n) and the lumped mass (n).
  * sta_dyn_set_state: overwrite u and/or v (3n each, host or device; NULL = keep).
  */
@@ -355,6 +358,7 @@ int sta_dyn_setup(sta_ctx *ctx, double rho, double h, const double *f, const uin
                   void *stream);
 int sta_dyn_step(sta_ctx *ctx, double tol, int32_t max_iter, int32_t *iters, double *rel_res,
                  void *stream);
+int sta_dyn_apply(sta_ctx *ctx, const double *x, double *y, void *stream);
 int sta_dyn_state(const sta_ctx *ctx, const double **u, const double **v, const double **mass);
 int sta_dyn_set_state(sta_ctx *ctx, const double *u, const double *v, int on_device, void *stream);
 

@@ -31,6 +31,7 @@ EXPORTED = (
     "sta_batch_create", "sta_batch_size", "sta_batch_instance", "sta_batch_apply_edits",
     "sta_graph_enable", "sta_graph_disable", "sta_set_policy", "sta_proxy_create",
     "sta_proxy_state", "sta_dyn_setup", "sta_dyn_step", "sta_dyn_state", "sta_dyn_set_state",
+    "sta_dyn_apply",
 )
 STA_NOALLOC_MAX_EDITED = 32768
 STA_POLICY_REFOLD = 0
@@ -99,6 +100,7 @@ def load_library(path: Path | str | None = None):
     L.sta_dyn_step.argtypes = [_p, C.c_double, C.c_int32, _P(C.c_int32), _P(C.c_double), _p]
     L.sta_dyn_state.argtypes = [_p, _P(_p), _P(_p), _P(_p)]
     L.sta_dyn_set_state.argtypes = [_p, _p, _p, _int, _p]
+    L.sta_dyn_apply.argtypes = [_p, _p, _p, _p]
     L.sta_last_error.restype = C.c_char_p
     L.sta_status_string.argtypes = [_int]
     L.sta_status_string.restype = C.c_char_p
@@ -212,6 +214,14 @@ def sta_dyn_step(h: int, tol: float = 1e-10, max_iter: int = 1000, stream=None):
     _check(load_library().sta_dyn_step(h, float(tol), int(max_iter), C.byref(it), C.byref(rr),
                                        _stream_handle(stream)))
     return int(it.value), float(rr.value)
+
+
+def sta_dyn_apply(h: int, x, stream=None):
+    """y = (M + h^2 K) x on the free DOFs (CUDA float64 tensors of 3n)."""
+    x = x.contiguous()
+    y = x.new_empty(x.shape)
+    _check(load_library().sta_dyn_apply(h, x.data_ptr(), y.data_ptr(), _stream_handle(stream)))
+    return y
 
 
 def sta_dyn_state(h: int, owner=None):
@@ -510,6 +520,9 @@ class Assembler:
 
     def dyn_step(self, tol: float = 1e-10, max_iter: int = 1000, stream=None):
         return sta_dyn_step(self.h, tol, max_iter, stream)
+
+    def dyn_apply(self, x, stream=None):
+        return sta_dyn_apply(self.h, x, stream)
 
     def dyn_state(self):
         """(u, v, mass) torch tensors viewing the context's device memory."""

@@ -336,6 +336,19 @@ __global__ void k_cg_pupdate(int64_t n3, double *__restrict__ p, const double *_
         p[i] = __fma_rn(beta, p[i], z[i]);
 }
 
+// x restricted to the free DOFs (0 elsewhere), with the free flags from mass and clamping.
+__global__ void k_dyn_restrict(int64_t n3, const double *__restrict__ mass,
+                               const uint8_t *__restrict__ clamped, const double *__restrict__ x,
+                               double *__restrict__ xf, uint8_t *__restrict__ fr) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = i / 3;
+        const bool free = !clamped[a] && mass[a] > 0.0;
+        fr[i] = free ? 1 : 0;
+        xf[i] = free ? x[i] : 0.0;
+    }
+}
+
 // u, v from the solution.
 __global__ void k_dyn_advance(int64_t n3, double *__restrict__ u, double *__restrict__ v,
                               const double *__restrict__ x, const uint8_t *__restrict__ fr,
@@ -530,6 +543,24 @@ extern "C" int sta_dyn_step(sta_ctx *x, double tol, int32_t max_iter, int32_t *i
     if (!c->dyn) return fail(STA_ESTATE, "call sta_dyn_setup first");
     if (!(tol >= 0.0) || max_iter < 0) return fail(STA_EINVAL, "tol and max_iter must be >= 0");
     return launch_dyn_step(c, tol, max_iter, iters, rel_res, (cudaStream_t)stream);
+}
+
+extern "C" int sta_dyn_apply(sta_ctx *x, const double *xv, double *y, void *stream) {
+    if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    Ctx *c = &x->c;
+    if (!c->dyn) return fail(STA_ESTATE, "call sta_dyn_setup first");
+    const int64_t n3 = 3 * c->n;
+    if (n3 == 0) return STA_OK;
+    if (!xv || !y) return fail(STA_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    double *xf = c->cg + 4 * n3;  // the CG's p buffer (free between steps)
+    const unsigned gv = (unsigned)c->cg_grid;
+    k_dyn_restrict<<<gv, DYN_TPB, 0, s>>>(n3, c->mass, c->clamped, xv, xf, c->cg_free);
+    k_cg_spmv<<<gv, DYN_TPB, 0, s>>>(c->n, c->dyn_perm, c->row_ptr, c->col, c->val, c->mass,
+                                    c->dyn_h * c->dyn_h, c->cg_free, xf, y, c->cg_part,
+                                    reinterpret_cast<CgState *>(c->cg_state), false);
+    STA_CUDA_TRY(cudaGetLastError());
+    return STA_OK;
 }
 
 extern "C" int sta_dyn_state(const sta_ctx *x, const double **u, const double **v,

@@ -160,3 +160,31 @@ def test_dynamics_edge_cases_and_determinism(sta, orc):
     px.close()
     a.close()
     b.close()
+
+
+def test_dyn_apply_vs_oracle_operator(sta, orc):
+    """sta_dyn_apply (the CG's operator) against (M + h^2 K) restricted to the free DOFs,
+    assembled from the oracle's values and mass."""
+    import scipy.sparse as sp
+    import torch
+    wl = W.adjoint_block(N=6)
+    P = orc.Pattern(wl.n_nodes, wl.tets)
+    Ke, _ = orc.element_all(wl.X, wl.tets, wl.E, wl.nu)
+    clamped = wl.meta["clamped_nodes"]
+    asm = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu)
+    mask = wl.masks()[5]
+    asm.full_rebuild(mask)
+    rho, h = 900.0, 3e-3
+    asm.dyn_setup(rho, h, None, clamped)
+    m = P.lumped_mass(wl.X, rho, mask)
+    free = orc.dyn_free(m, clamped)
+    A = (sp.diags(np.repeat(m, 3)) + h * h * P.csr(P.rebuild(Ke, mask))).tocsr()
+    x = np.random.default_rng(3).standard_normal(3 * wl.n_nodes)
+    xf = np.where(free, x, 0.0)
+    ref = np.where(free, A @ xf, 0.0)
+    y = asm.dyn_apply(torch.as_tensor(x, device="cuda")).cpu().numpy()
+    absA = (sp.diags(np.repeat(m, 3)) + h * h * abs(P.csr(P.rebuild(Ke, mask)))).tocsr()
+    bound = 1e-14 * (absA @ np.abs(xf)) + 1e-300
+    assert np.all(np.abs(y - ref) <= 64 * bound)
+    assert np.all(y[~free] == 0.0)
+    asm.close()
