@@ -242,41 +242,48 @@ k_adjoint(const double4_32a *__restrict__ X, const int4 *__restrict__ tets,
                         for (int j = 0; j < 3; ++j) M[i][j] += G[j * bo.y + i];
                 }
                 const double tr = M[0][0] + M[1][1] + M[2][2];
+                // (the adjoint needs no fixed evaluation order: every product-sum below is an
+                // explicit FMA chain, which halves its FP64 instructions under --fmad=false)
                 double Mgb[3], Mtga[3], Mtgb[3], Mga[3];
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
-                    Mgb[i] = M[i][0] * g[b][0] + M[i][1] * g[b][1] + M[i][2] * g[b][2];
-                    Mga[i] = M[i][0] * g[a][0] + M[i][1] * g[a][1] + M[i][2] * g[a][2];
-                    Mtga[i] = M[0][i] * g[a][0] + M[1][i] * g[a][1] + M[2][i] * g[a][2];
-                    Mtgb[i] = M[0][i] * g[b][0] + M[1][i] * g[b][1] + M[2][i] * g[b][2];
+                    Mgb[i] = __fma_rn(M[i][2], g[b][2], __fma_rn(M[i][1], g[b][1], M[i][0] * g[b][0]));
+                    Mga[i] = __fma_rn(M[i][2], g[a][2], __fma_rn(M[i][1], g[a][1], M[i][0] * g[a][0]));
+                    Mtga[i] = __fma_rn(M[2][i], g[a][2], __fma_rn(M[1][i], g[a][1], M[0][i] * g[a][0]));
+                    Mtgb[i] = __fma_rn(M[2][i], g[b][2], __fma_rn(M[1][i], g[b][1], M[0][i] * g[b][0]));
                 }
-                const double gab = g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2];
-                SA += g[a][0] * Mgb[0] + g[a][1] * Mgb[1] + g[a][2] * Mgb[2];
-                SB += g[b][0] * Mga[0] + g[b][1] * Mga[1] + g[b][2] * Mga[2] + tr * gab;
+                const double gab = __fma_rn(g[a][2], g[b][2], __fma_rn(g[a][1], g[b][1], g[a][0] * g[b][0]));
+                SA = __fma_rn(g[a][2], Mgb[2], __fma_rn(g[a][1], Mgb[1], __fma_rn(g[a][0], Mgb[0], SA)));
+                SB = __fma_rn(tr, gab, __fma_rn(g[b][2], Mga[2], __fma_rn(g[b][1], Mga[1],
+                                                                         __fma_rn(g[b][0], Mga[0], SB))));
 #pragma unroll
                 for (int m = 0; m < 3; ++m) {
                     hA[a][m] += Mgb[m];
                     hA[b][m] += Mtga[m];
-                    hB[a][m] += Mtgb[m] + tr * g[b][m];
-                    hB[b][m] += Mga[m] + tr * g[a][m];
+                    hB[a][m] = __fma_rn(tr, g[b][m], hB[a][m] + Mtgb[m]);
+                    hB[b][m] = __fma_rn(tr, g[a][m], hB[b][m] + Mga[m]);
                 }
             }
         const double lamE = nu / (onu * omn), muE = 1.0 / (onu + onu);
         const double lamN = E * (1.0 + 2.0 * nu * nu) / (onu * onu * omn * omn);
         const double muN = -E / (2.0 * onu * onu);
-        dE[t] = V * (lamE * SA + muE * SB);
-        dnu[t] = V * (lamN * SA + muN * SB);
-        const double S = lam * SA + mu * SB;
+        dE[t] = V * __fma_rn(lamE, SA, muE * SB);
+        dnu[t] = V * __fma_rn(lamN, SA, muN * SB);
+        const double S = __fma_rn(lam, SA, mu * SB);
+        double hh[4][3];  // lam hA + mu hB, once per node
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int m = 0; m < 3; ++m) hh[a][m] = __fma_rn(lam, hA[a][m], mu * hB[a][m]);
 #pragma unroll
         for (int cidx = 0; cidx < 4; ++cidx) {
             double o[3] = {S * g[cidx][0], S * g[cidx][1], S * g[cidx][2]};
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                const double hg = (lam * hA[a][0] + mu * hB[a][0]) * g[cidx][0] +
-                                  (lam * hA[a][1] + mu * hB[a][1]) * g[cidx][1] +
-                                  (lam * hA[a][2] + mu * hB[a][2]) * g[cidx][2];
+                const double hg = __fma_rn(hh[a][2], g[cidx][2],
+                                           __fma_rn(hh[a][1], g[cidx][1], hh[a][0] * g[cidx][0]));
 #pragma unroll
-                for (int m = 0; m < 3; ++m) o[m] -= hg * g[a][m];
+                for (int m = 0; m < 3; ++m) o[m] = __fma_rn(-hg, g[a][m], o[m]);
             }
 #pragma unroll
             for (int m = 0; m < 3; ++m) dXe[12 * t + 3 * cidx + m] = V * o[m];
