@@ -362,6 +362,25 @@ int sta_dyn_apply(sta_ctx *ctx, const double *x, double *y, void *stream);
 int sta_dyn_state(const sta_ctx *ctx, const double **u, const double **v, const double **mass);
 int sta_dyn_set_state(sta_ctx *ctx, const double *u, const double *v, int on_device, void *stream);
 
+/*
+ * sta_solve -- the consumer of the assembly (the paper's solver, Sec. 4: conjugate gradients
+ * with diagonal preconditioning) for a static problem A_ff x_f = b_f: Jacobi-PCG on the DOFs
+ * with free[i] != 0 (and a nonzero diagonal), x = 0 elsewhere, from the initial guess in x,
+ * until ||r|| <= tol ||b_f||, max_iter iterations, or no halving of the residual for 1000
+ * iterations (the attainable accuracy).  val: device nnz values of the context's pattern
+ * (NULL = the current values); b, x: device 3n doubles; free: device 3n bytes.  Same kernels
+ * as the implicit-Euler step (fixed-order reductions: deterministic).  Synchronises `stream`.
+ * *iters and *rel_res (||r|| / ||b_f|| from the recurrence) may be NULL.  Elasticity contexts.
+ *
+ * sta_outer_grad -- the adjoint rule of such a solve: grad_val[k] = -lam[row(k)] u[col(k)]
+ * for entries k between free DOFs, 0 elsewhere (lam, u: device nrows doubles; free: device
+ * nrows bytes; grad_val: device nnz doubles).  Asynchronous on `stream`.
+ */
+int sta_solve(sta_ctx *ctx, const double *val, const double *b, const uint8_t *free, double tol,
+              int32_t max_iter, double *x, int32_t *iters, double *rel_res, void *stream);
+int sta_outer_grad(sta_ctx *ctx, const double *lam, const double *u, const uint8_t *free,
+                   double *grad_val, void *stream);
+
 /* Human-readable message of the last error on the calling thread. */
 const char *sta_last_error(void);
 const char *sta_status_string(int status);

@@ -31,7 +31,7 @@ EXPORTED = (
     "sta_batch_create", "sta_batch_size", "sta_batch_instance", "sta_batch_apply_edits",
     "sta_graph_enable", "sta_graph_disable", "sta_set_policy", "sta_proxy_create",
     "sta_proxy_state", "sta_dyn_setup", "sta_dyn_step", "sta_dyn_state", "sta_dyn_set_state",
-    "sta_dyn_apply",
+    "sta_dyn_apply", "sta_solve", "sta_outer_grad",
 )
 STA_NOALLOC_MAX_EDITED = 32768
 STA_POLICY_REFOLD = 0
@@ -101,6 +101,9 @@ def load_library(path: Path | str | None = None):
     L.sta_dyn_state.argtypes = [_p, _P(_p), _P(_p), _P(_p)]
     L.sta_dyn_set_state.argtypes = [_p, _p, _p, _int, _p]
     L.sta_dyn_apply.argtypes = [_p, _p, _p, _p]
+    L.sta_solve.argtypes = [_p, _p, _p, _p, C.c_double, C.c_int32, _p, _P(C.c_int32),
+                            _P(C.c_double), _p]
+    L.sta_outer_grad.argtypes = [_p, _p, _p, _p, _p, _p]
     L.sta_last_error.restype = C.c_char_p
     L.sta_status_string.argtypes = [_int]
     L.sta_status_string.restype = C.c_char_p
@@ -222,6 +225,32 @@ def sta_dyn_apply(h: int, x, stream=None):
     y = x.new_empty(x.shape)
     _check(load_library().sta_dyn_apply(h, x.data_ptr(), y.data_ptr(), _stream_handle(stream)))
     return y
+
+
+def sta_solve(h: int, b, free, val=None, tol: float = 1e-12, max_iter: int = 20000, x0=None,
+              stream=None):
+    """Jacobi-PCG for A_ff x_f = b_f (CUDA tensors: b float64 3n, free bool/uint8 3n);
+    returns (x, iterations, relative residual)."""
+    import torch
+    b = b.contiguous()
+    fr = free.to(torch.uint8).contiguous()
+    x = torch.zeros_like(b) if x0 is None else x0.clone().contiguous()
+    vp = val.contiguous().data_ptr() if val is not None else None
+    it, rr = C.c_int32(), C.c_double()
+    _check(load_library().sta_solve(h, vp, b.data_ptr(), fr.data_ptr(), float(tol), int(max_iter),
+                                    x.data_ptr(), C.byref(it), C.byref(rr), _stream_handle(stream)))
+    return x, int(it.value), float(rr.value)
+
+
+def sta_outer_grad(h: int, lam, u, free, stream=None):
+    """dL/dval = -lam_i u_j on entries between free DOFs (CUDA tensors)."""
+    import torch
+    nnz = sta_sizes(h)["nnz"]
+    g = torch.empty(nnz, dtype=torch.float64, device=lam.device)
+    fr = free.to(torch.uint8).contiguous()
+    _check(load_library().sta_outer_grad(h, lam.contiguous().data_ptr(), u.contiguous().data_ptr(),
+                                         fr.data_ptr(), g.data_ptr(), _stream_handle(stream)))
+    return g
 
 
 def sta_dyn_state(h: int, owner=None):

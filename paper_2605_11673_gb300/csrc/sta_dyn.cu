@@ -336,6 +336,51 @@ __global__ void k_cg_pupdate(int64_t n3, double *__restrict__ p, const double *_
         p[i] = __fma_rn(beta, p[i], z[i]);
 }
 
+// Static solve (sta_solve): b, x0 and the Jacobi inverse diagonal on the caller's free DOFs.
+__global__ void k_cg_init_static(int64_t n3, const int32_t *__restrict__ adj_ptr,
+                                 const int32_t *__restrict__ adj,
+                                 const int32_t *__restrict__ row_ptr,
+                                 const double *__restrict__ val, const uint8_t *__restrict__ free_in,
+                                 const double *__restrict__ b_in, const double *__restrict__ x_in,
+                                 double *__restrict__ x, double *__restrict__ b,
+                                 double *__restrict__ dinv, uint8_t *__restrict__ fr) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = (int32_t)(i / 3), k = (int32_t)(i - 3 * (int64_t)a);
+        double kii = 0.0;
+        if (free_in[i] && adj_ptr[a + 1] > adj_ptr[a]) {
+            int32_t lo = adj_ptr[a], hi = adj_ptr[a + 1];  // the diagonal block of node a
+            while (lo < hi) {
+                const int32_t mid = (lo + hi) >> 1;
+                if (adj[mid] < a) lo = mid + 1; else hi = mid;
+            }
+            kii = val[row_ptr[i] + 3 * (lo - adj_ptr[a]) + k];
+        }
+        const bool free = free_in[i] && kii != 0.0;  // a free DOF needs a diagonal
+        fr[i] = free ? 1 : 0;
+        x[i] = free ? x_in[i] : 0.0;
+        b[i] = free ? b_in[i] : 0.0;
+        dinv[i] = free ? 1.0 / kii : 0.0;
+    }
+}
+
+// The adjoint rule of a solve (A_ff u_f = f_f): dL/dA_ij = -lam_i u_j on entries between free
+// DOFs, 0 elsewhere.  One thread per row.
+__global__ void k_outer_grad(int64_t nrows, const int32_t *__restrict__ row_ptr,
+                             const int32_t *__restrict__ col, const double *__restrict__ lam,
+                             const double *__restrict__ u, const uint8_t *__restrict__ free,
+                             double *__restrict__ g) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrows;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const bool fi = free[i] != 0;
+        const double li = -lam[i];
+        for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            const int32_t j = col[k];
+            g[k] = fi && free[j] ? li * u[j] : 0.0;
+        }
+    }
+}
+
 // x restricted to the free DOFs (0 elsewhere), with the free flags from mass and clamping.
 __global__ void k_dyn_restrict(int64_t n3, const double *__restrict__ mass,
                                const uint8_t *__restrict__ clamped, const double *__restrict__ x,
@@ -402,16 +447,17 @@ int launch_dyn_qmass(Ctx *c, cudaStream_t s) {
 
 namespace {
 
-// One chunk of CG_CHUNK iterations (3 launches each), launched or captured on s.
-int cg_chunk(Ctx *c, cudaStream_t s) {
+// One chunk of CG_CHUNK iterations (3 launches each) of A = diag(mass) + h2 K(val), launched
+// or captured on s.
+int cg_chunk(Ctx *c, const double *val, const double *mass, double h2, cudaStream_t s) {
     const int64_t n3 = 3 * c->n;
     const unsigned gv = c->cg_grid;
     double *x = c->cg, *b = x + n3, *r = b + n3, *z = r + n3, *p = z + n3, *q = p + n3;
     double *dinv = q + n3;
     CgState *st = reinterpret_cast<CgState *>(c->cg_state);
     for (int it = 0; it < CG_CHUNK; ++it) {
-        k_cg_spmv<<<gv, DYN_TPB, 0, s>>>(c->n, c->dyn_perm, c->row_ptr, c->col, c->val, c->mass,
-                                        c->dyn_h * c->dyn_h, c->cg_free, p, q, c->cg_part, st, true);
+        k_cg_spmv<<<gv, DYN_TPB, 0, s>>>(c->n, c->dyn_perm, c->row_ptr, c->col, val, mass, h2,
+                                        c->cg_free, p, q, c->cg_part, st, true);
         k_cg_update<<<gv, DYN_TPB, 0, s>>>(n3, x, r, z, p, q, dinv, c->cg_part, st);
         k_cg_pupdate<<<gv, DYN_TPB, 0, s>>>(n3, p, z, st);
     }
@@ -420,6 +466,63 @@ int cg_chunk(Ctx *c, cudaStream_t s) {
 }
 
 }  // namespace
+
+namespace {
+
+// CG iterations in chunks until converged or max_iter: the captured chunk `g` if given, else
+// direct launches of the chunk for (val, mass, h2).  The host reads the state between chunks;
+// with `stagnate`, it also stops once the residual has not halved for 1000 iterations (the
+// attainable accuracy reached).
+int cg_iterate(Ctx *c, cudaGraphExec_t g, const double *val, const double *mass, double h2,
+               int32_t max_iter, bool stagnate, cudaStream_t s, CgState *hs) {
+    CgState *st = reinterpret_cast<CgState *>(c->cg_state);
+    double best = -1.0;
+    int32_t best_it = 0;
+    for (;;) {
+        if (c->n > 0) {
+            STA_CUDA_TRY(cudaMemcpyAsync(hs, st, sizeof *hs, cudaMemcpyDeviceToHost, s));
+            STA_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+        if (c->n == 0 || hs->done || hs->iters >= max_iter) break;
+        if (stagnate) {
+            if (best < 0.0 || hs->rr < 0.25 * best) {
+                best = hs->rr;
+                best_it = hs->iters;
+            } else if (hs->iters - best_it > 1000) {
+                break;
+            }
+        }
+        if (g) STA_CUDA_TRY(cudaGraphLaunch(g, s));
+        else STA_TRY(cg_chunk(c, val, mass, h2, s));
+    }
+    return STA_OK;
+}
+
+}  // namespace
+
+// The CG buffers shared by the implicit-Euler step and the static solve, allocated once.
+int cg_alloc(Ctx *c) {
+    if (c->cg) return STA_OK;
+    const int64_t n = c->n, n3 = 3 * n;
+    c->cg_grid = (int)dyn_grid(c, n3 > 0 ? n3 : 1);
+    STA_TRY(dev_alloc(c, &c->cg, 7 * n3));
+    STA_TRY(dev_alloc(c, &c->cg_free, n3));
+    STA_TRY(dev_alloc(c, &c->cg_part, 3 * (int64_t)c->cg_grid));
+    STA_TRY(dev_alloc(c, &c->cg_state, (int64_t)sizeof(CgState)));
+    STA_TRY(dev_alloc(c, &c->cg_zero, n));
+    STA_CUDA_TRY(cudaMemset(c->cg_zero, 0, sizeof(double) * (size_t)(n > 0 ? n : 1)));
+    // the SpMV's node order: ascending row length (ties by node id)
+    STA_TRY(dev_alloc(c, &c->dyn_perm, n));
+    std::vector<int32_t> rp(3 * n + 1), perm(n);
+    STA_CUDA_TRY(cudaMemcpy(rp.data(), c->row_ptr, sizeof(int32_t) * (3 * n + 1),
+                            cudaMemcpyDeviceToHost));
+    for (int64_t a = 0; a < n; ++a) perm[a] = (int32_t)a;
+    std::stable_sort(perm.begin(), perm.end(), [&](int32_t p, int32_t q) {
+        return rp[3 * p + 3] - rp[3 * p] < rp[3 * q + 3] - rp[3 * q];
+    });
+    STA_CUDA_TRY(cudaMemcpy(c->dyn_perm, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+    return STA_OK;
+}
 
 int launch_dyn_step(Ctx *c, double tol, int32_t max_iter, int32_t *iters, double *rel_res,
                     cudaStream_t s) {
@@ -446,7 +549,7 @@ int launch_dyn_step(Ctx *c, double tol, int32_t max_iter, int32_t *iters, double
         STA_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        int rc = e == cudaSuccess ? cg_chunk(c, cs) : STA_ECUDA;
+        int rc = e == cudaSuccess ? cg_chunk(c, c->val, c->mass, c->dyn_h * c->dyn_h, cs) : STA_ECUDA;
         cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         if (rc == STA_OK && e == cudaSuccess && e2 == cudaSuccess)
             e2 = cudaGraphInstantiate(&c->g_cg, g, 0);
@@ -458,14 +561,7 @@ int launch_dyn_step(Ctx *c, double tol, int32_t max_iter, int32_t *iters, double
         }
     }
     CgState hs = {};
-    for (;;) {
-        if (n3 > 0) {
-            STA_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof hs, cudaMemcpyDeviceToHost, s));
-            STA_CUDA_TRY(cudaStreamSynchronize(s));
-        }
-        if (n3 == 0 || hs.done || hs.iters >= max_iter) break;
-        STA_CUDA_TRY(cudaGraphLaunch(c->g_cg, s));
-    }
+    STA_TRY(cg_iterate(c, c->g_cg, nullptr, nullptr, 0.0, max_iter, false, s, &hs));
     if (n3 > 0) {
         k_dyn_advance<<<gv, DYN_TPB, 0, s>>>(n3, c->du, c->dv, x, c->cg_free, c->clamped, c->dyn_h);
         STA_CUDA_TRY(cudaGetLastError());
@@ -491,29 +587,14 @@ extern "C" int sta_dyn_setup(sta_ctx *x, double rho, double h, const double *f,
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = c->n, n3 = 3 * n;
     if (!c->qmass) {
-        c->cg_grid = (int)dyn_grid(c, n3 > 0 ? n3 : 1);
         STA_TRY(dev_alloc(c, &c->qmass, c->T));
         STA_TRY(dev_alloc(c, &c->mass, n));
         STA_TRY(dev_alloc(c, &c->du, n3));
         STA_TRY(dev_alloc(c, &c->dv, n3));
         STA_TRY(dev_alloc(c, &c->df, n3));
         STA_TRY(dev_alloc(c, &c->clamped, n));
-        STA_TRY(dev_alloc(c, &c->cg, 7 * n3));
-        STA_TRY(dev_alloc(c, &c->cg_free, n3));
-        STA_TRY(dev_alloc(c, &c->cg_part, 3 * (int64_t)c->cg_grid));
-        STA_TRY(dev_alloc(c, &c->cg_state, (int64_t)sizeof(CgState)));
-        // the SpMV's node order: ascending row length (ties by node id)
-        STA_TRY(dev_alloc(c, &c->dyn_perm, n));
-        std::vector<int32_t> rp(3 * n + 1), perm(n);
-        STA_CUDA_TRY(cudaMemcpy(rp.data(), c->row_ptr, sizeof(int32_t) * (3 * n + 1),
-                                cudaMemcpyDeviceToHost));
-        for (int64_t a = 0; a < n; ++a) perm[a] = (int32_t)a;
-        std::stable_sort(perm.begin(), perm.end(), [&](int32_t p, int32_t q) {
-            return rp[3 * p + 3] - rp[3 * p] < rp[3 * q + 3] - rp[3 * q];
-        });
-        STA_CUDA_TRY(cudaMemcpy(c->dyn_perm, perm.data(), sizeof(int32_t) * n,
-                                cudaMemcpyHostToDevice));
     }
+    STA_TRY(cg_alloc(c));
     std::vector<double> hf(n3 > 0 ? n3 : 1, 0.0);
     std::vector<uint8_t> hc(n > 0 ? n : 1, 0);
     if (f) std::copy(f, f + n3, hf.begin());
@@ -559,6 +640,56 @@ extern "C" int sta_dyn_apply(sta_ctx *x, const double *xv, double *y, void *stre
     k_cg_spmv<<<gv, DYN_TPB, 0, s>>>(c->n, c->dyn_perm, c->row_ptr, c->col, c->val, c->mass,
                                     c->dyn_h * c->dyn_h, c->cg_free, xf, y, c->cg_part,
                                     reinterpret_cast<CgState *>(c->cg_state), false);
+    STA_CUDA_TRY(cudaGetLastError());
+    return STA_OK;
+}
+
+extern "C" int sta_solve(sta_ctx *x, const double *val, const double *b, const uint8_t *free,
+                         double tol, int32_t max_iter, double *xv, int32_t *iters,
+                         double *rel_res, void *stream) {
+    if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    Ctx *c = &x->c;
+    if (c->op != STA_OP_ELASTICITY) return fail(STA_ESTATE, "not an elasticity context");
+    if (!(tol >= 0.0) || max_iter < 0) return fail(STA_EINVAL, "tol and max_iter must be >= 0");
+    const int64_t n3 = 3 * c->n;
+    if (n3 > 0 && (!b || !free || !xv)) return fail(STA_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    STA_TRY(cg_alloc(c));
+    const double *A = val ? val : c->val;
+    double *xw = c->cg, *bw = xw + n3, *r = bw + n3, *z = r + n3, *p = z + n3, *q = p + n3;
+    double *dinv = q + n3;
+    CgState *st = reinterpret_cast<CgState *>(c->cg_state);
+    CgState h0 = {};
+    h0.tol2 = tol * tol;
+    h0.max_iter = max_iter;
+    STA_CUDA_TRY(cudaMemcpyAsync(st, &h0, sizeof h0, cudaMemcpyHostToDevice, s));
+    CgState hs = {};
+    if (n3 > 0) {
+        const unsigned gv = (unsigned)c->cg_grid;
+        k_cg_init_static<<<gv, DYN_TPB, 0, s>>>(n3, c->adj_ptr, c->adj, c->row_ptr, A, free, b, xv,
+                                                xw, bw, dinv, c->cg_free);
+        k_cg_spmv<<<gv, DYN_TPB, 0, s>>>(c->n, c->dyn_perm, c->row_ptr, c->col, A, c->cg_zero, 1.0,
+                                        c->cg_free, xw, q, c->cg_part, st, false);
+        k_cg_r0<<<gv, DYN_TPB, 0, s>>>(n3, bw, q, dinv, r, z, p, c->cg_part, st);
+        STA_CUDA_TRY(cudaGetLastError());
+        STA_TRY(cg_iterate(c, nullptr, A, c->cg_zero, 1.0, max_iter, true, s, &hs));
+        STA_CUDA_TRY(cudaMemcpyAsync(xv, xw, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s));
+        STA_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    if (iters) *iters = hs.iters;
+    if (rel_res) *rel_res = hs.bb > 0.0 ? std::sqrt(hs.rr / hs.bb) : 0.0;
+    return STA_OK;
+}
+
+extern "C" int sta_outer_grad(sta_ctx *x, const double *lam, const double *u,
+                              const uint8_t *free, double *grad_val, void *stream) {
+    if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    Ctx *c = &x->c;
+    if (c->nrows > 0 && (!lam || !u || !free || !grad_val)) return fail(STA_EINVAL, "NULL argument");
+    if (c->nrows == 0) return STA_OK;
+    const unsigned g = dyn_grid(c, c->nrows, 8);
+    k_outer_grad<<<g, DYN_TPB, 0, (cudaStream_t)stream>>>(c->nrows, c->row_ptr, c->col, lam, u,
+                                                          free, grad_val);
     STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;
 }

@@ -213,6 +213,7 @@ struct Ctx {
     double *cg_part = nullptr;  // 3 x cg_grid: per-CTA partial sums
     unsigned char *cg_state = nullptr;  // the solve's device scalars
     int32_t *dyn_perm = nullptr;  // n: the CG SpMV's node order (ascending row length)
+    double *cg_zero = nullptr;    // n zeros: the mass term of a static solve (sta_solve)
     int cg_grid = 0;
     cudaGraphExec_t g_cg = nullptr;     // one captured chunk of CG iterations
 

@@ -130,3 +130,37 @@ def test_chain_vs_central_differences(chain):
         fd = (Lp - Lm) / (2 * h)
         an = float(np.sum(chain["g"][name] * d))
         assert abs(an - fd) <= 1e-6 * abs(fd), (name, an, fd)
+
+
+def test_solve_and_outer_grad_vs_oracle(sta, orc):
+    """sta_solve (the CG consumer) against the oracle's sparse direct solve on the free DOFs;
+    sta_outer_grad against the adjoint rule written out in numpy."""
+    import torch
+    wl = W.adjoint_block(N=8)
+    mask = wl.masks()[6]
+    free_np = W.free_dofs(wl.tets, mask, wl.meta["clamped_nodes"])
+    P = orc.Pattern(wl.n_nodes, wl.tets)
+    Ke, _ = orc.element_all(wl.X, wl.tets, wl.E, wl.nu)
+    K = P.csr(P.rebuild(Ke, mask))
+    asm = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu)
+    asm.full_rebuild(mask)
+    f = torch.as_tensor(wl.meta["load"], device="cuda")
+    free = torch.as_tensor(free_np, device="cuda")
+    x, it, rel = sta.sta_solve(asm.h, f, free, tol=1e-12)
+    ref = orc.solve_free(K, wl.meta["load"], free_np)
+    xn = x.cpu().numpy()
+    assert rel <= 1e-12 and it > 0
+    assert np.linalg.norm(xn - ref) <= 1e-8 * np.linalg.norm(ref)
+    assert np.all(xn[~free_np] == 0.0)
+    # the same solve from a warm start takes fewer iterations; a zero right-hand side is 0
+    _, it2, _ = sta.sta_solve(asm.h, f, free, tol=1e-12, x0=x)
+    assert it2 < it
+    z, it0, rel0 = sta.sta_solve(asm.h, torch.zeros_like(f), free)
+    assert it0 == 0 and rel0 == 0.0 and not z.any()
+    lam = torch.as_tensor(np.random.default_rng(2).standard_normal(3 * wl.n_nodes), device="cuda")
+    g = sta.sta_outer_grad(asm.h, lam, x, free).cpu().numpy()
+    rows = np.repeat(np.arange(P.nrows), np.diff(P.row_ptr))
+    both = free_np[rows] & free_np[P.col]
+    want = np.where(both, -lam.cpu().numpy()[rows] * xn[P.col], 0.0)
+    assert np.array_equal(g, want)
+    asm.close()
