@@ -314,9 +314,12 @@ int sta_set_policy(sta_ctx *ctx, int32_t policy, void *stream);
  *    between 0 and > 0), sta_last_touched (entries the last frame visited: both entries of
  *    each edge and the diagonal entry of each node of the edited tetrahedra), sta_graph_*,
  *    sta_mask, sta_sizes, sta_spmv, sta_destroy.  The streamed state equals a rebuild on the
- *    same mask bit for bit.  Calls of the elasticity operator (sta_set_params,
- *    sta_recompute_elements, sta_element_matrices, sta_scatter_map, sta_adjoint,
- *    sta_set_policy) return STA_ESTATE.
+ *    same mask bit for bit.  sta_set_policy chooses the update: STA_POLICY_FIXED (the
+ *    default for the proxy: the maintained multiplicities updated by +-1, Sec. 3.2) or
+ *    STA_POLICY_REFOLD (the paper's local_recompute: each touched edge recounted over the
+ *    tetrahedra incident to it, each touched node's degree over its row); same values and
+ *    state.  Calls of the elasticity operator (sta_set_params, sta_recompute_elements,
+ *    sta_element_matrices, sta_scatter_map, sta_adjoint) return STA_ESTATE.
  * Create: tets (n_tets x 4 int32, host) as for sta_create; every tetrahedron starts inactive
  * (A = eps I on the nodes of the mesh).  Limits: n_tets < 2^27, nnz < 2^31.
  */

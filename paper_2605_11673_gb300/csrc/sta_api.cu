@@ -192,6 +192,7 @@ extern "C" int sta_proxy_create(int64_t n_nodes, const int32_t *tets, int64_t n_
     sta_ctx *x = new sta_ctx();
     Ctx *c = &x->c;
     c->op = STA_OP_PROXY;
+    c->policy = STA_POLICY_FIXED;  // the maintained-count update; REFOLD recounts touched entries
     c->n = n_nodes;
     c->T = n_tets;
     c->eps = eps;
@@ -460,12 +461,15 @@ int sta_recompute_elements(sta_ctx *x, int active_only, void *stream) {
 
 int sta_set_policy(sta_ctx *x, int32_t policy, void *stream) {
     if (!x) return fail(STA_EINVAL, "ctx is NULL");
-    if (x->c.op != STA_OP_ELASTICITY) return fail(STA_ESTATE, "not an elasticity context");
     if (policy != STA_POLICY_REFOLD && policy != STA_POLICY_FIXED)
         return fail(STA_EINVAL, "policy must be STA_POLICY_REFOLD or STA_POLICY_FIXED");
     Ctx *c = &x->c;
     if (c->graph_on) return fail(STA_ESTATE, "disable graph mode before changing the policy");
     cudaStream_t s = (cudaStream_t)stream;
+    if (c->op == STA_OP_PROXY) {  // integer state either way: nothing to prepare
+        c->policy = policy;
+        return launch_values(c, s);
+    }
     if (policy == STA_POLICY_FIXED) STA_TRY(launch_fx_prepare(c, s));
     c->policy = policy;
     return launch_rebuild(c, s);  // every value under the new policy, from the current mask

@@ -497,6 +497,12 @@ int build_pattern(Ctx *c, cudaStream_t s) {
         k_adj_fill<<<grid_for(n + 1), TPB, 0, s>>>(n, nt_ptr, scratch, adj_ptr64, c->adj_ptr,
                                                    c->adj, c->block_node);
         k_tet_maps<<<grid_for(T), TPB, 0, s>>>(c->tets, T, c->adj_ptr, c->adj, tblk, nullptr);
+        // node -> incident tetrahedra, kept for the local-recompute policy
+        STA_TRY(dev_alloc(c, &c->nt_ptr, n + 1));
+        STA_TRY(dev_alloc(c, &c->nt_list, 4 * T));
+        k_to_i32<<<grid_for(n + 1), TPB, 0, s>>>(nt_ptr, n + 1, c->nt_ptr);
+        STA_CUDA_TRY(cudaMemcpyAsync(c->nt_list, nt_list, sizeof(int32_t) * 4 * T,
+                                     cudaMemcpyDeviceToDevice, s));
         STA_TRY(build_proxy_maps(c, tblk, s));
         STA_CUDA_TRY(cudaGetLastError());
         STA_CUDA_TRY(cudaStreamSynchronize(s));  // the scratch is freed on return

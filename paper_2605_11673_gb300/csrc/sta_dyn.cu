@@ -364,6 +364,69 @@ __global__ void k_cg_init_static(int64_t n3, const int32_t *__restrict__ adj_ptr
     }
 }
 
+// Static solve of the scalar proxy operator (one row per node): b, x0 and the inverse diagonal.
+__global__ void k_cg_init_scalar(int64_t n, const int32_t *__restrict__ pdiag,
+                                 const double *__restrict__ val, const uint8_t *__restrict__ free_in,
+                                 const double *__restrict__ b_in, const double *__restrict__ x_in,
+                                 double *__restrict__ x, double *__restrict__ b,
+                                 double *__restrict__ dinv, uint8_t *__restrict__ fr) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = pdiag[i];
+        const double kii = free_in[i] && g >= 0 ? val[g] : 0.0;
+        const bool free = kii != 0.0;
+        fr[i] = free ? 1 : 0;
+        x[i] = free ? x_in[i] : 0.0;
+        b[i] = free ? b_in[i] : 0.0;
+        dinv[i] = free ? 1.0 / kii : 0.0;
+    }
+}
+
+// q = A x on the free rows of a scalar operator, four lanes per row (rows in the order `perm`,
+// ascending length), each row's lanes adding their partial sums as (s0 + s1) + (s2 + s3).
+// With `dots`, the last CTA forms p.q and alpha = rz / pq.
+__global__ void __launch_bounds__(DYN_TPB)
+k_cg_spmv_scalar(int64_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ row_ptr,
+                 const int32_t *__restrict__ col, const double *__restrict__ val,
+                 const uint8_t *__restrict__ fr, const double *__restrict__ xin,
+                 double *__restrict__ qout, double *__restrict__ part, CgState *st, bool dots) {
+    __shared__ double sh[DYN_WARPS];
+    if (dots && cg_stopped(st)) return;
+    const int lane = threadIdx.x & 31, qd = lane & 3;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double pq = 0.0;
+    for (int64_t base = 8 * warp; base < n; base += 8 * nwarps) {  // warp-uniform
+        const int64_t j = base + (lane >> 2);
+        double acc = 0.0;
+        int64_t a = -1;
+        if (j < n) {
+            a = perm[j];
+            const int32_t r0 = row_ptr[a], r1 = row_ptr[a + 1];
+            for (int32_t k = r0 + qd; k < r1; k += 4) acc = __fma_rn(val[k], xin[col[k]], acc);
+        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (a >= 0 && qd == 0) {
+            const double q = fr[a] ? acc : 0.0;
+            qout[a] = q;
+            pq = __fma_rn(xin[a], q, pq);
+        }
+    }
+    if (!dots) return;
+    const double t = cta_sum(pq, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+    if (last_cta(&st->arrive[0])) {
+        const double s = sum_parts(part, gridDim.x, sh);
+        if (threadIdx.x == 0) {
+            st->pq = s;
+            if (s > 0.0) st->alpha = st->rz / s;
+            else st->done = 1;
+            st->arrive[0] = 0u;
+        }
+    }
+}
+
 // The adjoint rule of a solve (A_ff u_f = f_f): dL/dA_ij = -lam_i u_j on entries between free
 // DOFs, 0 elsewhere.  One thread per row.
 __global__ void k_outer_grad(int64_t nrows, const int32_t *__restrict__ row_ptr,
@@ -450,14 +513,18 @@ namespace {
 // One chunk of CG_CHUNK iterations (3 launches each) of A = diag(mass) + h2 K(val), launched
 // or captured on s.
 int cg_chunk(Ctx *c, const double *val, const double *mass, double h2, cudaStream_t s) {
-    const int64_t n3 = 3 * c->n;
+    const int64_t n3 = c->nrows;  // DOFs: 3 per node, or 1 for the scalar proxy operator
     const unsigned gv = c->cg_grid;
     double *x = c->cg, *b = x + n3, *r = b + n3, *z = r + n3, *p = z + n3, *q = p + n3;
     double *dinv = q + n3;
     CgState *st = reinterpret_cast<CgState *>(c->cg_state);
     for (int it = 0; it < CG_CHUNK; ++it) {
-        k_cg_spmv<<<gv, DYN_TPB, 0, s>>>(c->n, c->dyn_perm, c->row_ptr, c->col, val, mass, h2,
-                                        c->cg_free, p, q, c->cg_part, st, true);
+        if (c->op == STA_OP_PROXY)
+            k_cg_spmv_scalar<<<gv, DYN_TPB, 0, s>>>(c->n, c->dyn_perm, c->row_ptr, c->col, val,
+                                                    c->cg_free, p, q, c->cg_part, st, true);
+        else
+            k_cg_spmv<<<gv, DYN_TPB, 0, s>>>(c->n, c->dyn_perm, c->row_ptr, c->col, val, mass, h2,
+                                            c->cg_free, p, q, c->cg_part, st, true);
         k_cg_update<<<gv, DYN_TPB, 0, s>>>(n3, x, r, z, p, q, dinv, c->cg_part, st);
         k_cg_pupdate<<<gv, DYN_TPB, 0, s>>>(n3, p, z, st);
     }
@@ -503,7 +570,8 @@ int cg_iterate(Ctx *c, cudaGraphExec_t g, const double *val, const double *mass,
 // The CG buffers shared by the implicit-Euler step and the static solve, allocated once.
 int cg_alloc(Ctx *c) {
     if (c->cg) return STA_OK;
-    const int64_t n = c->n, n3 = 3 * n;
+    const int64_t n = c->n, n3 = c->nrows;  // DOFs
+    const int rows = c->op == STA_OP_PROXY ? 1 : 3;  // rows per node
     c->cg_grid = (int)dyn_grid(c, n3 > 0 ? n3 : 1);
     STA_TRY(dev_alloc(c, &c->cg, 7 * n3));
     STA_TRY(dev_alloc(c, &c->cg_free, n3));
@@ -513,12 +581,12 @@ int cg_alloc(Ctx *c) {
     STA_CUDA_TRY(cudaMemset(c->cg_zero, 0, sizeof(double) * (size_t)(n > 0 ? n : 1)));
     // the SpMV's node order: ascending row length (ties by node id)
     STA_TRY(dev_alloc(c, &c->dyn_perm, n));
-    std::vector<int32_t> rp(3 * n + 1), perm(n);
-    STA_CUDA_TRY(cudaMemcpy(rp.data(), c->row_ptr, sizeof(int32_t) * (3 * n + 1),
+    std::vector<int32_t> rp(rows * n + 1), perm(n);
+    STA_CUDA_TRY(cudaMemcpy(rp.data(), c->row_ptr, sizeof(int32_t) * (rows * n + 1),
                             cudaMemcpyDeviceToHost));
     for (int64_t a = 0; a < n; ++a) perm[a] = (int32_t)a;
     std::stable_sort(perm.begin(), perm.end(), [&](int32_t p, int32_t q) {
-        return rp[3 * p + 3] - rp[3 * p] < rp[3 * q + 3] - rp[3 * q];
+        return rp[rows * p + rows] - rp[rows * p] < rp[rows * q + rows] - rp[rows * q];
     });
     STA_CUDA_TRY(cudaMemcpy(c->dyn_perm, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
     return STA_OK;
@@ -649,9 +717,8 @@ extern "C" int sta_solve(sta_ctx *x, const double *val, const double *b, const u
                          double *rel_res, void *stream) {
     if (!x) return fail(STA_EINVAL, "ctx is NULL");
     Ctx *c = &x->c;
-    if (c->op != STA_OP_ELASTICITY) return fail(STA_ESTATE, "not an elasticity context");
     if (!(tol >= 0.0) || max_iter < 0) return fail(STA_EINVAL, "tol and max_iter must be >= 0");
-    const int64_t n3 = 3 * c->n;
+    const int64_t n3 = c->nrows;  // DOFs: 3 per node, or 1 for the proxy operator
     if (n3 > 0 && (!b || !free || !xv)) return fail(STA_EINVAL, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
     STA_TRY(cg_alloc(c));
@@ -666,10 +733,17 @@ extern "C" int sta_solve(sta_ctx *x, const double *val, const double *b, const u
     CgState hs = {};
     if (n3 > 0) {
         const unsigned gv = (unsigned)c->cg_grid;
-        k_cg_init_static<<<gv, DYN_TPB, 0, s>>>(n3, c->adj_ptr, c->adj, c->row_ptr, A, free, b, xv,
-                                                xw, bw, dinv, c->cg_free);
-        k_cg_spmv<<<gv, DYN_TPB, 0, s>>>(c->n, c->dyn_perm, c->row_ptr, c->col, A, c->cg_zero, 1.0,
-                                        c->cg_free, xw, q, c->cg_part, st, false);
+        if (c->op == STA_OP_PROXY) {
+            k_cg_init_scalar<<<gv, DYN_TPB, 0, s>>>(n3, c->pdiag, A, free, b, xv, xw, bw, dinv,
+                                                    c->cg_free);
+            k_cg_spmv_scalar<<<gv, DYN_TPB, 0, s>>>(c->n, c->dyn_perm, c->row_ptr, c->col, A,
+                                                    c->cg_free, xw, q, c->cg_part, st, false);
+        } else {
+            k_cg_init_static<<<gv, DYN_TPB, 0, s>>>(n3, c->adj_ptr, c->adj, c->row_ptr, A, free, b,
+                                                    xv, xw, bw, dinv, c->cg_free);
+            k_cg_spmv<<<gv, DYN_TPB, 0, s>>>(c->n, c->dyn_perm, c->row_ptr, c->col, A, c->cg_zero,
+                                            1.0, c->cg_free, xw, q, c->cg_part, st, false);
+        }
         k_cg_r0<<<gv, DYN_TPB, 0, s>>>(n3, bw, q, dinv, r, z, p, c->cg_part, st);
         STA_CUDA_TRY(cudaGetLastError());
         STA_TRY(cg_iterate(c, nullptr, A, c->cg_zero, 1.0, max_iter, true, s, &hs));

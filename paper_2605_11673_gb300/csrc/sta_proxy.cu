@@ -14,6 +14,9 @@
 // touched entries from the final counts.  The atomics on one counter are totally ordered, so
 // the transitions they report sum to the net change of the edge's activity whatever the
 // order: the streamed state is bit-identical to the rebuild's.
+// Under STA_POLICY_REFOLD a frame instead recounts each touched edge over the tetrahedra
+// incident to it and each touched node's degree over its row (the paper's local_recompute,
+// O(|Delta| kappa)); same values and state.
 #include "sta_internal.cuh"
 
 namespace sta {
@@ -135,7 +138,7 @@ __global__ void k_proxy_claim(const int32_t *__restrict__ edited, int64_t m,
                               const int32_t *__restrict__ ptblk, int32_t *__restrict__ mult,
                               int32_t *__restrict__ deg, uint32_t *__restrict__ flag,
                               uint8_t *__restrict__ mask, int32_t *__restrict__ list,
-                              unsigned long long *__restrict__ counters) {
+                              unsigned long long *__restrict__ counters, bool count) {
     const int64_t items = 10 * (m_dev ? *m_dev : m);
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -152,7 +155,7 @@ __global__ void k_proxy_claim(const int32_t *__restrict__ edited, int64_t m,
             const bool on = (e >> 31) != 0u;
             g = ptblk[10 * t + s];
             edge = s >= 4;
-            if (edge) {
+            if (edge && count) {
                 const int step = on ? 1 : -1;
                 const int32_t before = atomicAdd(&mult[g], step);
                 if ((before == 0) != (before + step == 0)) {  // 0 <-> > 0
@@ -184,14 +187,23 @@ __global__ void k_proxy_write(const int32_t *__restrict__ list,
                               const unsigned long long *__restrict__ count,
                               const int32_t *__restrict__ block_node, const int32_t *__restrict__ adj,
                               const int32_t *__restrict__ pmir, const int32_t *__restrict__ mult,
-                              const int32_t *__restrict__ deg, double eps,
-                              uint32_t *__restrict__ flag, double *__restrict__ val) {
+                              int32_t *__restrict__ deg, double eps,
+                              uint32_t *__restrict__ flag, double *__restrict__ val,
+                              const int32_t *__restrict__ adj_ptr, const int32_t *__restrict__ pup) {
     const int64_t cnt = (int64_t)*count;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t g = list[i];
         const int32_t a = block_node[g];
         if (adj[g] == a) {
+            if (adj_ptr) {  // local recompute: the degree from the row's (final) multiplicities
+                int32_t d = 0;
+                for (int32_t b = adj_ptr[a]; b < adj_ptr[a + 1]; ++b) {
+                    const int32_t up = pup[b];
+                    d += up >= 0 && mult[up] > 0;
+                }
+                deg[a] = d;
+            }
             val[g] = (double)deg[a] + eps;
         } else {
             const double v = mult[g] > 0 ? -1.0 : 0.0;
@@ -199,6 +211,32 @@ __global__ void k_proxy_write(const int32_t *__restrict__ list,
             val[pmir[g]] = v;
         }
         flag[g] = 0u;
+    }
+}
+
+// Local recompute (STA_POLICY_REFOLD, the paper's local_recompute for the proxy): each claimed
+// edge's multiplicity counted from scratch over the active tetrahedra incident to its lower
+// node that also hold its upper node (O(|Delta| kappa)); diagonals are left to k_proxy_write.
+__global__ void k_proxy_recount(const int32_t *__restrict__ list,
+                                const unsigned long long *__restrict__ count,
+                                const int32_t *__restrict__ block_node,
+                                const int32_t *__restrict__ adj, const int32_t *__restrict__ nt_ptr,
+                                const int32_t *__restrict__ nt_list, const int4 *__restrict__ tets,
+                                const uint8_t *__restrict__ mask, int32_t *__restrict__ mult) {
+    const int64_t cnt = (int64_t)*count;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = list[i];
+        const int32_t u = block_node[g], v = adj[g];
+        if (u == v) continue;
+        int32_t c = 0;
+        for (int32_t e = nt_ptr[u]; e < nt_ptr[u + 1]; ++e) {
+            const int32_t t = nt_list[e];
+            if (!mask[t]) continue;
+            const int4 q = tets[t];
+            c += q.x == v || q.y == v || q.z == v || q.w == v;
+        }
+        mult[g] = c;
     }
 }
 
@@ -250,13 +288,19 @@ int launch_proxy_frame(Ctx *c, const int32_t *edited, int64_t m, const int64_t *
                        int64_t cap, int32_t *list, unsigned long long *counters, cudaStream_t s) {
     const int64_t items = 10 * (cap > 0 ? cap : 1);
     int32_t *deg = c->pmult + c->nblocks;
+    const bool rescan = c->policy == STA_POLICY_REFOLD;  // local recompute instead of +-1
     k_proxy_claim<<<px_grid(c, items, 16), PX_TPB, 0, s>>>(edited, m, m_dev, c->tets, c->ptblk,
                                                            c->pmult, deg, c->pflag, c->mask, list,
-                                                           counters);
+                                                           counters, !rescan);
     const int64_t most = items < c->nblocks ? items : c->nblocks;
+    if (rescan)
+        k_proxy_recount<<<px_grid(c, most, 16), PX_TPB, 0, s>>>(list, counters + 1, c->block_node,
+                                                                c->adj, c->nt_ptr, c->nt_list,
+                                                                c->tets, c->mask, c->pmult);
     k_proxy_write<<<px_grid(c, most, 16), PX_TPB, 0, s>>>(list, counters + 1, c->block_node,
                                                           c->adj, c->pmir, c->pmult, deg, c->eps,
-                                                          c->pflag, c->val);
+                                                          c->pflag, c->val,
+                                                          rescan ? c->adj_ptr : nullptr, c->pup);
     STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;
 }

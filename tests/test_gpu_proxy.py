@@ -54,9 +54,11 @@ class _Ref:
         assert np.array_equal(gd, deg), f"{what}: degrees"
 
 
-def _run(sta, orc, wl, eps=0.0, graph=False, noalloc=False, frames=None):
+def _run(sta, orc, wl, eps=0.0, graph=False, noalloc=False, frames=None, policy=None):
     R = _Ref(orc, wl, eps)
     px = sta.ProxyAssembler(wl.n_nodes, wl.tets, eps=eps)
+    if policy is not None:  # REFOLD: local recompute of the touched entries
+        px.set_policy(policy)
     rp, col, _ = px.csr()
     assert px.nnz == R.col.size
     assert np.array_equal(rp.cpu().numpy(), R.ptr)
@@ -93,6 +95,15 @@ def test_proxy_small_workloads(sta, orc):
     _run(sta, orc, W.prefractured_block(N=10, sites=8, frames=8), eps=0.5)
     _run(sta, orc, W.refinement_hierarchy(N=6, radius=0.3, frames=8))
     _run(sta, orc, W.edge_fan(seed=3, K=300))
+
+
+def test_proxy_local_recompute_policy(sta, orc):
+    for wl, eps in ((W.plain_small(seed=21), 0.0), (W.prefractured_block(N=10, sites=8, frames=8), 0.5),
+                    (W.refinement_hierarchy(N=6, radius=0.3, frames=8), 1e-3),
+                    (W.edge_fan(seed=5, K=300), 0.0)):
+        _run(sta, orc, wl, eps=eps, policy=sta.STA_POLICY_REFOLD)
+    _run(sta, orc, W.plain_small(seed=22), graph=True, policy=sta.STA_POLICY_REFOLD)
+    _run(sta, orc, W.plain_small(seed=23), noalloc=True, policy=sta.STA_POLICY_REFOLD)
 
 
 def test_proxy_graph_mode_and_noalloc(sta, orc):
@@ -143,8 +154,7 @@ def test_proxy_spmv_and_rejections(sta, orc):
     x = np.random.default_rng(0).standard_normal(wl.n_nodes)
     y = sta.sta_spmv(px.h, torch.as_tensor(x, device="cuda"))
     assert np.allclose(y.cpu().numpy(), A @ x, rtol=1e-14, atol=1e-14)
-    for call in (lambda: px.set_policy(sta.STA_POLICY_FIXED),
-                 lambda: px.set_params(E=wl.E),
+    for call in (lambda: px.set_params(E=wl.E),
                  lambda: px.element_matrices(np.array([0], np.int32)),
                  lambda: px.scatter_map(),
                  lambda: px.recompute_elements()):
@@ -157,3 +167,32 @@ def test_proxy_spmv_and_rejections(sta, orc):
         sta.sta_proxy_state(asm.h)
     assert ei.value.status == sta.STA_ESTATE
     asm.close()
+
+
+def test_proxy_solve_vs_direct(sta, orc):
+    """sta_solve on the proxy system A = L + eps I (the paper's per-frame solve, Algorithm 1)
+    against scipy's sparse direct solve, on the mesh's nodes."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    import torch
+    wl = W.prefractured_block(N=10, sites=8, frames=4)
+    eps = 1e-2
+    px = sta.ProxyAssembler(wl.n_nodes, wl.tets, eps=eps)
+    mask = wl.masks()[3]
+    px.full_rebuild(mask)
+    P = orc.Pattern(wl.n_nodes, wl.tets)
+    ptr, col = P.proxy_pattern()
+    _, _, val = P.proxy_rebuild(mask, eps)
+    A = sp.csr_matrix((val, col, ptr), shape=(wl.n_nodes, wl.n_nodes))
+    free = np.diff(ptr) > 0
+    b = np.random.default_rng(4).standard_normal(wl.n_nodes)
+    idx = np.flatnonzero(free)
+    ref = np.zeros(wl.n_nodes)
+    ref[idx] = spla.spsolve(A[idx][:, idx].tocsc(), b[idx])
+    x, it, rel = sta.sta_solve(px.h, torch.as_tensor(b, device="cuda"),
+                               torch.as_tensor(free, device="cuda"), tol=1e-12)
+    xn = x.cpu().numpy()
+    assert rel <= 1e-12 and it > 0
+    assert np.linalg.norm(xn - ref) <= 1e-9 * np.linalg.norm(ref)
+    assert np.all(xn[~free] == 0.0)
+    px.close()
