@@ -675,3 +675,17 @@ def test_implicit_euler_step_closed_forms(orc):
     want = np.linalg.solve(A, m1[3] * (u0[9:12] + 0.05 * v0[9:12]) + 0.05 ** 2 * f1[9:12])
     assert np.allclose(got[9:12], want, rtol=1e-12)
     assert np.all(got[:9] == 0.0) and np.array_equal(got[12:], u0[12:])   # node 4: no mass
+
+
+def test_slab_sequence_workloads_are_valid(orc):
+    """Fracture deletes disjoint slabs one per frame; merge starts from all of them deleted
+    and reinserts them; every frame is a valid edit list."""
+    for merge in (False, True):
+        wl = W.slab_sequence(N=8, half_width=0.02, frames=4, merge=merge)
+        masks = wl.masks()
+        for f, ed in enumerate(wl.frames):
+            assert orc.validate_edits(wl.n_tets, masks[f], ed) == 0
+            assert ed.shape[0] > 0 and np.all(ed[:, 0] == (1 if merge else 0))
+        ids = np.concatenate([ed[:, 1] for ed in wl.frames])
+        assert np.unique(ids).size == ids.size               # the slabs are disjoint
+        assert np.all(masks[-1] == (1 if merge else np.isin(np.arange(wl.n_tets), ids, invert=True)))

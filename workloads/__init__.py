@@ -328,6 +328,33 @@ def slab_cycles(seed: int = 0, N: int = 12, half_width: float = 0.04, frames: in
                      "grid_index": gi})
 
 
+def slab_sequence(seed: int = 0, N: int = 20, half_width: float = 0.01, frames: int = 8,
+                  merge: bool = False) -> Workload:
+    """Fracture and merge scenarios of the paper's multi-model comparison (Sec. 5.1, Table 2):
+    the unit cube, N^3 hexes x 6 (N = 20: 48,000 tets; 26: 105,456; 43: 477,042), jitter
+    +-0.15h, E lognormal, nu = 0.3.  A seeded unit normal and `frames` parallel slabs of
+    half-width `half_width` (centroid distance to the plane), spaced 4 half-widths apart around
+    the cube's centre.  Fracture: all tets active at start, frame f deletes slab f.  Merge:
+    every slab deleted at start, frame f reinserts slab f."""
+    rng = rng_for(8, seed)
+    X, tets, gi = kuhn_cube(N, 0.15, rng)
+    T = tets.shape[0]
+    nrm = rng.standard_normal(3)
+    nrm /= np.linalg.norm(nrm)
+    d = (X[tets].mean(axis=1) - 0.5) @ nrm
+    offs = (np.arange(frames) - (frames - 1) / 2.0) * 4.0 * half_width
+    slabs = [np.flatnonzero(np.abs(d - o) <= half_width) for o in offs]
+    mask0 = np.ones(T, np.uint8)
+    if merge:
+        for sl in slabs:
+            mask0[sl] = 0
+    fr = [make_edits(on=sl) if merge else make_edits(off=sl) for sl in slabs]
+    return Workload(f"slab_{'merge' if merge else 'fracture'}_N{N}", X, tets, lognormal_E(rng, T),
+                    np.full(T, 0.3), mask0, fr,
+                    {"N": N, "half_width": half_width, "slab_tets": [int(x.size) for x in slabs],
+                     "grid_index": gi})
+
+
 def refinement_hierarchy(seed: int = 0, N: int = 30, radius: float = 0.15, frames: int = 24
                          ) -> Workload:
     """Refinement hierarchy: N^3 hexes x 6 coarse tets (no jitter), each with its 8
