@@ -24,6 +24,22 @@ int fail(int code, const std::string &msg) {
 using namespace sta;
 
 
+// The host mirror of a new mask (and its 0/1 staging copy); returns the active count.  Plain
+// byte loops over restrict pointers, which the compiler vectorises.
+static int64_t set_host_mask(Ctx *c, const uint8_t *__restrict__ mask, uint8_t *__restrict__ stage) {
+    uint8_t *__restrict__ ts = c->tstate.data();
+    const int64_t T = c->T;
+    int64_t na = 0;
+    for (int64_t t = 0; t < T; ++t) {
+        const uint8_t on = mask[t] != 0;
+        ts[t] = (uint8_t)((ts[t] & TS_STAMP) | (on << 7));
+        na += on;
+    }
+    if (stage)
+        for (int64_t t = 0; t < T; ++t) stage[t] = mask[t] != 0;
+    return na;
+}
+
 static int wait_staging(sta_ctx *x) {
     if (x->h2d_pending) {
         STA_CUDA_TRY(cudaEventSynchronize(x->h2d_done));
@@ -249,14 +265,10 @@ int sta_full_rebuild(sta_ctx *x, const uint8_t *mask, int mask_on_device, void *
             STA_CUDA_TRY(cudaMemcpyAsync(c->mask, mask, (size_t)c->T, cudaMemcpyDeviceToDevice, s));
             STA_CUDA_TRY(cudaMemcpyAsync(hm.data(), mask, (size_t)c->T, cudaMemcpyDeviceToHost, s));
             STA_CUDA_TRY(cudaStreamSynchronize(s));
-            for (int64_t t = 0; t < c->T; ++t) ts_set_active(c, t, hm[t] != 0);
+            set_host_mask(c, hm.data(), nullptr);
         } else {
             STA_TRY(wait_staging(x));
-            for (int64_t t = 0; t < c->T; ++t) {
-                const bool on = mask[t] != 0;
-                ts_set_active(c, t, on);
-                x->h_mask[t] = on ? 1 : 0;
-            }
+            set_host_mask(c, mask, x->h_mask);
             STA_CUDA_TRY(cudaMemcpyAsync(c->mask, x->h_mask, (size_t)c->T, cudaMemcpyHostToDevice, s));
             STA_CUDA_TRY(cudaEventRecord(x->h2d_done, s));
             x->h2d_pending = true;
@@ -351,9 +363,12 @@ int sta_apply_edits(sta_ctx *x, const sta_edit *edits, int64_t n_edits, void *st
     const char *why = nullptr;
     for (; e < n_edits; ++e) {
         if (e + 16 < n_edits) {  // the per-tet state is accessed at random: fetch it ahead
+            // (a prefetch never faults, so an unchecked id -- tet2 of a non-swap is -1 -- costs
+            // at most a useless prefetch; the address is formed as an integer)
             const sta_edit &F = edits[e + 16];
-            if (F.tet >= 0 && F.tet < c->T) __builtin_prefetch(ts + F.tet, 1);
-            if (F.op == STA_SWAP && F.tet2 >= 0 && F.tet2 < c->T) __builtin_prefetch(ts + F.tet2, 1);
+            const uintptr_t base = (uintptr_t)ts;
+            __builtin_prefetch((const void *)(base + (uintptr_t)(intptr_t)F.tet), 1);
+            __builtin_prefetch((const void *)(base + (uintptr_t)(intptr_t)F.tet2), 1);
         }
         const sta_edit &E = edits[e];
         if (E.op < 0 || E.op > 2) { why = "bad op"; break; }
