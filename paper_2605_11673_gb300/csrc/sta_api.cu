@@ -1,6 +1,7 @@
 // C-ABI entry points of libsta (declared in include/sta.h): argument and edit validation on
 // the host, device memory management, and the launch sequence of each call.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cstdio>
 #include <cstring>
@@ -314,13 +315,15 @@ int sta_apply_edits(sta_ctx *x, const sta_edit *edits, int64_t n_edits, void *st
     // the frame block to stage into: the graph's (fixed) or the context's (grown on demand)
     const bool use_graph = c->graph_on && m <= c->gcap;
     FrameHeader *h = nullptr, *d = nullptr;
-    if (use_graph) {
-        if (c->g_pending) {
-            STA_CUDA_TRY(cudaEventSynchronize(c->g_h2d));
-            c->g_pending = false;
+    int gb = 0;
+    if (use_graph) {  // the staging block last used two frames ago: its kernels are done
+        gb = c->g_next;
+        if (c->g_pending[gb]) {
+            STA_CUDA_TRY(cudaEventSynchronize(c->g_done[gb]));
+            c->g_pending[gb] = false;
         }
-        h = c->h_gframe;
-        d = c->d_gframe;
+        h = c->h_gframe[gb];
+        d = c->m_gframe[gb];
     } else {
         STA_TRY(wait_staging(x));
         if (m > c->edit_cap || !c->h_frame) {
@@ -408,14 +411,17 @@ int sta_apply_edits(sta_ctx *x, const sta_edit *edits, int64_t n_edits, void *st
     h->m = m;
     h->cnt[0] = h->cnt[1] = h->cnt[2] = 0ull;
     c->last_edited = m;
-    c->last_counters = frame_counters(d);
-    STA_CUDA_TRY(cudaMemcpyAsync(d, h, frame_bytes(m), cudaMemcpyHostToDevice, s));
-    if (use_graph) {  // one captured launch sequence for every frame
-        STA_CUDA_TRY(cudaEventRecord(c->g_h2d, s));
-        c->g_pending = true;
-        STA_CUDA_TRY(cudaGraphLaunch(c->g_stream, s));
+    if (use_graph) {  // the captured sequence reads the host-mapped block itself: no copy call
+        c->last_counters = c->d_gcnt + 4 * gb;
+        std::atomic_thread_fence(std::memory_order_seq_cst);  // the block before the launch
+        STA_CUDA_TRY(cudaGraphLaunch(c->g_streams[gb], s));
+        STA_CUDA_TRY(cudaEventRecord(c->g_done[gb], s));
+        c->g_pending[gb] = true;
+        c->g_next = gb ^ 1;
         return STA_OK;
     }
+    c->last_counters = frame_counters(d);
+    STA_CUDA_TRY(cudaMemcpyAsync(d, h, frame_bytes(m), cudaMemcpyHostToDevice, s));
     STA_CUDA_TRY(cudaEventRecord(x->h2d_done, s));
     x->h2d_pending = true;
     if (m == 0) return STA_OK;  // the copy has zeroed the frame's counters

@@ -8,17 +8,22 @@
 namespace sta {
 
 void graph_release(Ctx *c) {
-    if (c->g_stream) cudaGraphExecDestroy(c->g_stream);
+    for (int b = 0; b < 2; ++b) {
+        if (c->g_streams[b]) cudaGraphExecDestroy(c->g_streams[b]);
+        if (c->h_gframe[b]) cudaFreeHost(c->h_gframe[b]);
+        if (c->g_done[b]) cudaEventDestroy(c->g_done[b]);
+        c->g_streams[b] = nullptr;
+        c->h_gframe[b] = c->m_gframe[b] = nullptr;
+        c->g_done[b] = nullptr;
+        c->g_pending[b] = false;
+    }
     if (c->g_refold) cudaGraphExecDestroy(c->g_refold);
     if (c->g_rebuild) cudaGraphExecDestroy(c->g_rebuild);
-    if (c->d_gframe) cudaFree(c->d_gframe);
-    if (c->h_gframe) cudaFreeHost(c->h_gframe);
-    if (c->g_h2d) cudaEventDestroy(c->g_h2d);
-    c->g_stream = c->g_refold = c->g_rebuild = nullptr;
-    c->d_gframe = c->h_gframe = nullptr;
-    c->g_h2d = nullptr;
+    if (c->d_gcnt) cudaFree(c->d_gcnt);
+    c->g_refold = c->g_rebuild = nullptr;
+    c->d_gcnt = nullptr;
     c->graph_on = false;
-    c->g_pending = false;
+    c->g_next = 0;
     c->gcap = 0;
 }
 
@@ -26,7 +31,7 @@ namespace {
 
 // Keep the last frame's touched counts when the graph staging goes away (sta_last_touched).
 int keep_last_counters(Ctx *c) {
-    if (c->d_gframe && c->last_counters == frame_counters(c->d_gframe)) {
+    if (c->d_gcnt && (c->last_counters == c->d_gcnt || c->last_counters == c->d_gcnt + 4)) {
         STA_CUDA_TRY(cudaMemcpy(c->counters + 1, c->last_counters + 1,
                                 3 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice));
         c->last_counters = c->counters;
@@ -71,17 +76,30 @@ extern "C" int sta_graph_enable(sta_ctx *x, int64_t max_edited, void *stream) {
         graph_release(c);
         return code;
     };
-    if (cudaMalloc((void **)&c->d_gframe, frame_bytes(max_edited)) != cudaSuccess ||
-        cudaMallocHost((void **)&c->h_gframe, frame_bytes(max_edited)) != cudaSuccess)
-        return bail(fail(STA_ENOMEM, "graph staging buffers"));
-    if (cudaEventCreateWithFlags(&c->g_h2d, cudaEventDisableTiming) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
-        return bail(fail(STA_ECUDA, "graph stream/event"));
+    if (cudaMalloc((void **)&c->d_gcnt, 8 * sizeof(unsigned long long)) != cudaSuccess)
+        return bail(fail(STA_ENOMEM, "graph counters"));
+    for (int b = 0; b < 2; ++b) {
+        void *dp = nullptr;
+        if (cudaHostAlloc((void **)&c->h_gframe[b], frame_bytes(max_edited), cudaHostAllocMapped) !=
+                cudaSuccess ||
+            cudaHostGetDevicePointer(&dp, c->h_gframe[b], 0) != cudaSuccess)
+            return bail(fail(STA_ENOMEM, "graph staging buffers (host-mapped)"));
+        c->m_gframe[b] = static_cast<FrameHeader *>(dp);
+        if (cudaEventCreateWithFlags(&c->g_done[b], cudaEventDisableTiming) != cudaSuccess)
+            return bail(fail(STA_ECUDA, "graph event"));
+    }
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(STA_ECUDA, "graph stream"));
     c->gcap = max_edited;
-    if ((rc = capture(cs, [&](cudaStream_t s) {
-             return launch_stream_frame(c, c->d_gframe, c->gcap, s);
-         }, &c->g_stream)))
-        return bail(rc);
+    for (int b = 0; b < 2; ++b) {
+        unsigned long long *cnt = c->d_gcnt + 4 * b;
+        FrameHeader *fb = c->m_gframe[b];
+        if ((rc = capture(cs, [&](cudaStream_t s) {
+                 STA_CUDA_TRY(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), s));
+                 return launch_stream_frame(c, frame_edited(fb), &fb->m, cnt, c->gcap, s);
+             }, &c->g_streams[b])))
+            return bail(rc);
+    }
     if ((rc = capture(cs, [&](cudaStream_t s) { return launch_values(c, s); }, &c->g_refold)))
         return bail(rc);
     if ((rc = capture(cs, [&](cudaStream_t s) {

@@ -219,11 +219,19 @@ struct Ctx {
 
     // CUDA-graph mode (sta_graph_enable): captured frame sequences and fixed staging
     bool graph_on = false;
-    cudaGraphExec_t g_stream = nullptr, g_refold = nullptr, g_rebuild = nullptr;
+    cudaGraphExec_t g_refold = nullptr, g_rebuild = nullptr;
+    // graph mode stages frames in two host-mapped pinned blocks that the captured kernels read
+    // directly (no copy call per frame), used alternately; each has its own captured sequence,
+    // its own device counters (zeroed by a memset node of that sequence) and an event recorded
+    // after its launch, waited on before the block is written again
     int64_t gcap = 0;
-    FrameHeader *d_gframe = nullptr, *h_gframe = nullptr;  // device / pinned, gcap entries
-    cudaEvent_t g_h2d = nullptr;
-    bool g_pending = false;
+    cudaGraphExec_t g_streams[2] = {nullptr, nullptr};
+    FrameHeader *h_gframe[2] = {nullptr, nullptr};  // host-mapped pinned, gcap entries each
+    FrameHeader *m_gframe[2] = {nullptr, nullptr};  // their device addresses
+    unsigned long long *d_gcnt = nullptr;           // 2 x 4 counters
+    cudaEvent_t g_done[2] = {nullptr, nullptr};
+    bool g_pending[2] = {false, false};
+    int g_next = 0;
 
     // batched form (sta_batch_create): instance offsets and per-instance CSR index arrays
     int32_t n_inst = 0;
@@ -275,6 +283,10 @@ int launch_adjoint(Ctx *c, const double *gval, double *dE, double *dnu, double *
 int launch_spmv(Ctx *c, const double *val, const double *x, double *y, cudaStream_t s);
 int launch_rebuild(Ctx *c, cudaStream_t s);                      // sta_assemble.cu
 int launch_stream_frame(Ctx *c, FrameHeader *frame, int64_t cap, cudaStream_t s);  // sta_stream.cu
+// the same with the edited list, its count and the counters at separate addresses (the graph
+// mode's host-mapped frames keep their counters in device memory)
+int launch_stream_frame(Ctx *c, const int32_t *edited, const int64_t *m_dev,
+                        unsigned long long *cnt, int64_t cap, cudaStream_t s);
 int launch_fx_prepare(Ctx *c, cudaStream_t s);                   // sta_fixed.cu
 int launch_fx_frame(Ctx *c, const int32_t *edited, int64_t m, const int64_t *m_dev, int64_t cap,
                     int32_t *touched, unsigned long long *counters, cudaStream_t s);

@@ -219,26 +219,27 @@ int launch_values(Ctx *c, cudaStream_t s) {
 // frame block (FrameHeader + edited list) already holding the frame; the count is read from
 // it, grids are sized for `cap` edited tetrahedra (so the sequence can be captured once and
 // replayed for any frame up to `cap`).
-int launch_stream_frame(Ctx *c, FrameHeader *frame, int64_t cap, cudaStream_t s) {
+int launch_stream_frame(Ctx *c, const int32_t *edited, const int64_t *m_dev,
+                        unsigned long long *cnt, int64_t cap, cudaStream_t s) {
     if (c->op == STA_OP_PROXY)
-        return launch_proxy_frame(c, frame_edited(frame), 0, &frame->m, cap, c->plist,
-                                  frame_counters(frame), s);
+        return launch_proxy_frame(c, edited, 0, m_dev, cap, c->plist, cnt, s);
     if (c->policy == STA_POLICY_FIXED) {
-        STA_TRY(launch_fx_frame(c, frame_edited(frame), 0, &frame->m, cap, c->touched,
-                                frame_counters(frame), s));
-        return launch_dyn_mass_edited(c, frame_edited(frame), 0, &frame->m, cap, s);
+        STA_TRY(launch_fx_frame(c, edited, 0, m_dev, cap, c->touched, cnt, s));
+        return launch_dyn_mass_edited(c, edited, 0, m_dev, cap, s);
     }
     const int threads = 256;
     int64_t g = (10 * cap + threads - 1) / threads;
     const int64_t gmax = (int64_t)c->num_sms * 16;
     g = g < 1 ? 1 : (g > gmax ? gmax : g);
-    unsigned long long *cnt = frame_counters(frame);
-    k_stream_claim<<<(unsigned)g, threads, 0, s>>>(frame_edited(frame), 0, &frame->m, c->T, c->tunit,
-                                                   c->cslot, c->ccode, c->mask, c->owner,
-                                                   c->touched, cnt);
+    k_stream_claim<<<(unsigned)g, threads, 0, s>>>(edited, 0, m_dev, c->T, c->tunit, c->cslot,
+                                                   c->ccode, c->mask, c->owner, c->touched, cnt);
     STA_CUDA_TRY(cudaGetLastError());
     STA_TRY(launch_fold_list(c, c->touched, cnt + 1, 10 * (cap > 0 ? cap : 1), s));
-    return launch_dyn_mass_edited(c, frame_edited(frame), 0, &frame->m, cap, s);
+    return launch_dyn_mass_edited(c, edited, 0, m_dev, cap, s);
+}
+
+int launch_stream_frame(Ctx *c, FrameHeader *frame, int64_t cap, cudaStream_t s) {
+    return launch_stream_frame(c, frame_edited(frame), &frame->m, frame_counters(frame), cap, s);
 }
 
 // Streaming update with caller-chosen scratch (the allocation-free entry point): the same two
