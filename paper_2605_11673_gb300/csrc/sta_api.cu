@@ -312,7 +312,8 @@ int sta_apply_edits(sta_ctx *x, const sta_edit *edits, int64_t n_edits, void *st
     int64_t m = n_edits;  // edited tetrahedra: a swap edits two
     for (int64_t e = 0; e < n_edits; ++e) m += edits[e].op == STA_SWAP;
 
-    // the frame block to stage into: the graph's (fixed) or the context's (grown on demand)
+    // the frame block to stage into: one of the graph mode's two host-mapped blocks (fixed
+    // capacity), or the context's pinned block (grown on demand)
     const bool use_graph = c->graph_on && m <= c->gcap;
     FrameHeader *h = nullptr, *d = nullptr;
     int gb = 0;
@@ -407,7 +408,8 @@ int sta_apply_edits(sta_ctx *x, const sta_edit *edits, int64_t n_edits, void *st
         return fail(STA_EINVAL, "edit " + std::to_string(e) + ": " + why);
     }
 
-    // header (count, zeroed counters) and list go to the device in one copy
+    // header (count, zeroed counters) before the list: in graph mode the captured kernels read
+    // the host-mapped block itself; otherwise block and list go to the device in one copy
     h->m = m;
     h->cnt[0] = h->cnt[1] = h->cnt[2] = 0ull;
     c->last_edited = m;
