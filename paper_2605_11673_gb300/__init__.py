@@ -120,16 +120,24 @@ def _check(status: int) -> None:
 
 
 _cuda_ok = None
+_raw_stream = None
 
 
 def _stream_handle(stream) -> int:
-    global _cuda_ok
+    """cudaStream_t of `stream` (None: torch's current stream on the current device)."""
+    global _cuda_ok, _raw_stream
     if stream is None:
         import torch
         if _cuda_ok is None:
             _cuda_ok = torch.cuda.is_available()
+            # the raw handle without building a Stream object each call, where torch has it
+            f = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+            if _cuda_ok and f is not None:
+                _raw_stream = lambda: f(torch._C._cuda_getDevice())  # noqa: E731
         if not _cuda_ok:
             return 0
+        if _raw_stream is not None:
+            return _raw_stream()
         return torch.cuda.current_stream().cuda_stream
     if isinstance(stream, int):
         return stream
