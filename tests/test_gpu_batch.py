@@ -116,3 +116,28 @@ def test_launch_shape_does_not_change_values(sta, threads, per_sm):
         assert _eq(ref.values(), got.values())
     ref.close()
     got.close()
+
+
+def test_graph_staging_mixed_with_oversized_frames(sta):
+    """Graph mode with a capacity below some frames: those take the copy path, the others the
+    two host-mapped blocks in turn; values and touched counts match plain launches on every
+    frame, and the last count survives sta_graph_disable."""
+    wl = W.plain_small(seed=8, frames=24)
+    sizes = [int(ed.shape[0] + (ed[:, 0] == 2).sum()) for ed in wl.frames]
+    cap = sorted(sizes)[len(sizes) // 2]          # about half the frames exceed it
+    a = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu)
+    b = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu)
+    a.full_rebuild(wl.mask0)
+    b.full_rebuild(wl.mask0)
+    b.graph_enable(max_edited=cap)
+    assert any(m > cap for m in sizes) and any(m <= cap for m in sizes)
+    for ed in wl.frames:
+        a.apply_edits(ed)
+        b.apply_edits(ed)
+        assert _eq(a.values(), b.values())
+        assert a.last_touched() == b.last_touched()
+    last = b.last_touched()
+    b.graph_disable()
+    assert b.last_touched() == last
+    a.close()
+    b.close()
