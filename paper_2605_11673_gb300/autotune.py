@@ -44,7 +44,7 @@ def pick_best(timings: dict) -> tuple:
     return best
 
 
-def measure(asm, shape, repeats: int = 5, flush_bytes: int = 256 << 20) -> float:
+def measure(asm, shape, repeats: int = 11, flush_bytes: int = 256 << 20) -> float:
     import torch
     asm.set_launch(*shape)
     flush = torch.empty(flush_bytes, dtype=torch.uint8, device="cuda")
@@ -63,7 +63,7 @@ def measure(asm, shape, repeats: int = 5, flush_bytes: int = 256 << 20) -> float
     return times[len(times) // 2]
 
 
-def tune(asm, repeats: int = 5, use_cache: bool = True, path: Path = CACHE,
+def tune(asm, repeats: int = 11, use_cache: bool = True, path: Path = CACHE,
          shapes=None) -> tuple:
     """Best (block_threads, blocks_per_sm) for this context; applied to it and cached."""
     import torch
