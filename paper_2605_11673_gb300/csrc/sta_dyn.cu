@@ -17,7 +17,8 @@
 // forming the matrix, one thread per node over its three rows (they share their columns).
 // Every dot product is a fixed-order reduction (warp tree, warps in order, CTAs in order by the
 // last CTA to arrive), so a solve is deterministic for a given context.  Iterations run in
-// captured chunks of CG_CHUNK (3 launches each); the host reads the state between chunks.
+// captured chunks of CG_CHUNK (2 launches each: the SpMV of z also forms p = z + beta p and
+// q = A z + beta q = A p, then the update); the host reads the state between chunks.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -181,9 +182,10 @@ k_cg_spmv(int64_t n, const int32_t *__restrict__ perm, const int32_t *__restrict
           const int32_t *__restrict__ col, const double *__restrict__ val,
           const double *__restrict__ mass, double h2, const uint8_t *__restrict__ fr,
           const double *__restrict__ xin, double *__restrict__ qout, double *__restrict__ part,
-          CgState *st, bool dots) {
+          CgState *st, bool dots, double *__restrict__ p) {
     __shared__ double sh[DYN_WARPS];
     if (dots && cg_stopped(st)) return;
+    const double beta = p ? st->beta : 0.0;
     const int lane = threadIdx.x & 31, qd = lane & 3;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -232,9 +234,17 @@ k_cg_spmv(int64_t n, const int32_t *__restrict__ perm, const int32_t *__restrict
             const int64_t d = 3 * a + qd;
             const double xd = xin[d];
             const double sd = qd == 0 ? s0 : (qd == 1 ? s1 : s2);
-            const double q = fr[d] ? __fma_rn(mass[a], xd, h2 * sd) : 0.0;
-            qout[d] = q;
-            pq = __fma_rn(xd, q, pq);
+            double q = fr[d] ? __fma_rn(mass[a], xd, h2 * sd) : 0.0;
+            if (p) {  // CG step: xin = z, p = z + beta p, q = A z + beta q = A p
+                const double pd = __fma_rn(beta, p[d], xd);
+                q = __fma_rn(beta, qout[d], q);
+                p[d] = pd;
+                qout[d] = q;
+                pq = __fma_rn(pd, q, pq);
+            } else {
+                qout[d] = q;
+                pq = __fma_rn(xd, q, pq);
+            }
         }
     }
     if (!dots) return;
@@ -251,9 +261,9 @@ k_cg_spmv(int64_t n, const int32_t *__restrict__ perm, const int32_t *__restrict
     }
 }
 
-// r = b - q, z = D^-1 r, p = z; rz, rr, bb; the convergence test.
+// r = b - q, z = D^-1 r, p = q = 0; rz, rr, bb; the convergence test.
 __global__ void __launch_bounds__(DYN_TPB)
-k_cg_r0(int64_t n3, const double *__restrict__ b, const double *__restrict__ q,
+k_cg_r0(int64_t n3, const double *__restrict__ b, double *__restrict__ q,
         const double *__restrict__ dinv, double *__restrict__ r, double *__restrict__ z,
         double *__restrict__ p, double *__restrict__ part, CgState *st) {
     __shared__ double sh[DYN_WARPS];
@@ -263,7 +273,8 @@ k_cg_r0(int64_t n3, const double *__restrict__ b, const double *__restrict__ q,
         const double ri = b[i] - q[i], zi = dinv[i] * ri;
         r[i] = ri;
         z[i] = zi;
-        p[i] = zi;
+        p[i] = 0.0;  // with beta = 0 the first step forms p = z and q = A z
+        q[i] = 0.0;
         rz = __fma_rn(ri, zi, rz);
         rr = __fma_rn(ri, ri, rr);
         bb = __fma_rn(b[i], b[i], bb);
@@ -282,6 +293,7 @@ k_cg_r0(int64_t n3, const double *__restrict__ b, const double *__restrict__ q,
             st->rz = s0;
             st->rr = s1;
             st->bb = s2;
+            st->beta = 0.0;
             st->iters = 0;
             st->done = s1 <= st->tol2 * s2 ? 1 : 0;
             st->arrive[1] = 0u;
@@ -326,15 +338,6 @@ k_cg_update(int64_t n3, double *__restrict__ x, double *__restrict__ r, double *
     }
 }
 
-// p = z + beta p.
-__global__ void k_cg_pupdate(int64_t n3, double *__restrict__ p, const double *__restrict__ z,
-                             const CgState *st) {
-    if (st->done || st->iters >= st->max_iter) return;
-    const double beta = st->beta;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3;
-         i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = __fma_rn(beta, p[i], z[i]);
-}
 
 // Static solve (sta_solve): b, x0 and the Jacobi inverse diagonal on the caller's free DOFs.
 __global__ void k_cg_init_static(int64_t n3, const int32_t *__restrict__ adj_ptr,
@@ -389,9 +392,11 @@ __global__ void __launch_bounds__(DYN_TPB)
 k_cg_spmv_scalar(int64_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ row_ptr,
                  const int32_t *__restrict__ col, const double *__restrict__ val,
                  const uint8_t *__restrict__ fr, const double *__restrict__ xin,
-                 double *__restrict__ qout, double *__restrict__ part, CgState *st, bool dots) {
+                 double *__restrict__ qout, double *__restrict__ part, CgState *st, bool dots,
+                 double *__restrict__ p) {
     __shared__ double sh[DYN_WARPS];
     if (dots && cg_stopped(st)) return;
+    const double beta = p ? st->beta : 0.0;
     const int lane = threadIdx.x & 31, qd = lane & 3;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -408,9 +413,17 @@ k_cg_spmv_scalar(int64_t n, const int32_t *__restrict__ perm, const int32_t *__r
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
         acc += __shfl_xor_sync(0xffffffffu, acc, 2);
         if (a >= 0 && qd == 0) {
-            const double q = fr[a] ? acc : 0.0;
-            qout[a] = q;
-            pq = __fma_rn(xin[a], q, pq);
+            double q = fr[a] ? acc : 0.0;
+            if (p) {  // CG step: xin = z, p = z + beta p, q = A z + beta q = A p
+                const double pa = __fma_rn(beta, p[a], xin[a]);
+                q = __fma_rn(beta, qout[a], q);
+                p[a] = pa;
+                qout[a] = q;
+                pq = __fma_rn(pa, q, pq);
+            } else {
+                qout[a] = q;
+                pq = __fma_rn(xin[a], q, pq);
+            }
         }
     }
     if (!dots) return;
@@ -510,7 +523,7 @@ int launch_dyn_qmass(Ctx *c, cudaStream_t s) {
 
 namespace {
 
-// One chunk of CG_CHUNK iterations (3 launches each) of A = diag(mass) + h2 K(val), launched
+// One chunk of CG_CHUNK iterations (2 launches each) of A = diag(mass) + h2 K(val), launched
 // or captured on s.
 int cg_chunk(Ctx *c, const double *val, const double *mass, double h2, cudaStream_t s) {
     const int64_t n3 = c->nrows;  // DOFs: 3 per node, or 1 for the scalar proxy operator
@@ -521,12 +534,11 @@ int cg_chunk(Ctx *c, const double *val, const double *mass, double h2, cudaStrea
     for (int it = 0; it < CG_CHUNK; ++it) {
         if (c->op == STA_OP_PROXY)
             k_cg_spmv_scalar<<<gv, DYN_TPB, 0, s>>>(c->n, c->dyn_perm, c->row_ptr, c->col, val,
-                                                    c->cg_free, p, q, c->cg_part, st, true);
+                                                    c->cg_free, z, q, c->cg_part, st, true, p);
         else
             k_cg_spmv<<<gv, DYN_TPB, 0, s>>>(c->n, c->dyn_perm, c->row_ptr, c->col, val, mass, h2,
-                                            c->cg_free, p, q, c->cg_part, st, true);
+                                            c->cg_free, z, q, c->cg_part, st, true, p);
         k_cg_update<<<gv, DYN_TPB, 0, s>>>(n3, x, r, z, p, q, dinv, c->cg_part, st);
-        k_cg_pupdate<<<gv, DYN_TPB, 0, s>>>(n3, p, z, st);
     }
     STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;
@@ -608,7 +620,7 @@ int launch_dyn_step(Ctx *c, double tol, int32_t max_iter, int32_t *iters, double
                                          c->clamped, c->du, c->dv, c->df, c->dyn_h, x, b, dinv,
                                          c->cg_free);
         k_cg_spmv<<<gv, DYN_TPB, 0, s>>>(c->n, c->dyn_perm, c->row_ptr, c->col, c->val, c->mass,
-                                        c->dyn_h * c->dyn_h, c->cg_free, x, q, c->cg_part, st, false);
+                                        c->dyn_h * c->dyn_h, c->cg_free, x, q, c->cg_part, st, false, nullptr);
         k_cg_r0<<<gv, DYN_TPB, 0, s>>>(n3, b, q, dinv, r, z, p, c->cg_part, st);
         STA_CUDA_TRY(cudaGetLastError());
     }
@@ -707,7 +719,7 @@ extern "C" int sta_dyn_apply(sta_ctx *x, const double *xv, double *y, void *stre
     k_dyn_restrict<<<gv, DYN_TPB, 0, s>>>(n3, c->mass, c->clamped, xv, xf, c->cg_free);
     k_cg_spmv<<<gv, DYN_TPB, 0, s>>>(c->n, c->dyn_perm, c->row_ptr, c->col, c->val, c->mass,
                                     c->dyn_h * c->dyn_h, c->cg_free, xf, y, c->cg_part,
-                                    reinterpret_cast<CgState *>(c->cg_state), false);
+                                    reinterpret_cast<CgState *>(c->cg_state), false, nullptr);
     STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;
 }
@@ -737,12 +749,12 @@ extern "C" int sta_solve(sta_ctx *x, const double *val, const double *b, const u
             k_cg_init_scalar<<<gv, DYN_TPB, 0, s>>>(n3, c->pdiag, A, free, b, xv, xw, bw, dinv,
                                                     c->cg_free);
             k_cg_spmv_scalar<<<gv, DYN_TPB, 0, s>>>(c->n, c->dyn_perm, c->row_ptr, c->col, A,
-                                                    c->cg_free, xw, q, c->cg_part, st, false);
+                                                    c->cg_free, xw, q, c->cg_part, st, false, nullptr);
         } else {
             k_cg_init_static<<<gv, DYN_TPB, 0, s>>>(n3, c->adj_ptr, c->adj, c->row_ptr, A, free, b,
                                                     xv, xw, bw, dinv, c->cg_free);
             k_cg_spmv<<<gv, DYN_TPB, 0, s>>>(c->n, c->dyn_perm, c->row_ptr, c->col, A, c->cg_zero,
-                                            1.0, c->cg_free, xw, q, c->cg_part, st, false);
+                                            1.0, c->cg_free, xw, q, c->cg_part, st, false, nullptr);
         }
         k_cg_r0<<<gv, DYN_TPB, 0, s>>>(n3, bw, q, dinv, r, z, p, c->cg_part, st);
         STA_CUDA_TRY(cudaGetLastError());
