@@ -557,6 +557,12 @@ int cg_iterate(Ctx *c, cudaGraphExec_t g, const double *val, const double *mass,
     CgState *st = reinterpret_cast<CgState *>(c->cg_state);
     double best = -1.0;
     int32_t best_it = 0;
+    // the first chunk goes out with the initial residual (its kernels return at once if that is
+    // already converged or max_iter is 0): one host round trip fewer per solve
+    if (c->n > 0) {
+        if (g) STA_CUDA_TRY(cudaGraphLaunch(g, s));
+        else STA_TRY(cg_chunk(c, val, mass, h2, s));
+    }
     for (;;) {
         if (c->n > 0) {
             STA_CUDA_TRY(cudaMemcpyAsync(hs, st, sizeof *hs, cudaMemcpyDeviceToHost, s));
