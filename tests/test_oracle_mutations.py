@@ -62,6 +62,15 @@ MUTATIONS = {
     "mass_volume_cross_sign": ("    double c1 = fma(d[1][2], d[2][0], -(d[1][0] * d[2][2]));",
                                "    double c1 = fma(d[1][0], d[2][2], -(d[1][2] * d[2][0]));",
                                [pins.test_lumped_mass_vs_volumes]),
+    "proxy_step_sign": ("            int32_t step = side == 0 ? -1 : 1;",
+                        "            int32_t step = side == 0 ? 1 : -1;",
+                        [pins.test_proxy_stream_equals_rebuild_every_frame]),
+    "proxy_eps_dropped": ("        if (kd >= 0) val[kd] = (double)deg[u] + eps;  /* a node of no tetrahedron has no row */",
+                          "        if (kd >= 0) val[kd] = (double)deg[u];",
+                          [pins.test_proxy_rebuild_vs_textbook_laplacian]),
+    "mass_ignores_mask": ("            if (!mask[t]) continue;\n            m += (rho * tet_volume",
+                          "            m += (rho * tet_volume",
+                          [pins.test_lumped_mass_vs_volumes]),
 }
 
 
