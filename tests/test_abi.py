@@ -85,3 +85,29 @@ def test_oracle_and_product_share_no_code():
         if f.is_file() and f.suffix in (".c", ".py", ".h"):
             text = f.read_text()
             assert "paper_2605_11673_gb300" not in text and "libsta" not in text
+
+
+def test_entry_points_reject_null_context_and_bad_meshes_on_the_host(lib):
+    """Every entry point checks its handle (and the proxy create its mesh) before any device
+    work: these calls fail with STA_EINVAL on a machine without a GPU."""
+    import ctypes as C
+    L = lib.load_library()
+    i32, f64 = C.c_int32(), C.c_double()
+    p = C.c_void_p()
+    calls = [
+        L.sta_set_policy(None, 0, None), L.sta_set_params(None, None, None, None, 0, None),
+        L.sta_proxy_state(None, C.byref(p), C.byref(p)),
+        L.sta_dyn_setup(None, 1.0, 1.0, None, None, None),
+        L.sta_dyn_step(None, 1e-8, 10, C.byref(i32), C.byref(f64), None),
+        L.sta_dyn_apply(None, None, None, None), L.sta_dyn_state(None, C.byref(p), None, None),
+        L.sta_dyn_set_state(None, None, None, 0, None),
+        L.sta_solve(None, None, None, None, 1e-8, 10, None, None, None, None),
+        L.sta_outer_grad(None, None, None, None, None, None),
+        L.sta_apply_edits(None, None, 0, None), L.sta_full_rebuild(None, None, 0, None),
+        L.sta_refold(None, None), L.sta_graph_enable(None, 1, None),
+    ]
+    assert all(r == lib.STA_EINVAL for r in calls), calls
+    for tets in (np.array([[0, 1, 2, 2]]), np.array([[0, 1, 2, 9]]), np.array([[-1, 1, 2, 3]])):
+        with pytest.raises(lib.StaError) as e:
+            lib.sta_proxy_create(4, tets)
+        assert e.value.status == lib.STA_EINVAL
