@@ -196,3 +196,27 @@ def test_proxy_solve_vs_direct(sta, orc):
     assert np.linalg.norm(xn - ref) <= 1e-9 * np.linalg.norm(ref)
     assert np.all(xn[~free] == 0.0)
     px.close()
+
+
+def test_proxy_full_size_local_recompute_and_solve(sta, orc):
+    """The full-size prefractured block under the local-recompute policy (bit-exact against the
+    oracle on each frame), and the per-frame solve's residual under the oracle's matrix."""
+    import scipy.sparse as sp
+    import torch
+    wl = W.prefractured_block()
+    _run(sta, orc, wl, eps=1e-2, frames=4, policy=sta.STA_POLICY_REFOLD)
+    px = sta.ProxyAssembler(wl.n_nodes, wl.tets, eps=1e-2)
+    mask = wl.masks()[4]
+    px.full_rebuild(mask)
+    P = orc.Pattern(wl.n_nodes, wl.tets)
+    ptr, col = P.proxy_pattern()
+    _, _, val = P.proxy_rebuild(mask, 1e-2)
+    A = sp.csr_matrix((val, col, ptr), shape=(wl.n_nodes, wl.n_nodes))
+    free = np.diff(ptr) > 0
+    b = np.where(free, np.random.default_rng(9).standard_normal(wl.n_nodes), 0.0)
+    x, it, rel = sta.sta_solve(px.h, torch.as_tensor(b, device="cuda"),
+                               torch.as_tensor(free, device="cuda"), tol=1e-10)
+    xn = x.cpu().numpy()
+    assert rel <= 1e-10 and it > 0
+    assert np.linalg.norm((A @ xn - b)[free]) <= 10 * 1e-10 * np.linalg.norm(b)
+    px.close()
