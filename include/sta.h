@@ -100,7 +100,8 @@ int sta_destroy(sta_ctx *ctx);
  *  mask            n_tets bytes, nonzero = active; host memory if mask_on_device == 0,
  *                  else device memory
  * With a device mask the host mirror used for edit validation is refreshed by a
- * device-to-host copy, which synchronises `stream`.
+ * device-to-host copy, which synchronises `stream`.  Either way the context keeps the mask as
+ * 0/1 bytes (sta_mask).
  */
 int sta_full_rebuild(sta_ctx *ctx, const uint8_t *mask, int mask_on_device, void *stream);
 

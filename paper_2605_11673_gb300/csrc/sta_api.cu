@@ -261,19 +261,18 @@ int sta_full_rebuild(sta_ctx *x, const uint8_t *mask, int mask_on_device, void *
     if (c->T > 0 && !mask) return fail(STA_EINVAL, "mask is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     if (c->T > 0) {
-        if (mask_on_device) {
+        STA_TRY(wait_staging(x));
+        if (mask_on_device) {  // read back for the host mirror; the device copy is the 0/1 one
             std::vector<uint8_t> hm((size_t)c->T);
-            STA_CUDA_TRY(cudaMemcpyAsync(c->mask, mask, (size_t)c->T, cudaMemcpyDeviceToDevice, s));
             STA_CUDA_TRY(cudaMemcpyAsync(hm.data(), mask, (size_t)c->T, cudaMemcpyDeviceToHost, s));
             STA_CUDA_TRY(cudaStreamSynchronize(s));
-            set_host_mask(c, hm.data(), nullptr);
+            set_host_mask(c, hm.data(), x->h_mask);
         } else {
-            STA_TRY(wait_staging(x));
             set_host_mask(c, mask, x->h_mask);
-            STA_CUDA_TRY(cudaMemcpyAsync(c->mask, x->h_mask, (size_t)c->T, cudaMemcpyHostToDevice, s));
-            STA_CUDA_TRY(cudaEventRecord(x->h2d_done, s));
-            x->h2d_pending = true;
         }
+        STA_CUDA_TRY(cudaMemcpyAsync(c->mask, x->h_mask, (size_t)c->T, cudaMemcpyHostToDevice, s));
+        STA_CUDA_TRY(cudaEventRecord(x->h2d_done, s));
+        x->h2d_pending = true;
     }
     if (c->graph_on) {
         STA_CUDA_TRY(cudaGraphLaunch(c->g_rebuild, s));

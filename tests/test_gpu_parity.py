@@ -108,8 +108,10 @@ def test_rebuild_device_mask_and_eps(sta, orc):
     Ke, _ = orc.element_all(wl.X, wl.tets, wl.E, wl.nu)
     asm = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu, eps=0.25)
     mask = wl.masks()[7]
-    asm.full_rebuild(torch.as_tensor(mask, device="cuda"))
+    raw = mask * np.where(np.arange(mask.size) % 3 == 0, 3, 255).astype(np.uint8)  # any nonzero
+    asm.full_rebuild(torch.as_tensor(raw, device="cuda"))
     _assert_bitwise(_vals(asm), P.rebuild(Ke, mask, 0.25), "device-mask rebuild with eps")
+    assert np.array_equal(asm.mask().cpu().numpy(), mask), "kept mask is 0/1"
     # edits validated against the refreshed host mirror
     asm.apply_edits(wl.frames[7])
     _assert_bitwise(_vals(asm), P.rebuild(Ke, wl.masks()[8], 0.25), "stream after device mask")
