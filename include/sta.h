@@ -317,13 +317,14 @@ int sta_set_policy(sta_ctx *ctx, int32_t policy, void *stream);
  *    entries set or cleared and the end nodes' degrees moved where a multiplicity moves
  *    between 0 and > 0), sta_last_touched (entries the last frame visited: both entries of
  *    each edge and the diagonal entry of each node of the edited tetrahedra), sta_graph_*,
- *    sta_mask, sta_sizes, sta_spmv, sta_destroy.  The streamed state equals a rebuild on the
- *    same mask bit for bit.  sta_set_policy chooses the update: STA_POLICY_FIXED (the
- *    default for the proxy: the maintained multiplicities updated by +-1, Sec. 3.2) or
- *    STA_POLICY_REFOLD (the paper's local_recompute: each touched edge recounted over the
- *    tetrahedra incident to it, each touched node's degree over its row); same values and
- *    state.  Calls of the elasticity operator (sta_set_params, sta_recompute_elements,
- *    sta_element_matrices, sta_scatter_map, sta_adjoint) return STA_ESTATE.
+ *    sta_mask, sta_sizes, sta_spmv, sta_solve, sta_destroy.  The streamed state equals a
+ *    rebuild on the same mask bit for bit.  sta_set_policy chooses the update:
+ *    STA_POLICY_FIXED (the default for the proxy: the maintained multiplicities updated by
+ *    +-1, Sec. 3.2) or STA_POLICY_REFOLD (the paper's local_recompute: each touched edge
+ *    recounted over the tetrahedra incident to it, each touched node's degree over its row);
+ *    same values and state.  Calls of the elasticity operator (sta_set_params,
+ *    sta_recompute_elements, sta_element_matrices, sta_scatter_map, sta_adjoint) return
+ *    STA_ESTATE.
  * Create: tets (n_tets x 4 int32, host) as for sta_create; every tetrahedron starts inactive
  * (A = eps I on the nodes of the mesh).  Limits: n_tets < 2^27, nnz < 2^31.
  */
@@ -375,9 +376,11 @@ int sta_dyn_set_state(sta_ctx *ctx, const double *u, const double *v, int on_dev
  * with free[i] != 0 (and a nonzero diagonal), x = 0 elsewhere, from the initial guess in x,
  * until ||r|| <= tol ||b_f||, max_iter iterations, or no halving of the residual for 1000
  * iterations (the attainable accuracy).  val: device nnz values of the context's pattern
- * (NULL = the current values); b, x: device 3n doubles; free: device 3n bytes.  Same kernels
- * as the implicit-Euler step (fixed-order reductions: deterministic).  Synchronises `stream`.
- * *iters and *rel_res (||r|| / ||b_f|| from the recurrence) may be NULL.  Elasticity contexts.
+ * (NULL = the current values); b, x: device n_rows doubles; free: device n_rows bytes
+ * (n_rows of sta_csr: 3n for elasticity, n for the proxy operator, whose solve is the paper's
+ * per-frame solve of Algorithm 1).  Same kernels as the implicit-Euler step (fixed-order
+ * reductions: deterministic).  Synchronises `stream`.  *iters and *rel_res (||r|| / ||b_f||
+ * from the recurrence) may be NULL.  Both operators.
  *
  * sta_outer_grad -- the adjoint rule of such a solve: grad_val[k] = -lam[row(k)] u[col(k)]
  * for entries k between free DOFs, 0 elsewhere (lam, u: device nrows doubles; free: device
