@@ -111,3 +111,46 @@ def test_entry_points_reject_null_context_and_bad_meshes_on_the_host(lib):
         with pytest.raises(lib.StaError) as e:
             lib.sta_proxy_create(4, tets)
         assert e.value.status == lib.STA_EINVAL
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include <string.h>
+#include "sta.h"
+
+int main(void) {
+    sta_options o;
+    sta_ctx *ctx = NULL;
+    const double X[12] = {0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0, 1};
+    const int32_t bad[4] = {0, 1, 2, 2};
+    const double E = 1.0, nu = 0.3;
+    sta_default_options(&o);
+    if (o.eps != 0.0 || o.block_threads != 0 || o.blocks_per_sm != 0) return 1;
+    if (sta_create(X, 4, bad, 1, &E, &nu, &o, NULL, &ctx) != STA_EINVAL || ctx != NULL) return 2;
+    if (strstr(sta_last_error(), "repeated node") == NULL) return 3;
+    if (strcmp(sta_status_string(STA_OK), "ok") != 0) return 4;
+    if (sta_destroy(NULL) != STA_OK) return 5;
+    if (sta_apply_edits(NULL, NULL, 0, NULL) != STA_EINVAL) return 6;
+    puts("ok");
+    return 0;
+}
+"""
+
+
+@pytest.mark.parametrize("compiler, std", [("gcc", "-std=c99"), ("g++", "-std=c++17")])
+def test_header_is_a_plain_c_boundary(lib, tmp_path, compiler, std):
+    """include/sta.h compiles as strict C99 (and as C++ through its extern "C" guard), and a
+    client with no Python and no torch links against libsta and calls it: host-side calls
+    only, so no GPU is needed."""
+    import shutil
+    if shutil.which(compiler) is None:
+        pytest.skip(f"{compiler} not installed")
+    src = tmp_path / ("client.c" if compiler == "gcc" else "client.cpp")
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = lib.LIB_PATH.parent
+    subprocess.run([compiler, std, "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    f"-I{ROOT / 'include'}", str(src), str(lib.LIB_PATH),
+                    f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True, capture_output=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
