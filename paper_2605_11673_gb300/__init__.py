@@ -2,7 +2,8 @@
 
 Argument marshalling only: every step of the assembly runs in the CUDA library
 (``_build/libsta.so``, built by ``paper_2605_11673_gb300.build``).  There is no CPU or
-PyTorch fallback: if the library is missing, importing the binding raises.
+PyTorch fallback: if the library is missing, the first call into the binding raises
+ImportError.
 
 The functions ``sta_*`` mirror the C-ABI of include/sta.h one to one; ``Assembler`` is a
 small convenience wrapper around them.  PyTorch is used for device memory of user-side
@@ -148,6 +149,50 @@ def _host(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
 
 
+# The C-ABI takes plain pointers and cannot see the length of what they point to, so the
+# binding checks every array it passes against the context's sizes: a wrong length raises
+# here instead of reading or writing past the end of a buffer.
+
+_fixed = {}  # handle -> the sizes fixed for the context's lifetime
+
+
+def _sizes(h: int) -> dict:
+    s = _fixed.get(h)
+    if s is None:
+        k = C.c_int32()
+        _check(load_library().sta_batch_size(h, C.byref(k)))
+        s = _fixed[h] = dict(sta_sizes(h), k=int(k.value))
+    return s
+
+
+def _host_n(a, dtype, n: int, what: str):
+    """Host copy of `a` as n contiguous elements of dtype."""
+    a = _host(a, dtype).reshape(-1)
+    if a.size != n:
+        raise ValueError(f"{what} must have {n} elements, got {a.size}")
+    return a
+
+
+def _dev(t, n: int, what: str, dtypes=None):
+    """`t` as a contiguous CUDA tensor of n elements; dtypes: the accepted dtypes (default
+    float64), or () for any."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    dtypes = (torch.float64,) if dtypes is None else dtypes
+    if dtypes and t.dtype not in dtypes:
+        raise TypeError(f"{what} must be one of {dtypes}, got {t.dtype}")
+    if t.numel() != n:
+        raise ValueError(f"{what} must have {n} elements, got {t.numel()}")
+    return t.contiguous()
+
+
+def _dev_flags(t, n: int, what: str):
+    """A CUDA tensor of n flags (any dtype) as contiguous uint8."""
+    import torch
+    return _dev(t, n, what, ()).to(torch.uint8).contiguous()
+
+
 class DeviceArray:
     """Zero-copy view of context-owned device memory (``__cuda_array_interface__``)."""
 
@@ -187,6 +232,7 @@ def sta_create(nodes, tets, young, poisson, opt: sta_options | None = None, stre
                         young.ctypes.data, poisson.ctypes.data,
                         C.byref(opt) if opt is not None else None, _stream_handle(stream),
                         C.byref(h)))
+    _fixed.pop(h.value, None)  # a new context may reuse a destroyed one's address
     return h.value
 
 
@@ -197,6 +243,7 @@ def sta_proxy_create(n_nodes: int, tets, eps: float = 0.0, stream=None) -> int:
     h = _p()
     _check(L.sta_proxy_create(int(n_nodes), tets.ctypes.data, tets.shape[0], float(eps),
                               _stream_handle(stream), C.byref(h)))
+    _fixed.pop(h.value, None)  # a new context may reuse a destroyed one's address
     return h.value
 
 
@@ -211,8 +258,10 @@ def sta_proxy_state(h: int, owner=None):
 
 def sta_dyn_setup(h: int, rho: float, dt: float, f=None, clamped=None, stream=None) -> None:
     """Implicit-Euler loop (include/sta.h): density, time step, load (3n), clamped nodes (n)."""
-    fp = _host(f, np.float64).reshape(-1) if f is not None else None
-    cp = _host(clamped, np.uint8).reshape(-1) if clamped is not None else None
+    s = _sizes(h)
+    fp = _host_n(f, np.float64, s["n_rows"], "f") if f is not None else None
+    cp = (_host_n(np.asarray(clamped) != 0, np.uint8, s["n_nodes"], "clamped")
+          if clamped is not None else None)
     _check(load_library().sta_dyn_setup(h, float(rho), float(dt),
                                         fp.ctypes.data if fp is not None else None,
                                         cp.ctypes.data if cp is not None else None,
@@ -229,7 +278,7 @@ def sta_dyn_step(h: int, tol: float = 1e-10, max_iter: int = 1000, stream=None):
 
 def sta_dyn_apply(h: int, x, stream=None):
     """y = (M + h^2 K) x on the free DOFs (CUDA float64 tensors of 3n)."""
-    x = x.contiguous()
+    x = _dev(x, _sizes(h)["n_rows"], "x")
     y = x.new_empty(x.shape)
     _check(load_library().sta_dyn_apply(h, x.data_ptr(), y.data_ptr(), _stream_handle(stream)))
     return y
@@ -240,10 +289,12 @@ def sta_solve(h: int, b, free, val=None, tol: float = 1e-12, max_iter: int = 200
     """Jacobi-PCG for A_ff x_f = b_f (CUDA tensors: b float64 3n, free bool/uint8 3n);
     returns (x, iterations, relative residual)."""
     import torch
-    b = b.contiguous()
-    fr = free.to(torch.uint8).contiguous()
-    x = torch.zeros_like(b) if x0 is None else x0.clone().contiguous()
-    vp = val.contiguous().data_ptr() if val is not None else None
+    s = _sizes(h)
+    b = _dev(b, s["n_rows"], "b")
+    fr = _dev_flags(free, s["n_rows"], "free")
+    x = torch.zeros_like(b) if x0 is None else _dev(x0, s["n_rows"], "x0").clone()
+    val = _dev(val, s["nnz"], "val") if val is not None else None
+    vp = val.data_ptr() if val is not None else None
     it, rr = C.c_int32(), C.c_double()
     _check(load_library().sta_solve(h, vp, b.data_ptr(), fr.data_ptr(), float(tol), int(max_iter),
                                     x.data_ptr(), C.byref(it), C.byref(rr), _stream_handle(stream)))
@@ -253,11 +304,12 @@ def sta_solve(h: int, b, free, val=None, tol: float = 1e-12, max_iter: int = 200
 def sta_outer_grad(h: int, lam, u, free, stream=None):
     """dL/dval = -lam_i u_j on entries between free DOFs (CUDA tensors)."""
     import torch
-    nnz = sta_sizes(h)["nnz"]
-    g = torch.empty(nnz, dtype=torch.float64, device=lam.device)
-    fr = free.to(torch.uint8).contiguous()
-    _check(load_library().sta_outer_grad(h, lam.contiguous().data_ptr(), u.contiguous().data_ptr(),
-                                         fr.data_ptr(), g.data_ptr(), _stream_handle(stream)))
+    s = _sizes(h)
+    lam, u = _dev(lam, s["n_rows"], "lam"), _dev(u, s["n_rows"], "u")
+    fr = _dev_flags(free, s["n_rows"], "free")
+    g = torch.empty(s["nnz"], dtype=torch.float64, device=lam.device)
+    _check(load_library().sta_outer_grad(h, lam.data_ptr(), u.data_ptr(), fr.data_ptr(),
+                                         g.data_ptr(), _stream_handle(stream)))
     return g
 
 
@@ -273,25 +325,29 @@ def sta_dyn_state(h: int, owner=None):
 
 def sta_dyn_set_state(h: int, u=None, v=None, stream=None) -> None:
     """Overwrite u and/or v from host arrays."""
-    up = _host(u, np.float64).reshape(-1) if u is not None else None
-    vp = _host(v, np.float64).reshape(-1) if v is not None else None
+    n = _sizes(h)["n_rows"]
+    up = _host_n(u, np.float64, n, "u") if u is not None else None
+    vp = _host_n(v, np.float64, n, "v") if v is not None else None
     _check(load_library().sta_dyn_set_state(h, up.ctypes.data if up is not None else None,
                                             vp.ctypes.data if vp is not None else None, 0,
                                             _stream_handle(stream)))
 
 
 def sta_destroy(h: int) -> None:
+    _fixed.pop(h, None)
     _check(load_library().sta_destroy(h))
 
 
 def sta_full_rebuild(h: int, mask, stream=None) -> None:
     """mask: numpy/host array (copied by the library) or a CUDA tensor (device path)."""
+    import torch
     L = load_library()
+    T = _sizes(h)["n_tets"]
     if hasattr(mask, "is_cuda") and mask.is_cuda:
-        m = mask.contiguous()
+        m = _dev(mask, T, "mask", (torch.uint8, torch.bool))
         _check(L.sta_full_rebuild(h, m.data_ptr(), 1, _stream_handle(stream)))
     else:
-        m = _host(mask, np.uint8)
+        m = _host_n(mask, np.uint8, T, "mask")
         _check(L.sta_full_rebuild(h, m.ctypes.data, 0, _stream_handle(stream)))
 
 
@@ -363,20 +419,19 @@ def sta_set_params(h: int, nodes=None, young=None, poisson=None, stream=None) ->
     """Host (numpy) arrays, or CUDA tensors (then all given arrays must be on the device)."""
     arrs = [a for a in (nodes, young, poisson) if a is not None]
     on_dev = bool(arrs) and all(hasattr(a, "is_cuda") and a.is_cuda for a in arrs)
+    s = _sizes(h)
     keep = []
 
-    def ptr(a):
+    def ptr(a, n, what):
         if a is None:
             return None
-        if on_dev:
-            a = a.contiguous()
-            keep.append(a)
-            return a.data_ptr()
-        a = _host(a, np.float64)
+        a = _dev(a, n, what) if on_dev else _host_n(a, np.float64, n, what)
         keep.append(a)
-        return a.ctypes.data
+        return a.data_ptr() if on_dev else a.ctypes.data
 
-    _check(load_library().sta_set_params(h, ptr(nodes), ptr(young), ptr(poisson),
+    _check(load_library().sta_set_params(h, ptr(nodes, 3 * s["n_nodes"], "nodes"),
+                                         ptr(young, s["n_tets"], "young"),
+                                         ptr(poisson, s["n_tets"], "poisson"),
                                          1 if on_dev else 0, _stream_handle(stream)))
 
 
@@ -393,9 +448,8 @@ def sta_element_matrices(h: int, tet_ids, stream=None):
 def sta_adjoint(h: int, grad_val, stream=None):
     """(dE, dnu, dX) CUDA tensors for dL/dval given as a CUDA float64 tensor of nnz values."""
     import torch
-    s = sta_sizes(h)
-    g = grad_val.contiguous()
-    assert g.is_cuda and g.dtype == torch.float64 and g.numel() == s["nnz"]
+    s = _sizes(h)
+    g = _dev(grad_val, s["nnz"], "grad_val")
     dE = torch.empty(s["n_tets"], dtype=torch.float64, device=g.device)
     dnu = torch.empty_like(dE)
     dX = torch.empty((s["n_nodes"], 3), dtype=torch.float64, device=g.device)
@@ -406,9 +460,11 @@ def sta_adjoint(h: int, grad_val, stream=None):
 
 def sta_spmv(h: int, x, val=None, stream=None):
     """y = A x (CUDA float64 tensors) over the pattern, with `val` or the current values."""
-    x = x.contiguous()
+    s = _sizes(h)
+    x = _dev(x, s["n_rows"], "x")
     y = x.new_empty(x.shape)
-    vp = val.contiguous().data_ptr() if val is not None else None
+    val = _dev(val, s["nnz"], "val") if val is not None else None
+    vp = val.data_ptr() if val is not None else None
     _check(load_library().sta_spmv(h, vp, x.data_ptr(), y.data_ptr(), _stream_handle(stream)))
     return y
 
@@ -453,6 +509,7 @@ def sta_batch_create(instances, opt: sta_options | None = None, stream=None) -> 
     _check(L.sta_batch_create(k, nn, arr["X"], nt, arr["T"], arr["E"], arr["NU"],
                               C.byref(opt) if opt is not None else None, _stream_handle(stream),
                               C.byref(h)))
+    _fixed.pop(h.value, None)  # a new context may reuse a destroyed one's address
     return h.value
 
 
@@ -470,6 +527,9 @@ def sta_batch_instance(h: int, i: int, owner=None):
 def sta_batch_apply_edits(h: int, edits_per_instance, stream=None) -> None:
     """edits_per_instance: list of (m_i, 3) int32 arrays with instance-local tet ids."""
     parts = [_host(e, np.int32).reshape(-1, 3) for e in edits_per_instance]
+    k = _sizes(h)["k"]
+    if len(parts) != k:
+        raise ValueError(f"one edit list per instance: {k} expected, got {len(parts)}")
     counts = (C.c_int64 * len(parts))(*[p.shape[0] for p in parts])
     allp = np.ascontiguousarray(np.concatenate(parts, 0)) if parts else np.zeros((0, 3), np.int32)
     _check(load_library().sta_batch_apply_edits(h, counts, allp.ctypes.data if allp.shape[0] else None,

@@ -154,3 +154,19 @@ def test_header_is_a_plain_c_boundary(lib, tmp_path, compiler, std):
                     f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True, capture_output=True)
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
+
+
+def test_binding_array_checks(lib):
+    """The binding's checks of what it hands the library (raw pointers, no lengths): host arrays
+    of the wrong length and tensors that are not CUDA tensors of the expected dtype and length
+    are rejected before any call (no GPU needed)."""
+    import torch
+    with pytest.raises(ValueError):
+        lib._host_n(np.zeros(5), np.float64, 6, "f")
+    assert lib._host_n(np.zeros((2, 3)), np.float64, 6, "f").shape == (6,)
+    with pytest.raises(TypeError):
+        lib._dev(torch.zeros(6, dtype=torch.float64), 6, "x")  # a host tensor
+    with pytest.raises(TypeError):
+        lib._dev(np.zeros(6), 6, "x")
+    with pytest.raises(TypeError):
+        lib._dev_flags([1, 0, 1], 3, "free")

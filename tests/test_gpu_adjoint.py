@@ -164,3 +164,45 @@ def test_solve_and_outer_grad_vs_oracle(sta, orc):
     want = np.where(both, -lam.cpu().numpy()[rows] * xn[P.col], 0.0)
     assert np.array_equal(g, want)
     asm.close()
+
+
+def test_binding_checks_array_sizes_before_the_library(sta, orc):
+    """The library takes raw pointers; the binding rejects arrays of the wrong length or dtype
+    before any call, and the context is unchanged afterwards."""
+    import torch
+    wl = W.plain_small(seed=6)
+    asm = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu)
+    mask = wl.masks()[2]
+    asm.full_rebuild(mask)
+    n3, nnz = asm.n_rows, asm.nnz
+    dev = lambda n, dt=torch.float64: torch.zeros(n, dtype=dt, device="cuda")  # noqa: E731
+    free = torch.ones(n3, dtype=torch.bool, device="cuda")
+    for call, err in (
+            (lambda: sta.sta_spmv(asm.h, dev(n3 - 1)), ValueError),
+            (lambda: sta.sta_spmv(asm.h, dev(n3, torch.float32)), TypeError),
+            (lambda: sta.sta_spmv(asm.h, dev(n3).cpu()), TypeError),
+            (lambda: sta.sta_spmv(asm.h, dev(n3), val=dev(nnz - 9)), ValueError),
+            (lambda: sta.sta_solve(asm.h, dev(n3), free[:-3]), ValueError),
+            (lambda: sta.sta_solve(asm.h, dev(n3), free, x0=dev(n3 + 3)), ValueError),
+            (lambda: sta.sta_outer_grad(asm.h, dev(n3), dev(n3 - 3), free), ValueError),
+            (lambda: sta.sta_adjoint(asm.h, dev(nnz + 1)), ValueError),
+            (lambda: asm.full_rebuild(mask[:-1]), ValueError),
+            (lambda: asm.full_rebuild(torch.as_tensor(mask[:-1], device="cuda")), ValueError),
+            (lambda: asm.full_rebuild(torch.as_tensor(mask, device="cuda").float()), TypeError),
+            (lambda: asm.set_params(E=wl.E[:-1]), ValueError),
+            (lambda: asm.set_params(X=wl.X[:-1]), ValueError),
+            (lambda: asm.dyn_setup(1.0, 1e-2, np.zeros(n3 - 3)), ValueError),
+            (lambda: asm.dyn_setup(1.0, 1e-2, None, np.zeros(wl.n_nodes + 1)), ValueError)):
+        with pytest.raises(err):
+            call()
+    # nothing reached the library: the values are still those of the mask
+    P = orc.Pattern(wl.n_nodes, wl.tets)
+    Ke, _ = orc.element_all(wl.X, wl.tets, wl.E, wl.nu)
+    ref = P.rebuild(Ke, mask)
+    assert np.array_equal(asm.values().cpu().numpy().view(np.uint64), ref.view(np.uint64))
+    asm.dyn_setup(1.0, 1e-2)
+    with pytest.raises(ValueError):
+        asm.dyn_apply(dev(n3 - 1))
+    with pytest.raises(ValueError):
+        asm.dyn_set_state(u=np.zeros(n3 + 3))
+    asm.close()

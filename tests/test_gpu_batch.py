@@ -73,6 +73,8 @@ def test_batch_rejects_out_of_instance_ids(sta):
     bad = [W.make_edits(off=[insts[0].n_tets]), W.make_edits(), W.make_edits()]
     with pytest.raises(sta.StaError):
         batch.apply_edits(bad)
+    with pytest.raises(ValueError):  # one edit list per instance, checked in the binding
+        batch.apply_edits([W.make_edits(), W.make_edits()])
     batch.close()
 
 
