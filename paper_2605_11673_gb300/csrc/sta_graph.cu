@@ -8,6 +8,9 @@
 namespace sta {
 
 void graph_release(Ctx *c) {
+    for (int b = 0; b < 2; ++b) {  // a frame still reading its staging block finishes first
+        if (c->g_pending[b] && c->g_done[b]) cudaEventSynchronize(c->g_done[b]);
+    }
     for (int b = 0; b < 2; ++b) {
         if (c->g_streams[b]) cudaGraphExecDestroy(c->g_streams[b]);
         if (c->h_gframe[b]) cudaFreeHost(c->h_gframe[b]);
