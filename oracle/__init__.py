@@ -7,7 +7,10 @@ its binding) never imports, links or runs it, and the two share no code.
 Functions follow STA-FEM (arXiv 2605.11673): Eq. 8 for the assembled operator, Sec. 3.3 for
 the rebuild-equality invariant, Sec. 3.5 for the full_rebuild / local_recompute /
 streaming_update policies, Eqs. 1-7 and Algorithm 1 for the graph-Laplacian proxy operator,
-Eq. 9 (Sec. 6.2) for the implicit-Euler step with the lumped mass.  See sta_oracle.c for the element formula and summation order.
+Eq. 9 (Sec. 6.2) for the implicit-Euler step with the lumped mass.  See sta_oracle.c for the
+element formula and summation order.  Every function is pinned by tests/test_oracle_pins.py
+against closed forms, invariants, brute force or finite differences; none is "parity
+unpinned".
 """
 from __future__ import annotations
 

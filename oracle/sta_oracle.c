@@ -16,7 +16,13 @@
  *   - Sec. 3.3: the maintained matrix must equal a from-scratch rebuild on the active set.
  *   - Sec. 3.5 (Proposition 1): full_rebuild, local_recompute (rescan every incident active
  *     tetrahedron of each touched entry) and streaming_update (add / subtract element
- *     contributions of the edited tetrahedra).
+ *     contributions of the edited tetrahedra), the latter also in fixed point (orc_fx_*:
+ *     per-entry exponents, contributions quantised once, exact integer sums).
+ *   - Sec. 3.1-3.3, Eqs. 1-7, Algorithm 1: the graph-Laplacian proxy operator (orc_proxy_*:
+ *     edge multiplicities, thresholded adjacency, degrees, L + eps I).
+ *   - Sec. 6.2, Eq. 9: the lumped mass of the implicit-Euler loop (orc_lumped_mass).
+ *   - The adjoint (not in the paper): element parameter gradients, complex-step position
+ *     gradients (orc_element_param_grad, orc_element_x_grad_cs, orc_grad_all).
  *
  * Summation order (reading of "rebuild from scratch", Sec. 3.3): every CSR value is the
  * left-to-right fold, starting at +0.0, of the contributions of its active tetrahedra in
