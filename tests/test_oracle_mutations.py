@@ -98,3 +98,45 @@ def test_planted_oracle_mistake_fails_a_pin(name, tmp_path):
         assert failed > 0, f"mutation {name} passed every pin"
     finally:
         oracle.use_library(None)
+
+
+# Mistakes planted in the oracle's Python steps: the function's source is edited, executed in
+# the oracle module's namespace and swapped in for the duration of the pins.
+PY_MUTATIONS = {
+    "euler_drops_velocity": ("implicit_euler_step", "b = m3 * (u + h * v) + (h * h) * f",
+                             "b = m3 * u + (h * h) * f",
+                             [pins.test_implicit_euler_step_closed_forms]),
+    "euler_h_not_h_squared": ("implicit_euler_step", "A = (sp.diags(m3) + (h * h) * K.tocsr())",
+                              "A = (sp.diags(m3) + h * K.tocsr())",
+                              [pins.test_implicit_euler_step_closed_forms]),
+    "euler_velocity_sign": ("implicit_euler_step", "v1[idx] = (u1[idx] - u[idx]) / h",
+                            "v1[idx] = (u[idx] - u1[idx]) / h",
+                            [pins.test_implicit_euler_step_closed_forms]),
+    "euler_clamped_keep_u": ("implicit_euler_step",
+                             "u1 = np.where(np.repeat(np.asarray(clamped, bool), 3), 0.0, u)",
+                             "u1 = np.asarray(u)",
+                             [pins.test_implicit_euler_step_closed_forms]),
+    "dyn_free_ignores_mass": ("dyn_free", "& (np.asarray(mass) > 0)", "",
+                              [pins.test_implicit_euler_step_closed_forms]),
+    "adjoint_rule_sign": ("compliance_grad_val", "g = -u[rows] * u[cols]", "g = u[rows] * u[cols]",
+                          [pins.test_compliance_gradient_vs_central_fd]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTATIONS))
+def test_planted_python_oracle_mistake_fails_a_pin(name, monkeypatch):
+    import inspect
+    import textwrap
+    fname, old, new, checks = PY_MUTATIONS[name]
+    src = textwrap.dedent(inspect.getsource(getattr(oracle, fname)))
+    assert src.count(old) == 1, name
+    ns = dict(vars(oracle))
+    exec(compile(src.replace(old, new), f"<mutant {name}>", "exec"), ns)
+    monkeypatch.setattr(oracle, fname, ns[fname])
+    failed = 0
+    for check in checks:
+        try:
+            check(oracle)
+        except (AssertionError, ValueError, RuntimeError):
+            failed += 1
+    assert failed > 0, f"mutation {name} passed every pin"
