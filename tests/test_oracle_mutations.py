@@ -133,10 +133,13 @@ def test_planted_python_oracle_mistake_fails_a_pin(name, monkeypatch):
     ns = dict(vars(oracle))
     exec(compile(src.replace(old, new), f"<mutant {name}>", "exec"), ns)
     monkeypatch.setattr(oracle, fname, ns[fname])
+    import warnings
     failed = 0
     for check in checks:
         try:
-            check(oracle)
+            with warnings.catch_warnings():  # a mutant may make the solve singular
+                warnings.simplefilter("ignore")
+                check(oracle)
         except (AssertionError, ValueError, RuntimeError):
             failed += 1
     assert failed > 0, f"mutation {name} passed every pin"
