@@ -38,6 +38,7 @@ __global__ void k_local_rowptr(const int32_t *row_ptr, int64_t nrows, const int6
     }
 }
 
+// Instance-local column indices: each entry's column less its instance's first DOF.
 __global__ void k_local_col(const int32_t *col, int64_t nnz, const int64_t *nnz_off,
                             const int64_t *row_off, int k, int32_t *local_col) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;

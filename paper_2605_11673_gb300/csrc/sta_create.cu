@@ -63,6 +63,8 @@ __global__ void k_scan_tiles(const In *in, int64_t m, int64_t *out, int64_t *til
     if (threadIdx.x == blockDim.x - 1) tile_sums[blockIdx.x] = inc;
 }
 
+// Second pass of the exclusive scan: one CTA turns the per-tile totals, in tile order, into
+// exclusive tile offsets.
 __global__ void k_scan_sums(int64_t *tile_sums, int64_t ntiles) {
     __shared__ int64_t ws[32];
     __shared__ int64_t carry;
@@ -80,6 +82,7 @@ __global__ void k_scan_sums(int64_t *tile_sums, int64_t ntiles) {
     }
 }
 
+// Third pass: each element gets its tile's offset; out[0] = 0.
 __global__ void k_scan_fix(int64_t *out, int64_t m, const int64_t *tile_off) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < m) out[i + 1] += tile_off[blockIdx.x];
@@ -101,6 +104,8 @@ int exclusive_scan(Ctx *c, const In *in, int64_t m, int64_t *out, int64_t *tmp_t
 
 // ---------------------------------------------------------------- node -> tetrahedra
 
+// Number of superset tetrahedra incident to each node (the incidence the paper precomputes,
+// Sec. 3.3).
 __global__ void k_count_node_tets(const int4 *tets, int64_t T, int32_t *cnt) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -112,6 +117,8 @@ __global__ void k_count_node_tets(const int4 *tets, int64_t T, int32_t *cnt) {
     }
 }
 
+// Node -> tetrahedra lists: each tetrahedron appends its id to its four nodes' lists; the
+// append order is arbitrary, so the lists are sorted afterwards (k_sort_segments).
 __global__ void k_fill_node_tets(const int4 *tets, int64_t T, const int64_t *nt_ptr,
                                  int32_t *fill, int32_t *nt_list) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
@@ -169,6 +176,8 @@ __global__ void k_node_neighbors(const int4 *tets, int64_t n, const int64_t *nt_
     }
 }
 
+// Node adjacency in CSR form (adj_ptr, adj) from the per-node neighbour sets, and the row
+// node of every block.
 __global__ void k_adj_fill(int64_t n, const int64_t *nt_ptr, const int32_t *scratch,
                            const int64_t *adj_ptr64, int32_t *adj_ptr, int32_t *adj,
                            int32_t *block_node) {
@@ -199,6 +208,7 @@ __global__ void k_row_ptr(int64_t n, const int32_t *adj_ptr, int32_t *row_ptr) {
     }
 }
 
+// Column indices: block g = (a, b) fills columns 3b .. 3b+2 of the three rows of node a.
 __global__ void k_col(int64_t nblocks, const int32_t *block_node, const int32_t *adj_ptr,
                       const int32_t *adj, int32_t *col) {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nblocks;
@@ -252,6 +262,7 @@ __global__ void k_block_off(int64_t nblocks, const int32_t *block_node, const in
     }
 }
 
+// 1 for the blocks (a, b) with b >= a: the blocks that own a fold unit.
 __global__ void k_upper_flags(int64_t nblocks, const int32_t *block_node, const int32_t *adj,
                               int32_t *upper) {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nblocks;
@@ -374,12 +385,14 @@ __global__ void k_unit_meta(int64_t nblocks, const int32_t *block_node, const in
     }
 }
 
+// Narrowing copy of node -> tetrahedron offsets (at most 4 n_tets < 2^29: they fit int32).
 __global__ void k_to_i32(const int64_t *in, int64_t m, int32_t *out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x)
         out[i] = (int32_t)in[i];
 }
 
+// p[0 .. m) = v.
 __global__ void k_fill_i32(int32_t *p, int64_t m, int32_t v) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x)

@@ -71,6 +71,8 @@ __device__ __forceinline__ double node_mass(int32_t a, const int32_t *__restrict
     return m;
 }
 
+// Lumped mass of every node: the fold of its active tetrahedra's quarter masses, ascending
+// tetrahedron id, from +0.0.
 __global__ void k_dyn_mass_all(int64_t n, const int32_t *__restrict__ nt_ptr,
                                const int32_t *__restrict__ nt_list, const uint8_t *__restrict__ mask,
                                const double *__restrict__ qmass, double *__restrict__ mass) {
