@@ -170,3 +170,28 @@ def test_binding_array_checks(lib):
         lib._dev(np.zeros(6), 6, "x")
     with pytest.raises(TypeError):
         lib._dev_flags([1, 0, 1], 3, "free")
+
+
+def test_size_limits_rejected_on_the_host(lib):
+    """Sizes whose indices would overflow the int32 pattern or the 31-bit element-cache offsets
+    are rejected with STA_ERANGE before any array is read or any device work (no GPU needed)."""
+    import ctypes as C
+    L = lib.load_library()
+    x = np.zeros(12)
+    t = np.array([0, 1, 2, 3], np.int32)
+    one = np.ones(1)
+    h = C.c_void_p()
+    P = lambda a: a.ctypes.data  # noqa: E731
+    # n_tets >= 2^27 (the arrays are never read: the size check comes first)
+    assert L.sta_create(P(x), 4, P(t), 1 << 27, P(one), P(one), None, None,
+                        C.byref(h)) == lib.STA_ERANGE
+    assert h.value is None
+    # 3 n_nodes + 1 beyond int32 (no tetrahedra, so nothing is read)
+    assert L.sta_create(P(x), (1 << 31) // 3 + 1, None, 0, None, None, None, None,
+                        C.byref(h)) == lib.STA_ERANGE
+    assert L.sta_proxy_create(1 << 27, P(t), 1 << 27, 0.0, None, C.byref(h)) == lib.STA_ERANGE
+    assert L.sta_proxy_create((1 << 31) - 1, None, 0, 0.0, None, C.byref(h)) == lib.STA_ERANGE
+    assert b"n_nodes" in L.sta_last_error()
+    # negative sizes
+    assert L.sta_create(P(x), -1, None, 0, None, None, None, None, C.byref(h)) == lib.STA_EINVAL
+    assert L.sta_graph_enable(None, 0, None) == lib.STA_EINVAL
