@@ -62,17 +62,25 @@ def short(name: str) -> str:
     return re.sub(r"\(.*", "", name)[:48]
 
 
+# nanoseconds per time unit, in both spellings ncu prints (launch-list CSV, raw page)
+NS_PER = {"ns": 1.0, "nsecond": 1.0, "us": 1e3, "usecond": 1e3, "ms": 1e6, "msecond": 1e6,
+          "s": 1e9, "second": 1e9}
+
+
 def launches(path: str) -> str:
-    rows = list(csv.reader(open(path)))
+    with open(path) as fh:
+        rows = list(csv.reader(fh))
     hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
     hdr = rows[hi]
     ki, mi, vi = hdr.index("Kernel Name"), hdr.index("Metric Name"), hdr.index("Metric Value")
-    tot = collections.defaultdict(lambda: [0, 0.0])
+    ui = hdr.index("Metric Unit") if "Metric Unit" in hdr else None
+    tot = collections.defaultdict(lambda: [0, 0.0])  # kernel -> [launches, total ns]
     for r in rows[hi + 1:]:
         if len(r) > vi and r[mi] == "gpu__time_duration.sum":
             k = short(r[ki])
+            scale = NS_PER.get(r[ui], 1.0) if ui is not None else 1.0
             tot[k][0] += 1
-            tot[k][1] += float(r[vi].replace(",", ""))
+            tot[k][1] += float(r[vi].replace(",", "")) * scale
     total = sum(t for _, t in tot.values())
     out = [f"{'kernel':44s} {'launches':>8s} {'total_ms':>9s} {'share':>7s}"]
     for k, (n, t) in sorted(tot.items(), key=lambda kv: -kv[1][1]):
@@ -112,7 +120,7 @@ def traffic(rep: str, kernel: str, workload: str, out_json: str, command: str = 
     rd = _bytes(r[col["dram__bytes_read.sum"]], units[col["dram__bytes_read.sum"]])
     wr = _bytes(r[col["dram__bytes_write.sum"]], units[col["dram__bytes_write.sum"]])
     t = float(r[col["gpu__time_duration.sum"]].replace(",", ""))
-    t_us = t / 1e3 if units[col["gpu__time_duration.sum"]] == "nsecond" else t
+    t_us = t * NS_PER.get(units[col["gpu__time_duration.sum"]], 1e3) / 1e3
     rec = {"kernel": short(r[ki]), "workload": workload, "source_sha": rebuild_source_sha(),
            "sources": list(REBUILD_SOURCES), "dram_bytes_read": rd, "dram_bytes_write": wr,
            "dram_bytes_per_launch": rd + wr, "duration_us_cold": t_us, "command": command}
