@@ -84,8 +84,8 @@ void sta_default_options(sta_options *opt);
  * active set is empty and all values are +0.0; call sta_full_rebuild with the initial mask
  * (Algorithm 1 "a_0").  Synchronises `stream`.  Errors: STA_EINVAL for a bad id, a repeated
  * node or a tetrahedron with det <= 0 (its index is in sta_last_error()); STA_ERANGE when
- * nnz or 16 * n_tets exceeds int32 or n_tets >= 2^31 / 84 (25,565,281: 31-bit offsets into the
- * element cache); STA_ENOMEM; STA_ECUDA.
+ * nnz or 16 * n_tets exceeds int32 or n_tets > 25,565,281 (84 n_tets < 2^31: 31-bit offsets
+ * into the element cache); STA_ENOMEM; STA_ECUDA.
  */
 int sta_create(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
                const double *young, const double *poisson, const sta_options *opt,

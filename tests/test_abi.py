@@ -186,6 +186,9 @@ def test_size_limits_rejected_on_the_host(lib):
     assert L.sta_create(P(x), 4, P(t), 1 << 27, P(one), P(one), None, None,
                         C.byref(h)) == lib.STA_ERANGE
     assert h.value is None
+    # element-cache offsets are 31-bit: 84 doubles per tetrahedron, so at most 25,565,281 tets
+    assert L.sta_create(P(x), 4, P(t), 25_565_282, P(one), P(one), None, None,
+                        C.byref(h)) == lib.STA_ERANGE
     # 3 n_nodes + 1 beyond int32 (no tetrahedra, so nothing is read)
     assert L.sta_create(P(x), (1 << 31) // 3 + 1, None, 0, None, None, None, None,
                         C.byref(h)) == lib.STA_ERANGE
