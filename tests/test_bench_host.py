@@ -1,6 +1,10 @@
 """Host logic of bench.py (no GPU): the clock record parsed from nvidia-smi samples, and the
-DRAM traffic record tied to the rebuild kernel's source."""
+ncu records (DRAM traffic, FP64 instructions per tet) used only while they match the current
+sources of their kernel."""
+import json
+
 import bench
+import ncu_summary
 
 
 def test_clock_samples_parse():
@@ -18,7 +22,28 @@ def test_clock_samples_parse():
     assert bench.ClockSampler.parse("n/a, n/a, n/a, n/a, a, b, c, d") is None
 
 
-def test_traffic_record_tied_to_the_kernel_source():
-    # the committed record of the prefractured block was taken on the current rebuild source
-    assert bench.traffic_from_profile("prefractured_block") == 412_581_632.0
-    assert bench.traffic_from_profile("no_such_workload") is None
+def _write_record(d, kernel, workload, sha, **extra):
+    rec = dict({"kernel": kernel, "workload": workload, "source_sha": sha}, **extra)
+    (d / f"{kernel}_{workload}.json").write_text(json.dumps(rec))
+
+
+def test_records_used_only_on_the_current_kernel_source(tmp_path):
+    cur = ncu_summary.source_sha("k_fold_flat")
+    _write_record(tmp_path, "k_fold_flat", "wl", cur, dram_bytes_per_launch=123.0)
+    _write_record(tmp_path, "k_fold_flat", "old", "0" * 16, dram_bytes_per_launch=456.0)
+    assert bench.traffic_from_profile("wl", tmp_path) == 123.0
+    assert bench.traffic_from_profile("old", tmp_path) is None  # stale hash
+    assert bench.traffic_from_profile("missing", tmp_path) is None
+    _write_record(tmp_path, "k_elements", "wl", ncu_summary.source_sha("k_elements"),
+                  fp64_inst_per_unit=300.0)
+    _write_record(tmp_path, "k_adjoint", "wl", "f" * 16, fp64_inst_per_unit=900.0)
+    assert bench.fp64_per_tet("k_elements", "wl", tmp_path) == 300.0
+    assert bench.fp64_per_tet("k_adjoint", "wl", tmp_path) is None
+
+
+def test_source_hash_covers_the_kernel_and_its_layout():
+    # the rebuild's traffic depends on the unit order that create builds
+    assert "sta_create.cu" in ncu_summary.KERNEL_SOURCES["k_fold_flat"]
+    for k, srcs in ncu_summary.KERNEL_SOURCES.items():
+        assert all((ncu_summary.CSRC / f).exists() for f in srcs), k
+    assert ncu_summary.source_sha("k_elements") != ncu_summary.source_sha("k_fold_flat")

@@ -1,6 +1,6 @@
 """Host logic of the profile summaries (no GPU, no ncu run): the launch-list table of an
 `ncu --metrics gpu__time_duration.sum --csv` log."""
-from paper_2605_11673_gb300 import ncu_summary as N
+import ncu_summary as N
 
 CSV = '''==PROF== Connected to process 1
 "ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size","Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"
