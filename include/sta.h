@@ -118,6 +118,28 @@ int sta_refold(sta_ctx *ctx, void *stream);
 int sta_set_launch(sta_ctx *ctx, int32_t block_threads, int32_t blocks_per_sm);
 
 /*
+ * sta_set_rebuild_form -- how the full rebuild (sta_full_rebuild, sta_refold; Sec. 3.5) writes
+ * the values; the values are the same bits in every form.
+ *  STA_REBUILD_FUSED:     one fold kernel writes every value, +0.0 for the entries without an
+ *                         active contributor.  Suits a superset that is mostly active.
+ *  STA_REBUILD_ZERO_FILL: a coalesced fill sets every value to +0.0 while the tiles of fold
+ *                         units with an active contributor are flagged from the mask; the fold
+ *                         then visits only the flagged tiles (and, when eps != 0, the diagonal
+ *                         ones).  Suits a superset that is mostly inactive (preallocated
+ *                         refinement children, split copies).  Takes 4 more bytes of device
+ *                         memory per fold unit and 2 per tile of 32 fold entries (at create).
+ *  STA_REBUILD_AUTO:      (default) ZERO_FILL while fewer than 40% of the tetrahedra are
+ *                         active, else FUSED; decided when the rebuild is issued (in graph mode:
+ *                         when sta_graph_enable captures it).
+ * A launch choice of the library with no counterpart in the paper.  Not allowed while graph
+ * mode is on (STA_ESTATE); STA_EINVAL for another value.
+ */
+#define STA_REBUILD_AUTO 0
+#define STA_REBUILD_FUSED 1
+#define STA_REBUILD_ZERO_FILL 2
+int sta_set_rebuild_form(sta_ctx *ctx, int32_t form);
+
+/*
  * sta_apply_edits -- one frame of the streaming update (Sec. 3.2; Algorithm 1 receive /
  * update mask / per-tet update; Sec. 3.5 local_recompute made bitwise): applies the edits to
  * the mask, marks every block of the pattern touched by an edited tetrahedron (its 16 node
@@ -211,12 +233,11 @@ int sta_spmv(sta_ctx *ctx, const double *val, const double *x, double *y, void *
  * sta_apply_edits_noalloc -- the same streaming update as sta_apply_edits, for callers that
  * must not allocate (no counterpart in the paper).  sta_apply_edits may grow a pinned host
  * buffer and a device buffer on its first call or when a frame edits more tetrahedra than
- * before; a frame loop that must never stall on cudaMalloc, a process whose GPU memory is
- * held by a framework's caching allocator, or work about to be captured into a CUDA graph
- * cannot allow that.  This variant calls no allocator: its per-call scratch (edited-tet list,
- * touched-block list, counters) is one fixed device array of about
- * 68 x STA_NOALLOC_MAX_EDITED bytes (2.2 MB) that every GPU loading the library holds until
- * the process exits.  Arguments, validation, results and errors are those of
+ * before; a frame loop that must never stall on cudaMalloc, or a process whose GPU memory is
+ * held by a framework's caching allocator, cannot allow that.  This variant calls no
+ * allocator: its per-call scratch (edited-tet list, touched-unit list, counters) is one
+ * fixed device array of 44 x STA_NOALLOC_MAX_EDITED + 32 bytes (about 1.4 MB) that every GPU
+ * loading the library holds until the process exits.  Arguments, validation, results and errors are those of
  * sta_apply_edits, plus:
  *  - at most STA_NOALLOC_MAX_EDITED edited tetrahedra per call (a swap counts two); more
  *    is rejected with STA_ERANGE before any device work;

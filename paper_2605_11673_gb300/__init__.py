@@ -32,11 +32,14 @@ EXPORTED = (
     "sta_batch_create", "sta_batch_size", "sta_batch_instance", "sta_batch_apply_edits",
     "sta_graph_enable", "sta_graph_disable", "sta_set_policy", "sta_proxy_create",
     "sta_proxy_state", "sta_dyn_setup", "sta_dyn_step", "sta_dyn_state", "sta_dyn_set_state",
-    "sta_dyn_apply", "sta_solve", "sta_outer_grad",
+    "sta_dyn_apply", "sta_solve", "sta_outer_grad", "sta_set_rebuild_form",
 )
 STA_NOALLOC_MAX_EDITED = 32768
 STA_POLICY_REFOLD = 0
 STA_POLICY_FIXED = 1
+STA_REBUILD_AUTO = 0
+STA_REBUILD_FUSED = 1
+STA_REBUILD_ZERO_FILL = 2
 
 
 class StaError(RuntimeError):
@@ -87,6 +90,7 @@ def load_library(path: Path | str | None = None):
     L.sta_adjoint.argtypes = [_p, _p, _p, _p, _p, _p]
     L.sta_spmv.argtypes = [_p, _p, _p, _p, _p]
     L.sta_set_launch.argtypes = [_p, C.c_int32, C.c_int32]
+    L.sta_set_rebuild_form.argtypes = [_p, C.c_int32]
     L.sta_batch_create.argtypes = [C.c_int32, _p, _p, _p, _p, _p, _p, _P(sta_options), _p, _P(_p)]
     L.sta_batch_size.argtypes = [_p, _P(C.c_int32)]
     L.sta_batch_instance.argtypes = [_p, C.c_int32, _P(_p), _P(_p), _P(_p), _P(_i64), _P(_i64),
@@ -473,6 +477,10 @@ def sta_set_launch(h: int, block_threads: int = 0, blocks_per_sm: int = 0) -> No
     _check(load_library().sta_set_launch(h, int(block_threads), int(blocks_per_sm)))
 
 
+def sta_set_rebuild_form(h: int, form: int = STA_REBUILD_AUTO) -> None:
+    _check(load_library().sta_set_rebuild_form(h, int(form)))
+
+
 def sta_graph_enable(h: int, max_edited: int, stream=None) -> None:
     _check(load_library().sta_graph_enable(h, int(max_edited), _stream_handle(stream)))
 
@@ -602,6 +610,9 @@ class Assembler:
 
     def set_launch(self, block_threads: int = 0, blocks_per_sm: int = 0):
         sta_set_launch(self.h, block_threads, blocks_per_sm)
+
+    def set_rebuild_form(self, form: int = STA_REBUILD_AUTO):
+        sta_set_rebuild_form(self.h, form)
 
     def graph_enable(self, max_edited: int, stream=None):
         sta_graph_enable(self.h, max_edited, stream)

@@ -266,9 +266,9 @@ int sta_full_rebuild(sta_ctx *x, const uint8_t *mask, int mask_on_device, void *
             std::vector<uint8_t> hm((size_t)c->T);
             STA_CUDA_TRY(cudaMemcpyAsync(hm.data(), mask, (size_t)c->T, cudaMemcpyDeviceToHost, s));
             STA_CUDA_TRY(cudaStreamSynchronize(s));
-            set_host_mask(c, hm.data(), x->h_mask);
+            c->n_active = set_host_mask(c, hm.data(), x->h_mask);
         } else {
-            set_host_mask(c, mask, x->h_mask);
+            c->n_active = set_host_mask(c, mask, x->h_mask);
         }
         STA_CUDA_TRY(cudaMemcpyAsync(c->mask, x->h_mask, (size_t)c->T, cudaMemcpyHostToDevice, s));
         STA_CUDA_TRY(cudaEventRecord(x->h2d_done, s));
@@ -290,6 +290,15 @@ int sta_set_launch(sta_ctx *x, int32_t block_threads, int32_t blocks_per_sm) {
     if (x->c.graph_on) return fail(STA_ESTATE, "disable graph mode before changing the launch shape");
     x->c.block_threads = block_threads ? block_threads : 128;
     x->c.blocks_per_sm = blocks_per_sm;
+    return STA_OK;
+}
+
+int sta_set_rebuild_form(sta_ctx *x, int32_t form) {
+    if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    if (form != STA_REBUILD_AUTO && form != STA_REBUILD_FUSED && form != STA_REBUILD_ZERO_FILL)
+        return fail(STA_EINVAL, "form must be STA_REBUILD_AUTO, _FUSED or _ZERO_FILL");
+    if (x->c.graph_on) return fail(STA_ESTATE, "disable graph mode before changing the rebuild form");
+    x->c.rebuild_form = form;
     return STA_OK;
 }
 
@@ -362,7 +371,7 @@ int sta_apply_edits(sta_ctx *x, const sta_edit *edits, int64_t n_edits, void *st
     const uint8_t gen = c->stamp_gen;
     uint8_t *ts = c->tstate.data();
     int32_t *stage = frame_edited(h);
-    int64_t k = 0, e = 0;
+    int64_t k = 0, e = 0, dact = 0;  // dact: change of the active count
     const char *why = nullptr;
     for (; e < n_edits; ++e) {
         if (e + 16 < n_edits) {  // the per-tet state is accessed at random: fetch it ahead
@@ -382,10 +391,12 @@ int sta_apply_edits(sta_ctx *x, const sta_edit *edits, int64_t n_edits, void *st
             if (!(s1 & TS_ACTIVE)) { why = "deactivating an inactive tet"; break; }
             ts[E.tet] = gen;
             stage[k++] = E.tet;
+            --dact;
         } else if (E.op == STA_ACTIVATE) {
             if (s1 & TS_ACTIVE) { why = "activating an active tet"; break; }
             ts[E.tet] = (uint8_t)(TS_ACTIVE | gen);
             stage[k++] = (int32_t)((uint32_t)E.tet | 0x80000000u);
+            ++dact;
         } else {
             if (E.tet2 < 0 || E.tet2 >= c->T) { why = "tet2 out of range"; break; }
             const uint8_t s2 = ts[E.tet2];
@@ -406,6 +417,7 @@ int sta_apply_edits(sta_ctx *x, const sta_edit *edits, int64_t n_edits, void *st
         }
         return fail(STA_EINVAL, "edit " + std::to_string(e) + ": " + why);
     }
+    c->n_active += dact;
 
     // header (count, zeroed counters) before the list: in graph mode the captured kernels read
     // the host-mapped block itself; otherwise block and list go to the device in one copy

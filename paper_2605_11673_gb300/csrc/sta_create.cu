@@ -595,6 +595,28 @@ int build_pattern(Ctx *c, cudaStream_t s) {
         unit_order(hcnt, hmin, hdiag, rn, htiles);
         c->ntiles = (int64_t)htiles.size();
         STA_TRY(dev_alloc(c, &c->ftile, c->ntiles));
+        // per unit (new ids) its first tile | (it also reaches the next tile) << 31, and per
+        // tile whether it is of diagonal units: the zero-fill rebuild's tile flags
+        {
+            std::vector<int32_t> hut(nunits, -1);
+            std::vector<uint8_t> htd(c->ntiles);
+            for (int64_t ti = 0; ti < c->ntiles; ++ti) {
+                const int4 t = htiles[ti];
+                const int per = (t.y >> 4) & 1 ? FOLD_TASKS_DIAG : FOLD_TASKS_PAIR;
+                const int64_t ulast = t.x + ((t.y & 15) + (t.y >> 5) - 1) / per;
+                htd[ti] = (uint8_t)((t.y >> 4) & 1);
+                for (int64_t u = t.x; u <= ulast; ++u)
+                    hut[u] = hut[u] < 0 ? (int32_t)ti : (int32_t)(hut[u] | INT32_MIN);
+            }
+            STA_TRY(dev_alloc(c, &c->utile, nunits));
+            STA_TRY(dev_alloc(c, &c->tdiag, c->ntiles));
+            STA_TRY(dev_alloc(c, &c->tflag, c->ntiles));
+            STA_CUDA_TRY(cudaMemcpyAsync(c->utile, hut.data(), sizeof(int32_t) * nunits,
+                                         cudaMemcpyHostToDevice, s));
+            STA_CUDA_TRY(cudaMemcpyAsync(c->tdiag, htd.data(), (size_t)c->ntiles,
+                                         cudaMemcpyHostToDevice, s));
+            STA_CUDA_TRY(cudaStreamSynchronize(s));  // host vectors go out of scope
+        }
         STA_CUDA_TRY(cudaMemcpyAsync(c->ftile, htiles.data(), sizeof(int4) * c->ntiles,
                                      cudaMemcpyHostToDevice, s));
         STA_CUDA_TRY(cudaMemcpyAsync(rn_dev, rn.data(), sizeof(int32_t) * nunits,

@@ -135,6 +135,8 @@ struct Ctx {
     double eps = 0.0;
     int block_threads = 256;
     int blocks_per_sm = 0;
+    int rebuild_form = STA_REBUILD_AUTO;  // sta_set_rebuild_form
+    int64_t n_active = 0;                 // active tetrahedra (host mirror count)
     int num_sms = 0;
     int device = 0;
 
@@ -159,6 +161,11 @@ struct Ctx {
     int64_t ntiles = 0;
     int4 *ftile = nullptr;         // ntiles: rebuild fold tiles {first unit, q0 | diag << 4 |
                                    //   entries << 5, code range of the tile's units}
+    // zero-fill rebuild (sta_rebuild.cu): per unit its first tile | reaches the next << 31;
+    // per tile whether its units are diagonal, and its flag "fold this tile"
+    int32_t *utile = nullptr;      // nunits
+    uint8_t *tdiag = nullptr;      // ntiles
+    uint8_t *tflag = nullptr;      // ntiles
     int4 *bmeta = nullptr;         // nunits: {value offset of (a,b), rs_a << 1 | diagonal, c0, c1}
     int2 *bmirror = nullptr;       // nunits: {value offset of (b,a), rs_b}
     int32_t *ccode = nullptr;      // 10 T: unit contributor words (word_offset), ascending tet id
@@ -281,7 +288,8 @@ int launch_elements(Ctx *c, bool active_only, cudaStream_t s);   // sta_element.
 int launch_expand_elements(Ctx *c, const int32_t *ids, int64_t n, double *out, cudaStream_t s);
 int launch_adjoint(Ctx *c, const double *gval, double *dE, double *dnu, double *dX, cudaStream_t s);
 int launch_spmv(Ctx *c, const double *val, const double *x, double *y, cudaStream_t s);
-int launch_rebuild(Ctx *c, cudaStream_t s);                      // sta_assemble.cu
+int launch_rebuild(Ctx *c, cudaStream_t s);                      // sta_rebuild.cu
+int rebuild_form_of(const Ctx *c);  // the form the next rebuild takes (AUTO resolved)
 int launch_stream_frame(Ctx *c, FrameHeader *frame, int64_t cap, cudaStream_t s);  // sta_stream.cu
 // the same with the edited list, its count and the counters at separate addresses (the graph
 // mode's host-mapped frames keep their counters in device memory)

@@ -2,11 +2,10 @@
 //
 // sta_apply_edits may allocate: its first call, and any call with more edited tetrahedra
 // than before, grows a pinned host buffer and a device buffer.  Some callers cannot allow
-// that -- a frame loop that must never hit cudaMalloc's implicit device synchronisation, a
-// process whose device memory is owned by a framework's caching allocator, code about to be
-// captured into a CUDA graph.  This variant keeps its per-call scratch (edited-tet list,
-// touched-block list, counters) in one file-scope device array of fixed size, so it calls
-// no allocator at all.
+// that -- a frame loop that must never hit cudaMalloc's implicit device synchronisation, or a
+// process whose device memory is owned by a framework's caching allocator.  This variant
+// keeps its per-call scratch (edited-tet list, touched-unit list, counters) in one
+// file-scope device array of fixed size, so it calls no allocator at all.
 #include <mutex>
 
 #include "sta_internal.cuh"
@@ -14,9 +13,11 @@
 namespace {
 
 constexpr int64_t kMaxEdited = STA_NOALLOC_MAX_EDITED;
-constexpr int64_t kMaxTouched = 16 * kMaxEdited;  // an edited tetrahedron touches 16 blocks
-// layout: counters (4 x u64) | edited tets (kMaxEdited x i32) | touched units (16 x that; an
-// edited tetrahedron touches 10)
+// Every writer of the touched list (k_stream_claim, k_fx_claim, k_proxy_claim) appends at
+// most one entry per unit slot of an edited tetrahedron, and a tetrahedron has 10 slots (4
+// diagonal, 6 node pairs).
+constexpr int64_t kMaxTouched = 10 * kMaxEdited;
+// layout: counters (4 x u64) | edited tets (kMaxEdited x i32) | touched units (kMaxTouched x i32)
 constexpr size_t kCountersBytes = 4 * sizeof(unsigned long long);
 constexpr size_t kScratchBytes =
     kCountersBytes + sizeof(int32_t) * (size_t)kMaxEdited + sizeof(int32_t) * (size_t)kMaxTouched;
@@ -46,7 +47,7 @@ extern "C" int sta_apply_edits_noalloc(sta_ctx *x, const sta_edit *edits, int64_
         return fail(STA_EINVAL, "the context's device must be current for this call");
     if (dev < 0 || dev >= kMaxDevices) return fail(STA_EINVAL, "device index out of range");
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_dev_addr[dev]) {  // one-time set-up on this device (do it before any capture)
+    if (!g_dev_addr[dev]) {  // one-time set-up on this device
         void *p = nullptr;
         STA_CUDA_TRY(cudaGetSymbolAddress(&p, g_scratch));
         g_dev_addr[dev] = static_cast<unsigned char *>(p);
@@ -87,9 +88,11 @@ extern "C" int sta_apply_edits_noalloc(sta_ctx *x, const sta_edit *edits, int64_
         if (E.op == STA_DEACTIVATE) {
             g_host_stage[k++] = E.tet;
             ts_set_active(c, E.tet, false);
+            --c->n_active;
         } else if (E.op == STA_ACTIVATE) {
             g_host_stage[k++] = (int32_t)((uint32_t)E.tet | 0x80000000u);
             ts_set_active(c, E.tet, true);
+            ++c->n_active;
         } else {
             g_host_stage[k++] = E.tet;
             g_host_stage[k++] = (int32_t)((uint32_t)E.tet2 | 0x80000000u);

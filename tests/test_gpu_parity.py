@@ -118,6 +118,58 @@ def test_rebuild_device_mask_and_eps(sta, orc):
     asm.close()
 
 
+@pytest.mark.parametrize("form", ["fused", "zero_fill"])
+def test_rebuild_forms_bitwise(sta, orc, form):
+    """Both rebuild forms give the oracle's values bit for bit: on a mostly inactive superset
+    (a small refinement hierarchy) and a mostly active one, with eps = 0 and eps != 0 (the
+    zero-fill form still writes eps on the diagonal of units without an active contributor),
+    after streaming, under the fixed-point policy, and captured in graph mode."""
+    code = {"fused": sta.STA_REBUILD_FUSED, "zero_fill": sta.STA_REBUILD_ZERO_FILL}[form]
+    for wl in (W.refinement_hierarchy(N=6, radius=0.3, frames=4),
+               W.prefractured_block(N=8, sites=5, frames=4)):
+        P = orc.Pattern(wl.n_nodes, wl.tets)
+        Ke, bad = orc.element_all(wl.X, wl.tets, wl.E, wl.nu)
+        assert bad == 0
+        masks = wl.masks()
+        for eps in (0.0, 0.5):
+            asm = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu, eps=eps)
+            asm.set_rebuild_form(code)
+            asm.full_rebuild(masks[0])
+            _assert_bitwise(_vals(asm), P.rebuild(Ke, masks[0], eps), f"{wl.name} {form} rebuild")
+            for f, ed in enumerate(wl.frames):
+                asm.apply_edits(ed)
+                streamed = _vals(asm)
+                asm.refold()
+                ref = P.rebuild(Ke, masks[f + 1], eps)
+                _assert_bitwise(streamed, ref, f"{wl.name} {form} frame {f}: stream")
+                _assert_bitwise(_vals(asm), ref, f"{wl.name} {form} frame {f}: refold")
+            asm.graph_enable(max(int(e.shape[0] + (e[:, 0] == 2).sum()) for e in wl.frames))
+            asm.full_rebuild(masks[2])
+            _assert_bitwise(_vals(asm), P.rebuild(Ke, masks[2], eps), f"{wl.name} {form} graph")
+            asm.graph_disable()
+            asm.set_policy(sta.STA_POLICY_FIXED)
+            _, fv = P.fx_rebuild(Ke, P.fx_exponents(Ke), masks[2], eps)
+            _assert_bitwise(_vals(asm), fv, f"{wl.name} {form} fixed-point rebuild")
+            asm.refold()
+            _assert_bitwise(_vals(asm), fv, f"{wl.name} {form} fixed-point refold")
+            asm.close()
+
+
+def test_rebuild_form_rejections(sta):
+    wl = W.plain_small(seed=3, frames=1)
+    asm = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu)
+    with pytest.raises(sta.StaError) as e:
+        asm.set_rebuild_form(3)
+    assert e.value.status == sta.STA_EINVAL
+    asm.graph_enable(64)
+    with pytest.raises(sta.StaError) as e:
+        asm.set_rebuild_form(sta.STA_REBUILD_FUSED)
+    assert e.value.status == sta.STA_ESTATE
+    asm.graph_disable()
+    asm.set_rebuild_form(sta.STA_REBUILD_AUTO)
+    asm.close()
+
+
 @pytest.mark.parametrize("seed", [0, 1, 2, 3, 4])
 def test_streaming_plain_small_every_frame(sta, orc, seed):
     _run_stream(sta, orc, W.plain_small(seed=seed))
