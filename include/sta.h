@@ -139,6 +139,10 @@ int sta_set_launch(sta_ctx *ctx, int32_t block_threads, int32_t blocks_per_sm);
 #define STA_REBUILD_ZERO_FILL 2
 int sta_set_rebuild_form(sta_ctx *ctx, int32_t form);
 
+/* The form (STA_REBUILD_FUSED or STA_REBUILD_ZERO_FILL) a rebuild issued now would take, AUTO
+ * resolved for the current mask. */
+int sta_get_rebuild_form(const sta_ctx *ctx, int32_t *form);
+
 /*
  * sta_apply_edits -- one frame of the streaming update (Sec. 3.2; Algorithm 1 receive /
  * update mask / per-tet update; Sec. 3.5 local_recompute made bitwise): applies the edits to

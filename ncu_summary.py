@@ -7,13 +7,14 @@ program those captures run.  Measurement tooling beside bench.py, not part of th
         compare shares, not absolutes)
     python ncu_summary.py full <report.ncu-rep>
         key counters of every captured launch of an `ncu --set full` report
-    python ncu_summary.py record <report.ncu-rep> <kernel> <workload> <out.json> \
-            [--units N] [--command "..."]
-        counters of the first launch of <kernel> (DRAM bytes, duration and, when captured, the
-        FP64 thread instructions; --units: the work items that launch processed, e.g. active
-        tetrahedra, for per-unit figures), recorded with the hash of the sources the kernel
-        and its data layout are built from (KERNEL_SOURCES): bench.py uses a record only while
-        that hash matches the current sources
+    python ncu_summary.py record <report.ncu-rep> <key> <workload> <out.json> \
+            --kernels <regex> [--units N] [--command "..."]
+        counters summed over the captured launches of the kernels matching <regex> -- one
+        launch sequence, e.g. a rebuild's k_tile_flags + k_fold_flat (DRAM bytes, duration and,
+        when captured, the FP64 thread instructions; --units: the work items it processed,
+        e.g. active tetrahedra, for per-unit figures) -- recorded as <key>_<workload> with the
+        hash of the sources the kernels and their data layout are built from
+        (KERNEL_SOURCES[key]): bench.py uses a record only while that hash matches
     python ncu_summary.py run <workload> [--stream] [--proxy] [--elements]
         the program to capture: one context on the workload (prefractured, refinement,
         refinement_r040; --proxy: the graph-Laplacian proxy operator), sta_full_rebuild of
@@ -39,7 +40,7 @@ CSRC = ROOT / "paper_2605_11673_gb300" / "csrc"
 # current only while these hash to the value it was taken with (the rebuild's traffic also
 # depends on the unit order and tiles that create builds)
 KERNEL_SOURCES = {
-    "k_fold_flat": ("sta_rebuild.cu", "sta_fold.cuh", "sta_create.cu", "sta_internal.cuh"),
+    "rebuild": ("sta_rebuild.cu", "sta_fold.cuh", "sta_create.cu", "sta_internal.cuh"),
     "k_elements": ("sta_element.cu", "sta_internal.cuh"),
     "k_adjoint": ("sta_element.cu", "sta_internal.cuh"),
 }
@@ -141,35 +142,46 @@ def _bytes(value: str, unit: str) -> float:
     return float(value.replace(",", "")) * scale
 
 
-def record(rep: str, kernel: str, workload: str, out_json: str, units: float = 0.0,
+def record(rep: str, key: str, workload: str, out_json: str, kernels: str, units: float = 0.0,
            command: str = "") -> dict:
+    """Sum the counters of every captured launch whose kernel name matches `kernels` (the
+    capture holds one launch sequence, e.g. the rebuild's k_tile_flags + k_fold_flat) and write
+    the record <key>_<workload>.json, tied to the hash of KERNEL_SOURCES[key]."""
     hdr, unit_row, rows = _raw(rep)
     ki = hdr.index("Kernel Name")
-    r = next(r for r in rows if short(r[ki]).split("<")[0] == kernel)
+    picked = [r for r in rows if re.search(kernels, short(r[ki]))]
+    if not picked:
+        raise SystemExit(f"no launch of {kernels!r} in {rep}")
 
-    def val(name):
+    def val(r, name):
         i = hdr.index(name)
         return float(r[i].replace(",", "")), unit_row[i]
 
-    rd = _bytes(*val("dram__bytes_read.sum"))
-    wr = _bytes(*val("dram__bytes_write.sum"))
-    t, tu = val("gpu__time_duration.sum")
-    rec = {"kernel": short(r[ki]), "workload": workload, "source_sha": source_sha(kernel),
-           "sources": list(KERNEL_SOURCES[kernel]), "dram_bytes_read": rd,
-           "dram_bytes_write": wr, "dram_bytes_per_launch": rd + wr,
-           "duration_us_cold": t * NS_PER.get(tu, 1e3) / 1e3}
+    rec = {"key": key, "kernels": [short(r[ki]) for r in picked], "workload": workload,
+           "source_sha": source_sha(key), "sources": list(KERNEL_SOURCES[key])}
+    rd = sum(_bytes(*val(r, "dram__bytes_read.sum")) for r in picked)
+    wr = sum(_bytes(*val(r, "dram__bytes_write.sum")) for r in picked)
+    t = sum(val(r, "gpu__time_duration.sum")[0] * NS_PER.get(val(r, "gpu__time_duration.sum")[1], 1e3)
+            for r in picked) / 1e3
+    rec.update({"dram_bytes_read": rd, "dram_bytes_write": wr, "dram_bytes_per_launch": rd + wr,
+                "duration_us_cold": t})
+    rec["per_kernel"] = {short(r[ki]): {
+        "dram_bytes": _bytes(*val(r, "dram__bytes_read.sum")) + _bytes(*val(r, "dram__bytes_write.sum")),
+        "duration_us_cold": val(r, "gpu__time_duration.sum")[0]
+        * NS_PER.get(val(r, "gpu__time_duration.sum")[1], 1e3) / 1e3} for r in picked}
     if all(m in hdr for m in FP64_INST):
-        fp64 = sum(val(m)[0] for m in FP64_INST)
+        fp64 = sum(val(r, m)[0] for r in picked for m in FP64_INST)
         rec["fp64_thread_inst"] = fp64
         for m in FP64_INST:
-            rec[m] = val(m)[0]
+            rec[m] = sum(val(r, m)[0] for r in picked)
         if units:
             rec["units"] = units
             rec["fp64_inst_per_unit"] = fp64 / units
     for m in ("sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active",
-              "smsp__issue_active.avg.pct_of_peak_sustained_active"):
+              "smsp__issue_active.avg.pct_of_peak_sustained_active",
+              "smsp__inst_executed.sum"):
         if m in hdr:
-            rec[m] = val(m)[0]
+            rec[m] = [val(r, m)[0] for r in picked]
     rec["command"] = command
     Path(out_json).write_text(json.dumps(rec, indent=1) + "\n")
     return rec
@@ -219,8 +231,9 @@ def main(argv) -> None:
     sub.add_parser("launches").add_argument("csv")
     sub.add_parser("full").add_argument("report")
     a = sub.add_parser("record")
-    for name in ("report", "kernel", "workload", "out_json"):
+    for name in ("report", "key", "workload", "out_json"):
         a.add_argument(name)
+    a.add_argument("--kernels", required=True, help="regex of the kernels to sum")
     a.add_argument("--units", type=float, default=0.0)
     a.add_argument("--command", default="")
     args = ap.parse_args(argv)
@@ -231,8 +244,8 @@ def main(argv) -> None:
     elif args.cmd == "full":
         print(full(args.report))
     else:
-        print(json.dumps(record(args.report, args.kernel, args.workload, args.out_json,
-                                args.units, args.command), indent=1))
+        print(json.dumps(record(args.report, args.key, args.workload, args.out_json,
+                                args.kernels, args.units, args.command), indent=1))
 
 
 if __name__ == "__main__":

@@ -33,6 +33,7 @@ EXPORTED = (
     "sta_graph_enable", "sta_graph_disable", "sta_set_policy", "sta_proxy_create",
     "sta_proxy_state", "sta_dyn_setup", "sta_dyn_step", "sta_dyn_state", "sta_dyn_set_state",
     "sta_dyn_apply", "sta_solve", "sta_outer_grad", "sta_set_rebuild_form",
+    "sta_get_rebuild_form",
 )
 STA_NOALLOC_MAX_EDITED = 32768
 STA_POLICY_REFOLD = 0
@@ -91,6 +92,7 @@ def load_library(path: Path | str | None = None):
     L.sta_spmv.argtypes = [_p, _p, _p, _p, _p]
     L.sta_set_launch.argtypes = [_p, C.c_int32, C.c_int32]
     L.sta_set_rebuild_form.argtypes = [_p, C.c_int32]
+    L.sta_get_rebuild_form.argtypes = [_p, _P(C.c_int32)]
     L.sta_batch_create.argtypes = [C.c_int32, _p, _p, _p, _p, _p, _p, _P(sta_options), _p, _P(_p)]
     L.sta_batch_size.argtypes = [_p, _P(C.c_int32)]
     L.sta_batch_instance.argtypes = [_p, C.c_int32, _P(_p), _P(_p), _P(_p), _P(_i64), _P(_i64),
@@ -481,6 +483,12 @@ def sta_set_rebuild_form(h: int, form: int = STA_REBUILD_AUTO) -> None:
     _check(load_library().sta_set_rebuild_form(h, int(form)))
 
 
+def sta_get_rebuild_form(h: int) -> int:
+    f = C.c_int32(0)
+    _check(load_library().sta_get_rebuild_form(h, C.byref(f)))
+    return f.value
+
+
 def sta_graph_enable(h: int, max_edited: int, stream=None) -> None:
     _check(load_library().sta_graph_enable(h, int(max_edited), _stream_handle(stream)))
 
@@ -613,6 +621,10 @@ class Assembler:
 
     def set_rebuild_form(self, form: int = STA_REBUILD_AUTO):
         sta_set_rebuild_form(self.h, form)
+
+    def rebuild_form(self) -> int:
+        """STA_REBUILD_FUSED or STA_REBUILD_ZERO_FILL: the form of a rebuild issued now."""
+        return sta_get_rebuild_form(self.h)
 
     def graph_enable(self, max_edited: int, stream=None):
         sta_graph_enable(self.h, max_edited, stream)

@@ -1,9 +1,11 @@
-"""Launch-shape autotuner for the fold kernels.
+"""Launch autotuner for the full rebuild.
 
-Sweeps the fold's CTA size (64, 128, 256 threads) and CTAs per SM (0 = occupancy maximum, or a
-fixed count) on a given context, timing the full refold with CUDA events after an L2 flush,
-and keeps the fastest shape in a JSON cache keyed by GPU name and the context's sizes.  The
-shape changes only the schedule: values are identical for every shape.
+Sweeps the rebuild form (fused, or zero fill + fold of the flagged tiles; sta_set_rebuild_form),
+the fold's CTA size (64, 128, 256 threads) and CTAs per SM (0 = occupancy maximum, or a fixed
+count) on a given context, timing the full refold with CUDA events after an L2 flush, and keeps
+the fastest choice in a JSON cache keyed by GPU name, the context's sizes and its active
+fraction (in tenths: the best form depends on how much of the superset is active).  The choice
+changes only the schedule: values are identical for every form and shape.
 """
 from __future__ import annotations
 
@@ -13,11 +15,14 @@ from pathlib import Path
 
 CACHE = Path(os.environ.get("STA_AUTOTUNE_CACHE",
                             Path(__file__).resolve().parent / "_build" / "autotune.json"))
-SHAPES = [(t, b) for t in (64, 128, 256) for b in (0, 1, 2, 3, 4, 6, 8)]
+FUSED, ZERO_FILL = 1, 2  # sta.h STA_REBUILD_FUSED, STA_REBUILD_ZERO_FILL
+SHAPES = [(f, t, b) for f in (FUSED, ZERO_FILL) for t in (64, 128, 256)
+          for b in (0, 1, 2, 3, 4, 6, 8)]
 
 
-def key_for(gpu_name: str, sizes: dict) -> str:
-    return f"{gpu_name}|T={sizes['n_tets']}|blocks={sizes['n_blocks']}|nnz={sizes['nnz']}"
+def key_for(gpu_name: str, sizes: dict, active_tenths: int = 10) -> str:
+    return (f"{gpu_name}|T={sizes['n_tets']}|blocks={sizes['n_blocks']}|nnz={sizes['nnz']}"
+            f"|active={active_tenths}/10")
 
 
 def load_cache(path: Path = CACHE) -> dict:
@@ -44,9 +49,15 @@ def pick_best(timings: dict) -> tuple:
     return best
 
 
+def apply(asm, choice) -> None:
+    form, threads, per_sm = choice
+    asm.set_rebuild_form(form)
+    asm.set_launch(threads, per_sm)
+
+
 def measure(asm, shape, repeats: int = 11, flush_bytes: int = 256 << 20) -> float:
     import torch
-    asm.set_launch(*shape)
+    apply(asm, shape)
     flush = torch.empty(flush_bytes, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     times = []
@@ -65,9 +76,12 @@ def measure(asm, shape, repeats: int = 11, flush_bytes: int = 256 << 20) -> floa
 
 def tune(asm, repeats: int = 11, use_cache: bool = True, path: Path = CACHE,
          shapes=None) -> tuple:
-    """Best (block_threads, blocks_per_sm) for this context; applied to it and cached."""
+    """Best (form, block_threads, blocks_per_sm) for this context at its current mask; applied
+    to it and cached."""
     import torch
-    key = key_for(torch.cuda.get_device_name(), asm.sizes())
+    sizes = asm.sizes()
+    tenths = int(10 * int(asm.mask().sum().item()) // max(1, sizes["n_tets"]))
+    key = key_for(torch.cuda.get_device_name(), sizes, tenths)
     cache = load_cache(path) if use_cache else {}
     if use_cache and key in cache:
         shape = tuple(cache[key]["shape"])
@@ -75,7 +89,7 @@ def tune(asm, repeats: int = 11, use_cache: bool = True, path: Path = CACHE,
         timings = {s: measure(asm, s, repeats) for s in (shapes or SHAPES)}
         shape = pick_best(timings)
         cache[key] = {"shape": list(shape), "ms": timings[shape],
-                      "all": {f"{t}x{b}": ms for (t, b), ms in timings.items()}}
+                      "all": {f"{f}:{t}x{b}": ms for (f, t, b), ms in timings.items()}}
         save_cache(cache, path)
-    asm.set_launch(*shape)
+    apply(asm, shape)
     return shape

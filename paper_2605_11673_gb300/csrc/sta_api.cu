@@ -302,6 +302,12 @@ int sta_set_rebuild_form(sta_ctx *x, int32_t form) {
     return STA_OK;
 }
 
+int sta_get_rebuild_form(const sta_ctx *x, int32_t *form) {
+    if (!x || !form) return fail(STA_EINVAL, "NULL argument");
+    *form = rebuild_form_of(&x->c);
+    return STA_OK;
+}
+
 int sta_refold(sta_ctx *x, void *stream) {
     if (!x) return fail(STA_EINVAL, "ctx is NULL");
     if (x->c.graph_on) {

@@ -3,16 +3,18 @@ from paper_2605_11673_gb300 import autotune as A
 
 
 def test_pick_best_and_ties():
-    t = {(128, 0): 1.0, (64, 2): 0.5, (256, 1): 0.5}
-    assert A.pick_best(t) == (64, 2)  # first in SHAPES order among equal times
+    t = {(A.FUSED, 128, 0): 1.0, (A.FUSED, 64, 2): 0.5, (A.ZERO_FILL, 64, 1): 0.5}
+    assert A.pick_best(t) == (A.FUSED, 64, 2)  # first in SHAPES order among equal times
     assert A.pick_best({}) is None
+    assert {f for f, _, _ in A.SHAPES} == {A.FUSED, A.ZERO_FILL}
 
 
 def test_cache_roundtrip(tmp_path):
     p = tmp_path / "c.json"
     assert A.load_cache(p) == {}
-    k = A.key_for("GPU", {"n_tets": 1, "n_blocks": 2, "nnz": 18})
-    A.save_cache({k: {"shape": [64, 3]}}, p)
-    assert A.load_cache(p)[k]["shape"] == [64, 3]
+    k = A.key_for("GPU", {"n_tets": 1, "n_blocks": 2, "nnz": 18}, 3)
+    assert k != A.key_for("GPU", {"n_tets": 1, "n_blocks": 2, "nnz": 18}, 9)
+    A.save_cache({k: {"shape": [2, 64, 3]}}, p)
+    assert A.load_cache(p)[k]["shape"] == [2, 64, 3]
     p.write_text("not json")
     assert A.load_cache(p) == {}

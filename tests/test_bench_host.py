@@ -28,9 +28,9 @@ def _write_record(d, kernel, workload, sha, **extra):
 
 
 def test_records_used_only_on_the_current_kernel_source(tmp_path):
-    cur = ncu_summary.source_sha("k_fold_flat")
-    _write_record(tmp_path, "k_fold_flat", "wl", cur, dram_bytes_per_launch=123.0)
-    _write_record(tmp_path, "k_fold_flat", "old", "0" * 16, dram_bytes_per_launch=456.0)
+    cur = ncu_summary.source_sha("rebuild")
+    _write_record(tmp_path, "rebuild", "wl", cur, dram_bytes_per_launch=123.0)
+    _write_record(tmp_path, "rebuild", "old", "0" * 16, dram_bytes_per_launch=456.0)
     assert bench.traffic_from_profile("wl", tmp_path) == 123.0
     assert bench.traffic_from_profile("old", tmp_path) is None  # stale hash
     assert bench.traffic_from_profile("missing", tmp_path) is None
@@ -43,7 +43,7 @@ def test_records_used_only_on_the_current_kernel_source(tmp_path):
 
 def test_source_hash_covers_the_kernel_and_its_layout():
     # the rebuild's traffic depends on the unit order that create builds
-    assert "sta_create.cu" in ncu_summary.KERNEL_SOURCES["k_fold_flat"]
+    assert "sta_create.cu" in ncu_summary.KERNEL_SOURCES["rebuild"]
     for k, srcs in ncu_summary.KERNEL_SOURCES.items():
         assert all((ncu_summary.CSRC / f).exists() for f in srcs), k
-    assert ncu_summary.source_sha("k_elements") != ncu_summary.source_sha("k_fold_flat")
+    assert ncu_summary.source_sha("k_elements") != ncu_summary.source_sha("rebuild")
