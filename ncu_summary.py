@@ -137,9 +137,9 @@ def full(rep: str) -> str:
     return "\n".join(out)
 
 
-def _bytes(value: str, unit: str) -> float:
+def _bytes(value, unit: str) -> float:
     scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}[unit]
-    return float(value.replace(",", "")) * scale
+    return float(str(value).replace(",", "")) * scale
 
 
 def record(rep: str, key: str, workload: str, out_json: str, kernels: str, units: float = 0.0,

@@ -27,3 +27,20 @@ def test_launch_table_sums_and_shares_in_any_time_unit(tmp_path):
     # 120,000 ns + 80 us = 0.200 ms; 0.05 ms of fill: shares 80% and 20%
     assert fold.split()[-3:] == ["2", "0.200", "80.0%"]
     assert fill.split()[-3:] == ["1", "0.050", "20.0%"]
+
+
+def test_record_sums_the_launches_of_one_sequence(tmp_path, monkeypatch):
+    hdr = ["ID", "Kernel Name", "dram__bytes_read.sum", "dram__bytes_write.sum",
+           "gpu__time_duration.sum"]
+    units = ["", "", "Mbyte", "Kbyte", "usecond"]
+    rows = [["0", "void sta::(anonymous namespace)::k_tile_flags(const unsigned char *)", "10", "200", "40"],
+            ["1", "void sta::(anonymous namespace)::k_fold_flat<4, 0, 1>(sta::FoldArgs)", "150", "24,000", "60"],
+            ["2", "void sta::(anonymous namespace)::k_stream_claim(const int *)", "1", "1", "9"]]
+    monkeypatch.setattr(N, "_raw", lambda rep: (hdr, units, rows))
+    out = tmp_path / "rebuild_wl.json"
+    rec = N.record("x.ncu-rep", "rebuild", "wl", str(out), "k_fold_flat|k_tile_flags")
+    assert rec["kernels"] == ["k_tile_flags", "k_fold_flat<4, 0, 1>"]
+    assert rec["dram_bytes_read"] == 160e6 and rec["dram_bytes_write"] == 200e3 + 24e6
+    assert rec["duration_us_cold"] == 100.0
+    assert rec["source_sha"] == N.source_sha("rebuild") and out.exists()
+    assert N.current_record("rebuild", "wl", tmp_path)["dram_bytes_per_launch"] == 160e6 + 24.2e6
