@@ -1,5 +1,7 @@
 """Adjoint form: the CUDA adjoint kernel and the autograd chain against the oracle's reference
-gradients (analytic dE/dnu, complex-step dX) and against central finite differences.
+gradients (analytic dE/dnu, complex-step dX) entry by entry, each against its own element's
+magnitude, and against central finite differences (directional, and on single elements and
+nodes).
 
 Workload for the chain: 20^3 hexes x 6 = 48,000 tets, lognormal E, bottom layer clamped,
 uniform downward traction on the top face, gradient of the compliance f^T u after frame 12
@@ -23,11 +25,51 @@ def sta():
     return P
 
 
-def _rel(a, b):
-    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+def element_scales(orc, X, tets, E, nu, mask, gv, P):
+    """Per-entry magnitudes for the adjoint comparisons, from the oracle's element matrices.
+    With G the upstream gradient gathered on an element (G_pq = gv at the element's CSR entry
+    (p, q)) and K = lambda A + mu B its matrix split into the lambda and mu parts:
+      dE_e  = sum G K / E           scale sum |G| |K| / E
+      dnu_e = sum G (lambda' A + mu' B)   scale sum |G| (|lambda'| |A| + |mu'| |B|)
+      dX_v  = sum over the active elements at v of sum G dK/dx_v   scale sum |G| |K| / h_e
+    (h_e = V_e^(1/3): dK/dx is K over a length).  A rounding error of the adjoint's arithmetic
+    is a small multiple of these, whatever the cancellation inside an element; 0 on an
+    inactive element."""
+    Ke, bad = orc.element_all(X, tets, E, nu)
+    assert bad == 0
+    G = np.abs(gv[P.scat])                                   # (T, 144)
+    act = mask.astype(bool)
+    sK = (G * np.abs(Ke)).sum(1) * act
+    B = orc.element_all(X, tets, np.full(len(E), 2.0), np.zeros(len(E)))[0]   # lambda 0, mu 1
+    K1 = orc.element_all(X, tets, np.ones(len(E)), np.full(len(E), 0.25))[0]  # lambda = mu = 0.4
+    A = (K1 - 0.4 * B) / 0.4
+    dlam = E * (1 + 2 * nu ** 2) / ((1 + nu) ** 2 * (1 - 2 * nu) ** 2)
+    dmu = -E / (2 * (1 + nu) ** 2)
+    s_nu = (G * (np.abs(dlam)[:, None] * np.abs(A) + np.abs(dmu)[:, None] * np.abs(B))).sum(1) * act
+    d = X[tets[:, 1:]] - X[tets[:, :1]]
+    h = (np.abs(np.linalg.det(d)) / 6.0) ** (1.0 / 3.0)
+    s_X = np.zeros(len(X))
+    for a in range(4):
+        np.add.at(s_X, tets[:, a], sK / h)
+    return sK / E, s_nu, s_X
+
+
+def assert_per_entry(got, ref, scale, tol, what):
+    """|got - ref| <= tol (|ref| + scale) entry by entry (scale broadcast over columns)."""
+    got, ref = np.asarray(got), np.asarray(ref)
+    sc = scale if np.ndim(scale) == np.ndim(ref) else scale[:, None]
+    lim = tol * (np.abs(ref) + sc)
+    bad = np.argwhere(np.abs(got - ref) > lim)
+    if bad.size:
+        k = tuple(bad[0])
+        raise AssertionError(f"{what}: {len(bad)} entries beyond {tol} x (|ref| + scale); first "
+                             f"{k}: {got[k]!r} vs {ref[k]!r} (scale {np.broadcast_to(sc, ref.shape)[k]!r})")
 
 
 def test_adjoint_kernel_vs_oracle(sta, orc):
+    """The adjoint kernel against the oracle's gradients -- analytic dE and dnu, complex-step dX
+    (an independent derivative, exact to rounding) -- entry by entry, each within 1e-12 of its
+    own element's magnitude."""
     import torch
     wl = W.plain_small(seed=5)
     rng = np.random.default_rng(0)
@@ -37,13 +79,15 @@ def test_adjoint_kernel_vs_oracle(sta, orc):
     asm = sta.Assembler(wl.X, wl.tets, E, nu)
     asm.full_rebuild(mask)
     P = orc.Pattern(wl.n_nodes, wl.tets)
-    gv = rng.standard_normal(P.nnz)
-    dE, dnu, dX = sta.sta_adjoint(asm.h, torch.as_tensor(gv, device="cuda"))
+    # an upstream gradient spanning six orders of magnitude over the pattern
+    gv = rng.standard_normal(P.nnz) * 10.0 ** rng.uniform(-3, 3, P.nnz)
+    dE, dnu, dX = (a.cpu().numpy() for a in sta.sta_adjoint(asm.h, torch.as_tensor(gv, device="cuda")))
     oE, onu, oX = P.grad_all(wl.X, E, nu, mask, gv)
-    assert np.all(dE.cpu().numpy()[mask == 0] == 0)
-    assert _rel(dE.cpu().numpy(), oE) < 1e-11
-    assert _rel(dnu.cpu().numpy(), onu) < 1e-11
-    assert _rel(dX.cpu().numpy(), oX) < 1e-11
+    sE, snu, sX = element_scales(orc, wl.X, wl.tets, E, nu, mask, gv, P)
+    assert np.all(dE[mask == 0] == 0) and np.all(dnu[mask == 0] == 0)
+    assert_per_entry(dE, oE, sE, 1e-12, "dE")
+    assert_per_entry(dnu, onu, snu, 1e-12, "dnu")
+    assert_per_entry(dX, oX, sX, 1e-12, "dX vs complex step")
     asm.close()
 
 
@@ -88,6 +132,10 @@ def chain(sta, orc):
     L = loss(E, nu, X)
     L.backward()
     g = {"E": E.grad.cpu().numpy(), "nu": nu.grad.cpu().numpy(), "X": X.grad.cpu().numpy()}
+    # the same chain with the solves to 1e-14, for the per-entry checks
+    E14, nu14, X14 = (t.detach().clone().requires_grad_() for t in (E, nu, X))
+    loss(E14, nu14, X14, tol=1e-14).backward()
+    g14 = {"E": E14.grad.cpu().numpy(), "nu": nu14.grad.cpu().numpy(), "X": X14.grad.cpu().numpy()}
     # oracle: element matrices, rebuild, sparse direct solve, adjoint rule, reference grads
     P = orc.Pattern(wl.n_nodes, wl.tets)
     Ke, bad = orc.element_all(wl.X, wl.tets, wl.E, wl.nu)
@@ -96,16 +144,52 @@ def chain(sta, orc):
     u_o = orc.solve_free(K, f_np, free_np)
     gv = orc.compliance_grad_val(P, u_o, free_np)
     oE, onu, oX = P.grad_all(wl.X, wl.E, wl.nu, mask, gv)
-    yield {"wl": wl, "mask": mask, "loss": loss, "L": float(L.detach()), "g": g, "L_o": float(f_np @ u_o),
-           "o": {"E": oE, "nu": onu, "X": oX}, "asm": asm}
+    yield {"wl": wl, "mask": mask, "loss": loss, "L": float(L.detach()), "g": g, "g14": g14,
+           "L_o": float(f_np @ u_o), "o": {"E": oE, "nu": onu, "X": oX}, "asm": asm, "gv_o": gv,
+           "P": P}
     asm.close()
 
 
-def test_chain_matches_oracle_gradient(chain):
+def test_chain_matches_oracle_gradient(chain, orc):
+    """The whole GPU chain (assembly, CG to 1e-14, adjoint CG, adjoint kernel) against the
+    oracle's (assembly, sparse direct solve, adjoint rule, reference gradients), entry by entry
+    within 1e-7 of each element's own magnitude (the solves' difference, about 1e-9 relative to
+    u, enters each element's gradient through its u values)."""
     assert abs(chain["L"] - chain["L_o"]) <= 1e-9 * abs(chain["L_o"])
-    for k in ("E", "nu", "X"):
-        assert _rel(chain["g"][k], chain["o"][k]) < 1e-7, k
-    assert np.all(chain["g"]["E"][chain["mask"] == 0] == 0)
+    wl, mask = chain["wl"], chain["mask"]
+    g = chain["g14"]
+    sE, snu, sX = element_scales(orc, wl.X, wl.tets, wl.E, wl.nu, mask, chain["gv_o"], chain["P"])
+    assert_per_entry(g["E"], chain["o"]["E"], sE, 1e-7, "dL/dE")
+    assert_per_entry(g["nu"], chain["o"]["nu"], snu, 1e-7, "dL/dnu")
+    assert_per_entry(g["X"], chain["o"]["X"], sX, 1e-7, "dL/dX")
+    assert np.all(chain["g"]["E"][mask == 0] == 0)
+
+
+def test_chain_per_element_central_differences(chain):
+    """Central finite differences of the GPU chain's loss on single parameters: the 8 elements
+    with the largest |dL/dE| and, for the 4 nodes with the largest |dL/dX|, their largest
+    component; each within 1e-6 of the adjoint gradient.  Step: 1e-4 relative (a single element
+    changes the compliance by about its share of the strain energy, so a smaller step would
+    leave the difference at the solves' rounding; the truncation error at this step is about
+    1e-8 relative)."""
+    import torch
+    wl, loss, g = chain["wl"], chain["loss"], chain["g14"]
+    dev = "cuda"
+    base = {"E": wl.E, "nu": wl.nu, "X": wl.X}
+    picks = [("E", int(e), 1e-4 * wl.E[int(e)]) for e in np.argsort(-np.abs(g["E"]))[:8]]
+    for v in np.argsort(-np.abs(g["X"]).max(1))[:4]:
+        k = int(np.argmax(np.abs(g["X"][v])))
+        picks.append(("X", (int(v), k), 1e-4 / wl.meta["N"]))
+    for name, idx, h in picks:
+        Lpm = []
+        for sgn in (1.0, -1.0):
+            args = {k2: torch.as_tensor(v2.copy(), device=dev) for k2, v2 in base.items()}
+            args[name][idx] += sgn * h
+            with torch.no_grad():
+                Lpm.append(float(loss(args["E"], args["nu"], args["X"], tol=1e-14)))
+        fd = (Lpm[0] - Lpm[1]) / (2 * h)
+        an = float(g[name][idx])
+        assert abs(an - fd) <= 1e-6 * abs(fd), (name, idx, an, fd)
 
 
 def test_chain_vs_central_differences(chain):
