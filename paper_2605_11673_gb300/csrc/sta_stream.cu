@@ -13,23 +13,36 @@ namespace {
 // longest folds (diagonal units, ~24 contributions) set the latency, so here each lane folds ONE
 // matrix entry: a warp takes 3 listed units, lanes 9g .. 9g+8 fold the 9 entries (i, j) of
 // unit g (6 of them for a diagonal unit), and one FP64 instruction per step advances all 27
-// folds.  The unit's active codes are compacted (in list order) into shared memory first; each
-// step then loads one operand per lane (4 steps of loads in flight).  Operands, order and
-// operations are those of k_fold_flat, so the values are the same bits.
+// folds.  The unit's active codes are compacted (in list order) into shared memory first, 27
+// codes per step (three loads in flight per lane).  Then the element-cache runs of the active
+// contributors (48 B for a diagonal unit, 80 B for a pair; 16-byte aligned) are copied into
+// shared memory with 16-byte cp.async copies, all in flight at once, so a unit costs one round
+// trip for its operands however long its list; the fold reads them from there.  A unit with
+// more than ENT_SCAP active contributions loads its operands from global memory instead (4
+// steps in flight).  Operands, order and operations are those of k_fold_flat, so the values are
+// the same bits.
 // ------------------------------------------------------------------------------------------
 constexpr int ENT_UNITS = 3;    // units per warp round (27 lanes)
-constexpr int ENT_CAP = 96;     // active contributions staged per unit; larger units fold directly
+constexpr int ENT_CAP = 96;     // active contributions listed per unit; larger units fold directly
+constexpr int ENT_SCAP = 24;    // active contributions whose runs are staged in shared memory
 constexpr int ENT_WARPS = 4;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
 
 __global__ void __launch_bounds__(ENT_WARPS * 32)
 k_fold_entries(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *__restrict__ count,
                int32_t *__restrict__ owner) {
     __shared__ uint32_t sop_all[ENT_WARPS][ENT_UNITS][ENT_CAP];
+    __shared__ __align__(16) double stage_all[ENT_WARPS][ENT_UNITS][ENT_SCAP * 10];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int g = lane / 9, q = lane % 9;  // g == 3: lanes 27..31 idle
     const int qi = q / 3, qj = q % 3;
     uint32_t *sop = sop_all[wid][g < ENT_UNITS ? g : 0];
+    double *stage = stage_all[wid][g < ENT_UNITS ? g : 0];  // run j at stage[10 j]
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nitems = (int64_t)*count;
@@ -45,30 +58,58 @@ k_fold_entries(FoldArgs A, const int32_t *__restrict__ list, const unsigned long
             mir = __ldg(A.bmirror + u);
             if (q == 0) owner[u] = INT32_MAX;  // release the claim (all claims are done)
         }
-        // compact the unit's active contributors (as operand bases), 9 lanes striding over its list
+        // compact the unit's active contributors (as operand bases), 9 lanes striding over its
+        // list, three 9-code chunks loaded together and taken in list order
         int nact = 0;
         const int span = valid ? bm.w - bm.z : 0;
         const int max_span = __reduce_max_sync(FULL, span);
-        for (int c0 = 0; c0 < max_span; c0 += 9) {
-            const int c = c0 + q;
-            const int32_t code = (valid && c < span) ? __ldg(A.ccode + bm.z + c) : 0;
-            const unsigned m = __ballot_sync(FULL, code < 0);
-            const unsigned gm = (m >> (9 * g)) & 0x1ffu;
-            const int pos = nact + __popc(gm & ((1u << q) - 1u));
-            if (code < 0 && pos < ENT_CAP) sop[pos] = word_offset((uint32_t)code);
-            nact += __popc(gm);
+        const unsigned below_q = (1u << q) - 1u;
+        for (int c0 = 0; c0 < max_span; c0 += 27) {
+            int32_t k[3];
+#pragma unroll
+            for (int h = 0; h < 3; ++h) {
+                const int c = c0 + 9 * h + q;
+                k[h] = (valid && c < span) ? __ldg(A.ccode + bm.z + c) : 0;
+            }
+#pragma unroll
+            for (int h = 0; h < 3; ++h) {
+                const unsigned m = __ballot_sync(FULL, k[h] < 0);
+                const unsigned gm = (m >> (9 * g)) & 0x1ffu;
+                const int pos = nact + __popc(gm & below_q);
+                if (k[h] < 0 && pos < ENT_CAP) sop[pos] = word_offset((uint32_t)k[h]);
+                nact += __popc(gm);
+            }
         }
         __syncwarp();
         const bool big = valid && nact > ENT_CAP;
-        if (big && q == 0) fold_direct(A, bm, mir);  // rare: more active contributions than staged
+        if (big && q == 0) fold_direct(A, bm, mir);  // rare: more active contributions than listed
         const bool diag = (bm.y & 1) != 0;
         const bool mine = valid && !big && (!diag || q < 6);  // a diagonal unit folds 6 entries
-        const int n = mine ? nact : 0;
+        // stage the runs of the unit's active contributors (16-byte pieces: 3 of a 48-byte
+        // diagonal run, 5 of an 80-byte pair run), the unit's 9 lanes sharing the copies
+        const bool staged = valid && !big && nact <= ENT_SCAP;
+        if (staged) {
+            const int cpr = diag ? 3 : 5;
+            for (int kk = q; kk < nact * cpr; kk += 9) {
+                const int j = kk / cpr, p = kk - j * cpr;
+                cp_async16(stage + 10 * j + 2 * p, A.Ke + sop[j] + 2 * p);
+            }
+        }
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+        __syncwarp();
         double acc = 0.0;
+        const int ns = mine && staged ? nact : 0;
+        const int maxs = __reduce_max_sync(FULL, ns);
+        if (maxs > 0) {  // warp-uniform; the same operands in the same order as below
+            if (ns > 0) acc = plus_zero(stage[q]);  // the first contribution: +0.0 + v
+            for (int j = 1; j < maxs; ++j)
+                if (j < ns) acc += stage[10 * j + q];
+        }
+        const int n = mine && !staged ? nact : 0;  // longer lists: operands from global memory
         const int maxn = __reduce_max_sync(FULL, n);
 #define STA_LD(j) ((j) < n ? __ldg(A.Ke + sop[(j)] + q) : 0.0)
         if (maxn > 0) {  // warp-uniform guards, as in k_fold_flat
-            acc = plus_zero(STA_LD(0));  // the first contribution: +0.0 + v, no FP64 add
+            if (n > 0) acc = plus_zero(STA_LD(0));  // the first contribution: +0.0 + v
             double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
             if (maxn > 1) v0 = STA_LD(1);
             if (maxn > 2) v1 = STA_LD(2);
