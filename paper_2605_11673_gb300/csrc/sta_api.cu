@@ -56,6 +56,8 @@ static void free_ctx(sta_ctx *x) {
     if (x->c.h_frame) cudaFreeHost(x->c.h_frame);
     if (x->c.d_frame) cudaFree(x->c.d_frame);
     if (x->h_mask) cudaFreeHost(x->h_mask);
+    if (x->h_count) cudaFreeHost(x->h_count);
+    if (x->c.h_count_mapped) cudaFreeHost(x->c.h_count_mapped);
     if (x->h2d_done) cudaEventDestroy(x->h2d_done);
     if (x->c.g_cg) cudaGraphExecDestroy(x->c.g_cg);
     graph_release(&x->c);
@@ -181,8 +183,12 @@ int sta::create_impl(const double *nodes, int64_t n_nodes, const int32_t *tets, 
     c->tstate.assign((size_t)n_tets, 0);
     c->seen.assign((size_t)n_tets, 0);
     c->last_counters = c->counters;
-    if (cudaMallocHost((void **)&x->h_mask, (size_t)(n_tets > 0 ? n_tets : 1)) != cudaSuccess)
-        return bail(fail(STA_ENOMEM, "pinned mask buffer"));
+    if (cudaMallocHost((void **)&x->h_count, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost((void **)&x->h_mask, (size_t)(n_tets > 0 ? n_tets : 1)) != cudaSuccess ||
+        cudaHostAlloc((void **)&c->h_count_mapped, sizeof(unsigned long long),
+                      cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&c->d_count_mapped, c->h_count_mapped, 0) != cudaSuccess)
+        return bail(fail(STA_ENOMEM, "pinned host buffers"));
     *out = x;
     return STA_OK;
 }
@@ -240,7 +246,8 @@ extern "C" int sta_proxy_create(int64_t n_nodes, const int32_t *tets, int64_t n_
     c->tstate.assign((size_t)n_tets, 0);
     c->seen.assign((size_t)n_tets, 0);
     c->last_counters = c->counters;
-    if (cudaMallocHost((void **)&x->h_mask, (size_t)(n_tets > 0 ? n_tets : 1)) != cudaSuccess)
+    if (cudaMallocHost((void **)&x->h_count, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost((void **)&x->h_mask, (size_t)(n_tets > 0 ? n_tets : 1)) != cudaSuccess)
         return bail(fail(STA_ENOMEM, "pinned mask buffer"));
     *out = x;
     return STA_OK;
@@ -430,6 +437,9 @@ int sta_apply_edits(sta_ctx *x, const sta_edit *edits, int64_t n_edits, void *st
     h->m = m;
     h->cnt[0] = h->cnt[1] = h->cnt[2] = 0ull;
     c->last_edited = m;
+    // the fold kernel stores the frame's touched count into the host-mapped word (a frame
+    // without edits launches no kernel outside graph mode)
+    c->count_on_host = frame_counts_to_host(c) && (use_graph || m > 0);
     if (use_graph) {  // the captured sequence reads the host-mapped block itself: no copy call
         c->last_counters = c->d_gcnt + 4 * gb;
         std::atomic_thread_fence(std::memory_order_seq_cst);  // the block before the launch
@@ -449,11 +459,17 @@ int sta_apply_edits(sta_ctx *x, const sta_edit *edits, int64_t n_edits, void *st
 
 int sta_last_touched(sta_ctx *x, int64_t *touched_nnz, void *stream) {
     if (!x || !touched_nnz) return fail(STA_EINVAL, "NULL argument");
-    unsigned long long v = 0;
     cudaStream_t s = (cudaStream_t)stream;
-    STA_CUDA_TRY(cudaMemcpyAsync(&v, x->c.last_counters + 3, sizeof v, cudaMemcpyDeviceToHost, s));
+    if (x->c.count_on_host) {  // the frame's fold kernel stored it in host-mapped memory
+        STA_CUDA_TRY(cudaStreamSynchronize(s));
+        *touched_nnz = (int64_t)*reinterpret_cast<volatile unsigned long long *>(x->c.h_count_mapped);
+        return STA_OK;
+    }
+    // into a pinned word: a plain asynchronous copy (a pageable target is staged, and slower)
+    STA_CUDA_TRY(cudaMemcpyAsync(x->h_count, x->c.last_counters + 3, sizeof *x->h_count,
+                                 cudaMemcpyDeviceToHost, s));
     STA_CUDA_TRY(cudaStreamSynchronize(s));
-    *touched_nnz = (int64_t)v;
+    *touched_nnz = (int64_t)*x->h_count;
     return STA_OK;
 }
 

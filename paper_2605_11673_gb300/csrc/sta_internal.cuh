@@ -196,6 +196,10 @@ struct Ctx {
     int64_t edit_cap = 0;         // edited tetrahedra a frame block holds
     int64_t last_edited = 0;
     unsigned long long *last_counters = nullptr;  // device counters of the last frame
+    // host-mapped pinned word the re-fold streaming frame's fold kernel stores its touched-entry
+    // count into (h: host address, d: its device address); count_on_host: the last frame did
+    unsigned long long *h_count_mapped = nullptr, *d_count_mapped = nullptr;
+    bool count_on_host = false;
     uint8_t stamp_gen = 0;        // the sta_apply_edits call's stamp (1 .. 127), see tstate
 
     // graph-Laplacian proxy operator (sta_proxy.cu); its CSR is the node-level pattern
@@ -291,6 +295,8 @@ int launch_spmv(Ctx *c, const double *val, const double *x, double *y, cudaStrea
 int launch_rebuild(Ctx *c, cudaStream_t s);                      // sta_rebuild.cu
 int rebuild_form_of(const Ctx *c);  // the form the next rebuild takes (AUTO resolved)
 int launch_stream_frame(Ctx *c, FrameHeader *frame, int64_t cap, cudaStream_t s);  // sta_stream.cu
+// whether a streaming frame of this context stores its touched count into h_count_mapped
+bool frame_counts_to_host(const Ctx *c);
 // the same with the edited list, its count and the counters at separate addresses (the graph
 // mode's host-mapped frames keep their counters in device memory)
 int launch_stream_frame(Ctx *c, const int32_t *edited, const int64_t *m_dev,
@@ -326,4 +332,5 @@ struct sta_ctx {
     cudaEvent_t h2d_done = nullptr;
     bool h2d_pending = false;
     uint8_t *h_mask = nullptr;  // pinned staging for host masks, T bytes
+    unsigned long long *h_count = nullptr;  // pinned word: sta_last_touched's read-back
 };

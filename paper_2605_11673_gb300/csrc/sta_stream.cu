@@ -34,7 +34,7 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 
 __global__ void __launch_bounds__(ENT_WARPS * 32)
 k_fold_entries(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *__restrict__ count,
-               int32_t *__restrict__ owner) {
+               int32_t *__restrict__ owner, unsigned long long *host_count) {
     __shared__ uint32_t sop_all[ENT_WARPS][ENT_UNITS][ENT_CAP];
     __shared__ __align__(16) double stage_all[ENT_WARPS][ENT_UNITS][ENT_SCAP * 10];
     const unsigned FULL = 0xffffffffu;
@@ -47,6 +47,9 @@ k_fold_entries(FoldArgs A, const int32_t *__restrict__ list, const unsigned long
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nitems = (int64_t)*count;
     const bool has_eps = A.eps != 0.0;
+    // the frame's touched-entry count (count[2], final since the claim kernel ended) into the
+    // host-mapped word sta_last_touched reads
+    if (host_count && blockIdx.x == 0 && threadIdx.x == 0) *host_count = count[2];
     for (int64_t base = warp * ENT_UNITS; base < nitems; base += nwarps * ENT_UNITS) {  // warp-uniform
         const int64_t item = base + g;
         const bool valid = g < ENT_UNITS && item < nitems;
@@ -228,12 +231,12 @@ int persistent_grid(const Ctx *c, const void *kernel, int threads, int64_t items
 }
 
 int launch_fold_list(Ctx *c, const int32_t *list, const unsigned long long *count,
-                     int64_t max_items, cudaStream_t s) {
+                     int64_t max_items, cudaStream_t s, unsigned long long *host_count) {
     const int threads = ENT_WARPS * 32;
     // one unit per 9 lanes (3 per warp) for the largest possible list, at most the resident CTAs
     const int grid = persistent_grid(c, (const void *)k_fold_entries, threads,
                                      (max_items + ENT_UNITS - 1) / ENT_UNITS * 32);
-    k_fold_entries<<<grid, threads, 0, s>>>(fold_args(c), list, count, c->owner);
+    k_fold_entries<<<grid, threads, 0, s>>>(fold_args(c), list, count, c->owner, host_count);
     STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;
 }
@@ -275,8 +278,12 @@ int launch_stream_frame(Ctx *c, const int32_t *edited, const int64_t *m_dev,
     k_stream_claim<<<(unsigned)g, threads, 0, s>>>(edited, 0, m_dev, c->T, c->tunit, c->cslot,
                                                    c->ccode, c->mask, c->owner, c->touched, cnt);
     STA_CUDA_TRY(cudaGetLastError());
-    STA_TRY(launch_fold_list(c, c->touched, cnt + 1, 10 * (cap > 0 ? cap : 1), s));
+    STA_TRY(launch_fold_list(c, c->touched, cnt + 1, 10 * (cap > 0 ? cap : 1), s, c->d_count_mapped));
     return launch_dyn_mass_edited(c, edited, 0, m_dev, cap, s);
+}
+
+bool frame_counts_to_host(const Ctx *c) {
+    return c->op == STA_OP_ELASTICITY && c->policy == STA_POLICY_REFOLD && c->d_count_mapped;
 }
 
 int launch_stream_frame(Ctx *c, FrameHeader *frame, int64_t cap, cudaStream_t s) {
@@ -301,13 +308,14 @@ int launch_stream_scratch(Ctx *c, int64_t m, const int32_t *d_edited, int32_t *t
                                                        c->ccode, c->mask, c->owner, touched,
                                                        counters);
         STA_CUDA_TRY(cudaGetLastError());
-        STA_TRY(launch_fold_list(c, touched, counters + 1, 10 * m, s));
+        STA_TRY(launch_fold_list(c, touched, counters + 1, 10 * m, s, nullptr));
     }
     if (m > 0) STA_TRY(launch_dyn_mass_edited(c, d_edited, m, nullptr, m, s));
     // touched units and touched entries, for sta_last_touched
     STA_CUDA_TRY(cudaMemcpyAsync(c->counters + 1, counters + 1, 3 * sizeof(unsigned long long),
                                  cudaMemcpyDeviceToDevice, s));
     c->last_counters = c->counters;
+    c->count_on_host = false;  // read back from the device counters
     return STA_OK;
 }
 
