@@ -111,7 +111,8 @@ constexpr int FOLD_TASKS_PAIR = 9;
 // state << 31) right after the header.
 struct FrameHeader {
     int64_t m;                     // edited tetrahedra
-    unsigned long long cnt[3];     // touched units, unused, touched CSR entries
+    unsigned long long cnt[3];     // touched units, unused, touched CSR entries (the FP64
+                                   // re-fold counts its units as diagonal | pair << 32)
 };
 static_assert(sizeof(FrameHeader) == 32, "frame header layout");
 // counter view with the indices of Ctx::counters: [1] touched units, [3] touched entries

@@ -11,167 +11,203 @@ namespace {
 // ------------------------------------------------------------------------------------------
 // Entry-parallel fold of a list of units (streaming).  A frame's touched list is short and its
 // longest folds (diagonal units, ~24 contributions) set the latency, so here each lane folds ONE
-// matrix entry: a warp takes 3 listed units, lanes 9g .. 9g+8 fold the 9 entries (i, j) of
-// unit g (6 of them for a diagonal unit), and one FP64 instruction per step advances all 27
-// folds.  The unit's active codes are compacted (in list order) into shared memory first, 27
-// codes per step (three loads in flight per lane).  Then the element-cache runs of the active
-// contributors (48 B for a diagonal unit, 80 B for a pair; 16-byte aligned) are copied into
-// shared memory with 16-byte cp.async copies, all in flight at once, so a unit costs one round
-// trip for its operands however long its list; the fold reads them from there.  A unit with
-// more than ENT_SCAP active contributions loads its operands from global memory instead (4
-// steps in flight).  Operands, order and operations are those of k_fold_flat, so the values are
-// the same bits.
+// matrix entry, and one FP64 instruction per step advances a whole warp of folds.  The claim
+// kernel lists the two kinds of unit apart (diagonal units from the front of the list, pair
+// units from the back), so that a warp folds units of one kind: 5 diagonal units (lanes
+// 6g .. 6g+5 fold the 6 entries i <= j of unit g) or 3 pair units (lanes 9g .. 9g+8 fold the
+// 9 entries (i, j)).  A warp's step count is its longest fold, and on GB300 an FP64 warp
+// instruction holds the SM's FP64 pipe for about 16 cycles: mixing a ~24-contribution diagonal
+// unit with ~6-contribution pair units would leave most of those steps idle.
+// The unit's active codes are compacted (in list order) into shared memory first, three codes
+// per lane and step.  Then the element-cache runs of the active contributors (48 B for a
+// diagonal unit, 80 B for a pair; 16-byte aligned) are copied into shared memory with 16-byte
+// cp.async copies, all in flight at once, so a unit costs one round trip for its operands
+// however long its list; the fold reads them from there.  A unit with more than ENT_SCAP
+// active contributions loads its operands from global memory instead (4 steps in flight).
+// Operands, order and operations are those of k_fold_flat, so the values are the same bits.
 // ------------------------------------------------------------------------------------------
-constexpr int ENT_UNITS = 3;    // units per warp round (27 lanes)
-constexpr int ENT_CAP = 96;     // active contributions listed per unit; larger units fold directly
-constexpr int ENT_SCAP = 24;    // active contributions whose runs are staged in shared memory
+constexpr int ENT_DG = 5;      // diagonal units per warp round (6 lanes each: 30 lanes)
+constexpr int ENT_PG = 3;      // pair units per warp round (9 lanes each: 27 lanes)
+constexpr int ENT_DCAP = 64;   // listed active contributions of a diagonal unit (larger: direct)
+constexpr int ENT_PCAP = 96;   // the same for a pair unit
+constexpr int ENT_SCAP = 24;   // active contributions whose runs are staged in shared memory
 constexpr int ENT_WARPS = 4;
+constexpr int ENT_SOP = ENT_DG * ENT_DCAP > ENT_PG * ENT_PCAP ? ENT_DG * ENT_DCAP : ENT_PG * ENT_PCAP;
+constexpr int ENT_STAGE = ENT_DG * ENT_SCAP * 6;  // doubles per warp: = ENT_PG * ENT_SCAP * 10
+static_assert(ENT_DG * ENT_SCAP * 6 == ENT_PG * ENT_SCAP * 10, "stage shared by both kinds");
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
 }
 
-__global__ void __launch_bounds__(ENT_WARPS * 32)
-k_fold_entries(FoldArgs A, const int32_t *__restrict__ list, const unsigned long long *__restrict__ count,
-               int32_t *__restrict__ owner, unsigned long long *host_count) {
-    __shared__ uint32_t sop_all[ENT_WARPS][ENT_UNITS][ENT_CAP];
-    __shared__ __align__(16) double stage_all[ENT_WARPS][ENT_UNITS][ENT_SCAP * 10];
+// One warp round over units first .. first+NG-1 of one kind (k-th diagonal unit at list[k],
+// k-th pair unit at list[cap - 1 - k]); `sop`, `stage` are the warp's shared buffers.
+template <bool DIAG>
+__device__ __forceinline__ void fold_units(const FoldArgs &A, const int32_t *__restrict__ list,
+                                           int64_t first, int64_t n_units, int64_t cap,
+                                           int32_t *__restrict__ owner, uint32_t *sop_w,
+                                           double *stage_w, int lane, bool has_eps) {
+    constexpr int GW = DIAG ? 6 : 9;                 // lanes (entries) per unit
+    constexpr int NG = DIAG ? ENT_DG : ENT_PG;       // units per warp round
+    constexpr int CAP = DIAG ? ENT_DCAP : ENT_PCAP;  // listed active contributions
+    constexpr int RUN = DIAG ? 6 : 10;               // staged doubles per run (48 B, 80 B)
+    constexpr int CPR = DIAG ? 3 : 5;                // 16-byte copies per run
     const unsigned FULL = 0xffffffffu;
+    const int g = lane / GW, q = lane % GW;          // g == NG: idle lanes
+    const int64_t k = first + g;
+    const bool valid = g < NG && k < n_units;
+    uint32_t *sop = sop_w + (g < NG ? g : 0) * CAP;
+    double *stage = stage_w + (g < NG ? g : 0) * (ENT_SCAP * RUN);  // run j at stage[RUN j]
+    int4 bm = make_int4(0, 0, 0, 0);
+    int2 mir = make_int2(0, 0);
+    if (valid) {
+        const int32_t u = __ldg(list + (DIAG ? k : cap - 1 - k));
+        bm = __ldg(A.bmeta + u);
+        if (!DIAG) mir = __ldg(A.bmirror + u);
+        if (q == 0) owner[u] = INT32_MAX;  // release the claim (all claims are done)
+    }
+    // compact the unit's active contributors (as operand bases), its GW lanes striding over its
+    // list, three GW-code chunks loaded together and taken in list order
+    int nact = 0;
+    const int span = valid ? bm.w - bm.z : 0;
+    const int max_span = __reduce_max_sync(FULL, span);
+    const unsigned below_q = (1u << q) - 1u;
+    for (int c0 = 0; c0 < max_span; c0 += 3 * GW) {
+        int32_t kc[3];
+#pragma unroll
+        for (int h = 0; h < 3; ++h) {
+            const int c = c0 + GW * h + q;
+            kc[h] = (valid && c < span) ? __ldg(A.ccode + bm.z + c) : 0;
+        }
+#pragma unroll
+        for (int h = 0; h < 3; ++h) {
+            const unsigned m = __ballot_sync(FULL, kc[h] < 0);
+            const unsigned gm = (m >> (GW * g)) & ((1u << GW) - 1u);
+            const int pos = nact + __popc(gm & below_q);
+            if (kc[h] < 0 && pos < CAP) sop[pos] = word_offset((uint32_t)kc[h]);
+            nact += __popc(gm);
+        }
+    }
+    __syncwarp();
+    const bool big = valid && nact > CAP;
+    if (big && q == 0) fold_direct(A, bm, mir);  // rare: more active contributions than listed
+    const bool mine = valid && !big;
+    // stage the runs of the unit's active contributors, the unit's GW lanes sharing the copies
+    const bool staged = mine && nact <= ENT_SCAP;
+    if (staged) {
+        for (int kk = q; kk < nact * CPR; kk += GW) {
+            const int j = kk / CPR, p = kk - j * CPR;
+            cp_async16(stage + RUN * j + 2 * p, A.Ke + sop[j] + 2 * p);
+        }
+    }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+    double acc = 0.0;
+    const int ns = staged ? nact : 0;
+    const int maxs = __reduce_max_sync(FULL, ns);
+    if (maxs > 0) {  // warp-uniform; the same operands in the same order as below
+        if (ns > 0) acc = plus_zero(stage[q]);  // the first contribution: +0.0 + v
+        for (int j = 1; j < maxs; ++j)
+            if (j < ns) acc += stage[RUN * j + q];
+    }
+    const int n = mine && !staged ? nact : 0;  // longer lists: operands from global memory
+    const int maxn = __reduce_max_sync(FULL, n);
+#define STA_LD(j) ((j) < n ? __ldg(A.Ke + sop[(j)] + q) : 0.0)
+    if (maxn > 0) {  // warp-uniform guards, as in k_fold_flat
+        if (n > 0) acc = plus_zero(STA_LD(0));  // the first contribution: +0.0 + v
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+        if (maxn > 1) v0 = STA_LD(1);
+        if (maxn > 2) v1 = STA_LD(2);
+        if (maxn > 3) v2 = STA_LD(3);
+        if (maxn > 4) v3 = STA_LD(4);
+        int j = 1;
+        for (; j + 4 <= maxn; j += 4) {  // next 4 operands in flight
+            double x0 = 0.0, x1 = 0.0, x2 = 0.0, x3 = 0.0;
+            if (j + 4 < maxn) x0 = STA_LD(j + 4);
+            if (j + 5 < maxn) x1 = STA_LD(j + 5);
+            if (j + 6 < maxn) x2 = STA_LD(j + 6);
+            if (j + 7 < maxn) x3 = STA_LD(j + 7);
+            if (j < n) acc += v0;
+            if (j + 1 < n) acc += v1;
+            if (j + 2 < n) acc += v2;
+            if (j + 3 < n) acc += v3;
+            v0 = x0;
+            v1 = x1;
+            v2 = x2;
+            v3 = x3;
+        }
+        if (j < maxn && j < n) acc += v0;
+        if (j + 1 < maxn && j + 1 < n) acc += v1;
+        if (j + 2 < maxn && j + 2 < n) acc += v2;
+    }
+#undef STA_LD
+    if (mine) {
+        if (DIAG) {
+            // 6-run entry q = (i, j), i <= j
+            const int i = q < 3 ? 0 : (q < 5 ? 1 : 2), j = q < 3 ? q : (q < 5 ? q - 2 : 2);
+            double a = acc;
+            if (i == j && has_eps) a += A.eps;
+            double *out = A.val + bm.x;
+            const int rs = bm.y >> 1;
+            out[i * rs + j] = a;
+            if (i != j) out[j * rs + i] = a;
+        } else {
+            const int qi = q / 3, qj = q % 3;
+            A.val[bm.x + qi * (bm.y >> 1) + qj] = acc;
+            A.val[mir.x + qj * mir.y + qi] = acc;
+        }
+    }
+    __syncwarp();
+}
+
+// count[0]: diagonal units | pair units << 32 (the claim kernel's); count[2] gets the frame's
+// touched CSR entries (9 per diagonal unit, 18 = both blocks per pair unit), also stored into
+// the host-mapped word `host_count` when given.  `cap`: the list's length.
+__global__ void __launch_bounds__(ENT_WARPS * 32)
+k_fold_entries(FoldArgs A, const int32_t *__restrict__ list, unsigned long long *count, int64_t cap,
+               int32_t *__restrict__ owner, unsigned long long *host_count) {
+    __shared__ uint32_t sop_all[ENT_WARPS][ENT_SOP];
+    __shared__ __align__(16) double stage_all[ENT_WARPS][ENT_STAGE];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int g = lane / 9, q = lane % 9;  // g == 3: lanes 27..31 idle
-    const int qi = q / 3, qj = q % 3;
-    uint32_t *sop = sop_all[wid][g < ENT_UNITS ? g : 0];
-    double *stage = stage_all[wid][g < ENT_UNITS ? g : 0];  // run j at stage[10 j]
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t nitems = (int64_t)*count;
+    const unsigned long long packed = *count;  // final: the claim kernel has ended
+    const int64_t nd = (int64_t)(packed & 0xffffffffull), np = (int64_t)(packed >> 32);
+    const int64_t gd = (nd + ENT_DG - 1) / ENT_DG, gp = (np + ENT_PG - 1) / ENT_PG;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const unsigned long long entries = 9ull * (unsigned long long)nd + 18ull * (unsigned long long)np;
+        count[2] = entries;
+        if (host_count) *host_count = entries;
+    }
     const bool has_eps = A.eps != 0.0;
-    // the frame's touched-entry count (count[2], final since the claim kernel ended) into the
-    // host-mapped word sta_last_touched reads
-    if (host_count && blockIdx.x == 0 && threadIdx.x == 0) *host_count = count[2];
-    for (int64_t base = warp * ENT_UNITS; base < nitems; base += nwarps * ENT_UNITS) {  // warp-uniform
-        const int64_t item = base + g;
-        const bool valid = g < ENT_UNITS && item < nitems;
-        int4 bm = make_int4(0, 0, 0, 0);
-        int2 mir = make_int2(0, 0);
-        if (valid) {
-            const int32_t u = __ldg(list + item);
-            bm = __ldg(A.bmeta + u);
-            mir = __ldg(A.bmirror + u);
-            if (q == 0) owner[u] = INT32_MAX;  // release the claim (all claims are done)
-        }
-        // compact the unit's active contributors (as operand bases), 9 lanes striding over its
-        // list, three 9-code chunks loaded together and taken in list order
-        int nact = 0;
-        const int span = valid ? bm.w - bm.z : 0;
-        const int max_span = __reduce_max_sync(FULL, span);
-        const unsigned below_q = (1u << q) - 1u;
-        for (int c0 = 0; c0 < max_span; c0 += 27) {
-            int32_t k[3];
-#pragma unroll
-            for (int h = 0; h < 3; ++h) {
-                const int c = c0 + 9 * h + q;
-                k[h] = (valid && c < span) ? __ldg(A.ccode + bm.z + c) : 0;
-            }
-#pragma unroll
-            for (int h = 0; h < 3; ++h) {
-                const unsigned m = __ballot_sync(FULL, k[h] < 0);
-                const unsigned gm = (m >> (9 * g)) & 0x1ffu;
-                const int pos = nact + __popc(gm & below_q);
-                if (k[h] < 0 && pos < ENT_CAP) sop[pos] = word_offset((uint32_t)k[h]);
-                nact += __popc(gm);
-            }
-        }
-        __syncwarp();
-        const bool big = valid && nact > ENT_CAP;
-        if (big && q == 0) fold_direct(A, bm, mir);  // rare: more active contributions than listed
-        const bool diag = (bm.y & 1) != 0;
-        const bool mine = valid && !big && (!diag || q < 6);  // a diagonal unit folds 6 entries
-        // stage the runs of the unit's active contributors (16-byte pieces: 3 of a 48-byte
-        // diagonal run, 5 of an 80-byte pair run), the unit's 9 lanes sharing the copies
-        const bool staged = valid && !big && nact <= ENT_SCAP;
-        if (staged) {
-            const int cpr = diag ? 3 : 5;
-            for (int kk = q; kk < nact * cpr; kk += 9) {
-                const int j = kk / cpr, p = kk - j * cpr;
-                cp_async16(stage + 10 * j + 2 * p, A.Ke + sop[j] + 2 * p);
-            }
-        }
-        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-        __syncwarp();
-        double acc = 0.0;
-        const int ns = mine && staged ? nact : 0;
-        const int maxs = __reduce_max_sync(FULL, ns);
-        if (maxs > 0) {  // warp-uniform; the same operands in the same order as below
-            if (ns > 0) acc = plus_zero(stage[q]);  // the first contribution: +0.0 + v
-            for (int j = 1; j < maxs; ++j)
-                if (j < ns) acc += stage[10 * j + q];
-        }
-        const int n = mine && !staged ? nact : 0;  // longer lists: operands from global memory
-        const int maxn = __reduce_max_sync(FULL, n);
-#define STA_LD(j) ((j) < n ? __ldg(A.Ke + sop[(j)] + q) : 0.0)
-        if (maxn > 0) {  // warp-uniform guards, as in k_fold_flat
-            if (n > 0) acc = plus_zero(STA_LD(0));  // the first contribution: +0.0 + v
-            double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-            if (maxn > 1) v0 = STA_LD(1);
-            if (maxn > 2) v1 = STA_LD(2);
-            if (maxn > 3) v2 = STA_LD(3);
-            if (maxn > 4) v3 = STA_LD(4);
-            int j = 1;
-            for (; j + 4 <= maxn; j += 4) {  // next 4 operands in flight
-                double x0 = 0.0, x1 = 0.0, x2 = 0.0, x3 = 0.0;
-                if (j + 4 < maxn) x0 = STA_LD(j + 4);
-                if (j + 5 < maxn) x1 = STA_LD(j + 5);
-                if (j + 6 < maxn) x2 = STA_LD(j + 6);
-                if (j + 7 < maxn) x3 = STA_LD(j + 7);
-                if (j < n) acc += v0;
-                if (j + 1 < n) acc += v1;
-                if (j + 2 < n) acc += v2;
-                if (j + 3 < n) acc += v3;
-                v0 = x0;
-                v1 = x1;
-                v2 = x2;
-                v3 = x3;
-            }
-            if (j < maxn && j < n) acc += v0;
-            if (j + 1 < maxn && j + 1 < n) acc += v1;
-            if (j + 2 < maxn && j + 2 < n) acc += v2;
-        }
-#undef STA_LD
-        if (mine) {
-            if (diag) {
-                // 6-run entry q = (i, j), i <= j
-                const int i = q < 3 ? 0 : (q < 5 ? 1 : 2), j = q < 3 ? q : (q < 5 ? q - 2 : 2);
-                double a = acc;
-                if (i == j && has_eps) a += A.eps;
-                double *out = A.val + bm.x;
-                const int rs = bm.y >> 1;
-                out[i * rs + j] = a;
-                if (i != j) out[j * rs + i] = a;
-            } else {
-                A.val[bm.x + qi * (bm.y >> 1) + qj] = acc;
-                A.val[mir.x + qj * mir.y + qi] = acc;
-            }
-        }
-        __syncwarp();
+    for (int64_t item = warp; item < gd + gp; item += nwarps) {  // warp-uniform
+        if (item < gd)
+            fold_units<true>(A, list, item * ENT_DG, nd, cap, owner, sop_all[wid], stage_all[wid],
+                             lane, has_eps);
+        else
+            fold_units<false>(A, list, (item - gd) * ENT_PG, np, cap, owner, sop_all[wid],
+                              stage_all[wid], lane, has_eps);
     }
 }
 
 // Streaming, phase 1: apply the frame's mask changes and collect the touched fold units.  One
 // thread per (edited tet k, unit slot s): it writes the contributor's new activity bit, and
 // claims the slot's unit with a compare-and-swap on its owner word (INT32_MAX = free); the
-// thread that wins appends the unit to the fold list (warp-aggregated) and counts its entries
-// (9 for a diagonal unit, 18 = both blocks for a pair).  The fold releases the claims.  The
-// list order depends on scheduling, the values do not (each unit folds independently).
-// edited[k] = tet id | (new state << 31); the edited count is *m_dev if m_dev, else m;
-// counters[1] (units) and counters[3] (entries) start at zero.
+// thread that wins appends the unit to the fold list, a diagonal unit (slots 0-3) at the front
+// and a pair unit at the back of the `cap` entries, both counted by one warp-aggregated atomic
+// on counters[1] = diagonal units | pair units << 32.  The fold releases the claims and counts
+// the touched entries.  The list order depends on scheduling, the values do not (each unit
+// folds independently).  edited[k] = tet id | (new state << 31); the edited count is *m_dev if
+// m_dev, else m; counters[1] starts at zero; a frame lists at most 10 units per edited tet and
+// at most every unit once, so the two ends never meet when cap >= min(10 m, units).
 __global__ void k_stream_claim(const int32_t *__restrict__ edited, int64_t m,
                                const int64_t *__restrict__ m_dev, int64_t T,
                                const int32_t *__restrict__ tunit,
                                const int32_t *__restrict__ cslot, int32_t *__restrict__ ccode,
                                uint8_t *__restrict__ mask, int32_t *__restrict__ owner,
-                               int32_t *__restrict__ list, unsigned long long *counters) {
+                               int32_t *__restrict__ list, int64_t cap,
+                               unsigned long long *counters) {
     const int64_t n = 10 * (m_dev ? *m_dev : m);
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -192,15 +228,16 @@ __global__ void k_stream_claim(const int32_t *__restrict__ edited, int64_t m,
             diag = s < 4;
             won = atomicCAS(&owner[u], INT32_MAX, 0) == INT32_MAX;
         }
-        const unsigned ball = __ballot_sync(0xffffffffu, won);
         const unsigned dball = __ballot_sync(0xffffffffu, won && diag);
+        const unsigned pball = __ballot_sync(0xffffffffu, won && !diag);
         unsigned long long base = 0;
-        if (lane == 0 && ball) {
-            base = atomicAdd(&counters[1], (unsigned long long)__popc(ball));
-            atomicAdd(&counters[3], (unsigned long long)(18 * __popc(ball) - 9 * __popc(dball)));
-        }
+        if (lane == 0 && (dball | pball))
+            base = atomicAdd(&counters[1], (unsigned long long)__popc(dball) |
+                                               ((unsigned long long)__popc(pball) << 32));
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (won) list[base + __popc(ball & ((1u << lane) - 1u))] = u;
+        const unsigned below = (1u << lane) - 1u;
+        if (won && diag) list[(base & 0xffffffffull) + __popc(dball & below)] = u;
+        if (won && !diag) list[cap - 1 - (int64_t)((base >> 32) + __popc(pball & below))] = u;
     }
 }
 
@@ -230,13 +267,14 @@ int persistent_grid(const Ctx *c, const void *kernel, int threads, int64_t items
     return (int)(g < 1 ? 1 : g);
 }
 
-int launch_fold_list(Ctx *c, const int32_t *list, const unsigned long long *count,
+int launch_fold_list(Ctx *c, const int32_t *list, int64_t cap, unsigned long long *count,
                      int64_t max_items, cudaStream_t s, unsigned long long *host_count) {
     const int threads = ENT_WARPS * 32;
-    // one unit per 9 lanes (3 per warp) for the largest possible list, at most the resident CTAs
+    // a warp round per 3 units for the largest possible list (all pair units), at most the
+    // resident CTAs
     const int grid = persistent_grid(c, (const void *)k_fold_entries, threads,
-                                     (max_items + ENT_UNITS - 1) / ENT_UNITS * 32);
-    k_fold_entries<<<grid, threads, 0, s>>>(fold_args(c), list, count, c->owner, host_count);
+                                     (max_items + ENT_PG - 1) / ENT_PG * 32);
+    k_fold_entries<<<grid, threads, 0, s>>>(fold_args(c), list, count, cap, c->owner, host_count);
     STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;
 }
@@ -276,9 +314,11 @@ int launch_stream_frame(Ctx *c, const int32_t *edited, const int64_t *m_dev,
     const int64_t gmax = (int64_t)c->num_sms * 16;
     g = g < 1 ? 1 : (g > gmax ? gmax : g);
     k_stream_claim<<<(unsigned)g, threads, 0, s>>>(edited, 0, m_dev, c->T, c->tunit, c->cslot,
-                                                   c->ccode, c->mask, c->owner, c->touched, cnt);
+                                                   c->ccode, c->mask, c->owner, c->touched,
+                                                   c->nunits, cnt);
     STA_CUDA_TRY(cudaGetLastError());
-    STA_TRY(launch_fold_list(c, c->touched, cnt + 1, 10 * (cap > 0 ? cap : 1), s, c->d_count_mapped));
+    STA_TRY(launch_fold_list(c, c->touched, c->nunits, cnt + 1, 10 * (cap > 0 ? cap : 1), s,
+                             c->d_count_mapped));
     return launch_dyn_mass_edited(c, edited, 0, m_dev, cap, s);
 }
 
@@ -304,11 +344,12 @@ int launch_stream_scratch(Ctx *c, int64_t m, const int32_t *d_edited, int32_t *t
     } else if (m > 0) {
         const int threads = 256;
         const int64_t g = (10 * m + threads - 1) / threads;
+        // the touched list holds 10 m units (at most 10 per edited tet)
         k_stream_claim<<<(unsigned)g, threads, 0, s>>>(d_edited, m, nullptr, c->T, c->tunit, c->cslot,
                                                        c->ccode, c->mask, c->owner, touched,
-                                                       counters);
+                                                       10 * m, counters);
         STA_CUDA_TRY(cudaGetLastError());
-        STA_TRY(launch_fold_list(c, touched, counters + 1, 10 * m, s, nullptr));
+        STA_TRY(launch_fold_list(c, touched, 10 * m, counters + 1, 10 * m, s, nullptr));
     }
     if (m > 0) STA_TRY(launch_dyn_mass_edited(c, d_edited, m, nullptr, m, s));
     // touched units and touched entries, for sta_last_touched

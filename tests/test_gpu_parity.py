@@ -155,6 +155,31 @@ def test_rebuild_forms_bitwise(sta, orc, form):
             asm.close()
 
 
+def test_rebuild_form_auto_follows_the_active_fraction(sta):
+    """AUTO resolves to zero fill while fewer than 40% of the tetrahedra are active, else to the
+    fused form, following the mask through rebuilds and streamed edits; an explicit form holds."""
+    wl = W.plain_small(seed=4, frames=1)
+    T = wl.n_tets
+    asm = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu)
+    k = -(-2 * T // 5)  # the fewest active tetrahedra that are not below 40%
+    mask = np.zeros(T, np.uint8)
+    mask[:k] = 1
+    asm.full_rebuild(mask)
+    assert asm.rebuild_form() == sta.STA_REBUILD_FUSED
+    asm.apply_edits(W.make_edits(off=[0]))  # one fewer: below 40%
+    assert asm.rebuild_form() == sta.STA_REBUILD_ZERO_FILL
+    asm.apply_edits(W.make_edits(on=[0]))
+    assert asm.rebuild_form() == sta.STA_REBUILD_FUSED
+    asm.full_rebuild(np.ones(T, np.uint8))
+    assert asm.rebuild_form() == sta.STA_REBUILD_FUSED
+    asm.set_rebuild_form(sta.STA_REBUILD_ZERO_FILL)
+    assert asm.rebuild_form() == sta.STA_REBUILD_ZERO_FILL
+    asm.set_rebuild_form(sta.STA_REBUILD_AUTO)
+    asm.full_rebuild(np.zeros(T, np.uint8))
+    assert asm.rebuild_form() == sta.STA_REBUILD_ZERO_FILL
+    asm.close()
+
+
 def test_rebuild_form_rejections(sta):
     wl = W.plain_small(seed=3, frames=1)
     asm = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu)
@@ -184,9 +209,11 @@ def test_streaming_eps_and_small_variants(sta, orc):
 
 
 def test_long_contributor_lists(sta, orc):
-    # one node pair and both its nodes shared by K tetrahedra: lists longer than the folds'
-    # shared-memory staging (rebuild tiles and streamed units fall back to unstaged folds)
-    for K, eps in ((300, 0.0), (1000, 1e-2)):
+    # one node pair and both its nodes shared by K tetrahedra (70% active at start): lists
+    # longer than the folds' shared-memory staging (streamed units: 24 runs staged, longer
+    # lists load their operands from global memory, lists beyond 64 active contributions of a
+    # diagonal unit or 96 of a pair fold directly; rebuild tiles: 448 codes)
+    for K, eps in ((40, 0.0), (80, 1e-3), (300, 0.0), (1000, 1e-2)):
         _run_stream(sta, orc, W.edge_fan(seed=K, K=K), eps=eps)
 
 
