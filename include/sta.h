@@ -117,6 +117,13 @@ int sta_refold(sta_ctx *ctx, void *stream);
  * graph mode is on (STA_ESTATE). */
 int sta_set_launch(sta_ctx *ctx, int32_t block_threads, int32_t blocks_per_sm);
 
+/* Operand loads each lane of the rebuild fold keeps in flight: 4 (default; the fold kernel
+ * then fits 64 registers a thread, 32 resident warps per SM) or 6 (80 registers, 24 warps).
+ * The fold is bound by load latency and which choice hides it better depends on the mesh and
+ * mask; results do not depend on it.  A launch choice of the library with no counterpart in
+ * the paper.  Not allowed while graph mode is on (STA_ESTATE); STA_EINVAL for another value. */
+int sta_set_fold_depth(sta_ctx *ctx, int32_t operands_in_flight);
+
 /*
  * sta_set_rebuild_form -- how the full rebuild (sta_full_rebuild, sta_refold; Sec. 3.5) writes
  * the values; the values are the same bits in every form.

@@ -32,7 +32,7 @@ EXPORTED = (
     "sta_batch_create", "sta_batch_size", "sta_batch_instance", "sta_batch_apply_edits",
     "sta_graph_enable", "sta_graph_disable", "sta_set_policy", "sta_proxy_create",
     "sta_proxy_state", "sta_dyn_setup", "sta_dyn_step", "sta_dyn_state", "sta_dyn_set_state",
-    "sta_dyn_apply", "sta_solve", "sta_outer_grad", "sta_set_rebuild_form",
+    "sta_dyn_apply", "sta_solve", "sta_outer_grad", "sta_set_rebuild_form", "sta_set_fold_depth",
     "sta_get_rebuild_form",
 )
 STA_NOALLOC_MAX_EDITED = 32768
@@ -92,6 +92,7 @@ def load_library(path: Path | str | None = None):
     L.sta_spmv.argtypes = [_p, _p, _p, _p, _p]
     L.sta_set_launch.argtypes = [_p, C.c_int32, C.c_int32]
     L.sta_set_rebuild_form.argtypes = [_p, C.c_int32]
+    L.sta_set_fold_depth.argtypes = [_p, C.c_int32]
     L.sta_get_rebuild_form.argtypes = [_p, _P(C.c_int32)]
     L.sta_batch_create.argtypes = [C.c_int32, _p, _p, _p, _p, _p, _p, _P(sta_options), _p, _P(_p)]
     L.sta_batch_size.argtypes = [_p, _P(C.c_int32)]
@@ -479,6 +480,10 @@ def sta_set_launch(h: int, block_threads: int = 0, blocks_per_sm: int = 0) -> No
     _check(load_library().sta_set_launch(h, int(block_threads), int(blocks_per_sm)))
 
 
+def sta_set_fold_depth(h: int, operands_in_flight: int = 4) -> None:
+    _check(load_library().sta_set_fold_depth(h, int(operands_in_flight)))
+
+
 def sta_set_rebuild_form(h: int, form: int = STA_REBUILD_AUTO) -> None:
     _check(load_library().sta_set_rebuild_form(h, int(form)))
 
@@ -618,6 +623,10 @@ class Assembler:
 
     def set_launch(self, block_threads: int = 0, blocks_per_sm: int = 0):
         sta_set_launch(self.h, block_threads, blocks_per_sm)
+
+    def set_fold_depth(self, operands_in_flight: int = 4):
+        """Operand loads in flight per lane of the rebuild fold (4 or 6; schedule only)."""
+        sta_set_fold_depth(self.h, operands_in_flight)
 
     def set_rebuild_form(self, form: int = STA_REBUILD_AUTO):
         sta_set_rebuild_form(self.h, form)

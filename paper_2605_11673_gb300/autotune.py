@@ -1,11 +1,12 @@
 """Launch autotuner for the full rebuild.
 
 Sweeps the rebuild form (fused, or zero fill + fold of the flagged tiles; sta_set_rebuild_form),
-the fold's CTA size (64, 128, 256 threads) and CTAs per SM (0 = occupancy maximum, or a fixed
-count) on a given context, timing the full refold with CUDA events after an L2 flush, and keeps
-the fastest choice in a JSON cache keyed by GPU name, the context's sizes and its active
-fraction (in tenths: the best form depends on how much of the superset is active).  The choice
-changes only the schedule: values are identical for every form and shape.
+the fold's CTA size (64, 128, 256 threads), CTAs per SM (0 = occupancy maximum, or a fixed
+count) and the operand loads each lane keeps in flight (4 at 32 resident warps per SM, or 6 at
+24; sta_set_fold_depth) on a given context, timing the full refold with CUDA events after an L2
+flush, and keeps the fastest choice in a JSON cache keyed by GPU name, the context's sizes and
+its active fraction (in tenths: the best form depends on how much of the superset is active).
+The choice changes only the schedule: values are identical for every form and shape.
 """
 from __future__ import annotations
 
@@ -16,7 +17,8 @@ from pathlib import Path
 CACHE = Path(os.environ.get("STA_AUTOTUNE_CACHE",
                             Path(__file__).resolve().parent / "_build" / "autotune.json"))
 FUSED, ZERO_FILL = 1, 2  # sta.h STA_REBUILD_FUSED, STA_REBUILD_ZERO_FILL
-SHAPES = [(f, t, b) for f in (FUSED, ZERO_FILL) for t in (64, 128, 256)
+# (rebuild form, threads per CTA, CTAs per SM, operand loads in flight)
+SHAPES = [(f, t, b, d) for f in (FUSED, ZERO_FILL) for d in (4, 6) for t in (64, 128, 256)
           for b in (0, 1, 2, 3, 4, 6, 8)]
 
 
@@ -50,9 +52,10 @@ def pick_best(timings: dict) -> tuple:
 
 
 def apply(asm, choice) -> None:
-    form, threads, per_sm = choice
+    form, threads, per_sm, depth = choice
     asm.set_rebuild_form(form)
     asm.set_launch(threads, per_sm)
+    asm.set_fold_depth(depth)
 
 
 def measure(asm, shape, repeats: int = 11, flush_bytes: int = 256 << 20) -> float:
@@ -76,20 +79,20 @@ def measure(asm, shape, repeats: int = 11, flush_bytes: int = 256 << 20) -> floa
 
 def tune(asm, repeats: int = 11, use_cache: bool = True, path: Path = CACHE,
          shapes=None) -> tuple:
-    """Best (form, block_threads, blocks_per_sm) for this context at its current mask; applied
-    to it and cached."""
+    """Best (form, block_threads, blocks_per_sm, operands in flight) for this context at its
+    current mask; applied to it and cached."""
     import torch
     sizes = asm.sizes()
     tenths = int(10 * int(asm.mask().sum().item()) // max(1, sizes["n_tets"]))
     key = key_for(torch.cuda.get_device_name(), sizes, tenths)
     cache = load_cache(path) if use_cache else {}
-    if use_cache and key in cache:
+    if use_cache and key in cache and len(cache[key].get("shape", ())) == len(SHAPES[0]):
         shape = tuple(cache[key]["shape"])
     else:
         timings = {s: measure(asm, s, repeats) for s in (shapes or SHAPES)}
         shape = pick_best(timings)
         cache[key] = {"shape": list(shape), "ms": timings[shape],
-                      "all": {f"{f}:{t}x{b}": ms for (f, t, b), ms in timings.items()}}
+                      "all": {f"{f}:{t}x{b}:d{d}": ms for (f, t, b, d), ms in timings.items()}}
         save_cache(cache, path)
     apply(asm, shape)
     return shape

@@ -300,6 +300,15 @@ int sta_set_launch(sta_ctx *x, int32_t block_threads, int32_t blocks_per_sm) {
     return STA_OK;
 }
 
+int sta_set_fold_depth(sta_ctx *x, int32_t operands_in_flight) {
+    if (!x) return fail(STA_EINVAL, "ctx is NULL");
+    if (operands_in_flight != 4 && operands_in_flight != 6)
+        return fail(STA_EINVAL, "operands_in_flight must be 4 or 6");
+    if (x->c.graph_on) return fail(STA_ESTATE, "disable graph mode before changing the fold depth");
+    x->c.fold_depth = operands_in_flight;
+    return STA_OK;
+}
+
 int sta_set_rebuild_form(sta_ctx *x, int32_t form) {
     if (!x) return fail(STA_EINVAL, "ctx is NULL");
     if (form != STA_REBUILD_AUTO && form != STA_REBUILD_FUSED && form != STA_REBUILD_ZERO_FILL)

@@ -136,6 +136,7 @@ struct Ctx {
     double eps = 0.0;
     int block_threads = 256;
     int blocks_per_sm = 0;
+    int fold_depth = 4;            // operand loads in flight per lane of the rebuild fold: 4 or 6
     int rebuild_form = STA_REBUILD_AUTO;  // sta_set_rebuild_form
     int64_t n_active = 0;                 // active tetrahedra (host mirror count)
     int num_sms = 0;

@@ -64,7 +64,7 @@ struct FxArgs {
 // 32-code chunks of the range (already loaded), `bm`, `mir` the lane's unit records.  A tile
 // that is not `live` (a code range of at most 96 codes, none active) folds nothing: every
 // entry is the empty fold +0.0 (+ eps on the diagonal), written only if `write_dead`.
-template <bool FX, typename V>
+template <bool FX, int PF, typename V>
 __device__ __forceinline__ void flat_tile(const FoldArgs &A, const FxArgs &X, const V *__restrict__ src,
                                           int32_t *scode, int lane, const FlatLane &L, int4 bm,
                                           int2 mir, int32_t cr0, int32_t cr1, int32_t code0,
@@ -111,7 +111,27 @@ __device__ __forceinline__ void flat_tile(const FoldArgs &A, const FxArgs &X, co
         // every guard on maxn is warp-uniform: a tile issues no operand work past its
         // longest fold (a tile of units without active contributors issues none at all)
 #define STA_LD(j) ((j) < n ? __ldg(src + sc[(j)] + q) : V(0))
-        if (maxn > 0) {
+        if (maxn > 0 && PF != 4) {  // PF operands in flight, in registers v[]
+            if constexpr (FX) acc = STA_LD(0);
+            else acc = plus_zero(STA_LD(0));  // the first contribution: +0.0 + v, no FP64 add
+            V v[PF];
+#pragma unroll
+            for (int k = 0; k < PF; ++k) v[k] = maxn > 1 + k ? STA_LD(1 + k) : V(0);
+            int j = 1;
+            for (; j + PF <= maxn; j += PF) {  // next PF operands in flight
+                V x[PF];
+#pragma unroll
+                for (int k = 0; k < PF; ++k) x[k] = j + PF + k < maxn ? STA_LD(j + PF + k) : V(0);
+#pragma unroll
+                for (int k = 0; k < PF; ++k)
+                    if (j + k < n) acc += v[k];
+#pragma unroll
+                for (int k = 0; k < PF; ++k) v[k] = x[k];
+            }
+#pragma unroll
+            for (int k = 0; k < PF - 1; ++k)
+                if (j + k < maxn && j + k < n) acc += v[k];
+        } else if (maxn > 0) {  // PF == 4, written out (the array form spills in one instance)
             if constexpr (FX) acc = STA_LD(0);
             else acc = plus_zero(STA_LD(0));  // the first contribution: +0.0 + v, no FP64 add
             V v0 = V(0), v1 = V(0), v2 = V(0), v3 = V(0);
@@ -211,8 +231,11 @@ struct FlagStream {
 // ZF = false (fused form): every tile, each writing all its entries, +0.0 for the tiles
 // without an active code.  ZF = true (zero-fill form): the values were set to zero and the
 // tiles to fold flagged by k_tile_flags; the warp visits only the flagged tiles of its stripe.
-template <int WARPS, bool FX, bool ZF>  // warps per CTA: 2, 4 or 8 (at most 64 registers a thread)
-__global__ void __launch_bounds__(WARPS * 32, 32 / WARPS)
+// PF: operand loads in flight per lane, 4 (at most 64 registers a thread: 32 resident warps per
+// SM) or 6 (at most 80: 24 warps).  The fold is bound by load latency; which of the two hides
+// it better depends on the workload (the autotuner chooses).
+template <int WARPS, bool FX, bool ZF, int PF>  // warps per CTA: 2, 4 or 8
+__global__ void __launch_bounds__(WARPS * 32, (PF == 4 ? 32 : 24) / WARPS)
 k_fold_flat(FoldArgs A, const int4 *__restrict__ trec, int64_t ntiles, FxArgs X,
             const uint8_t *__restrict__ tflag) {
     using V = typename std::conditional<FX, long long, double>::type;
@@ -266,7 +289,7 @@ k_fold_flat(FoldArgs A, const int4 *__restrict__ trec, int64_t ntiles, FxArgs X,
         const int32_t code1c = nr0 + 64 + lane < nr1 ? __ldg(A.ccode + nr0 + 64 + lane) : 0;
         const int2 mir1 = L1.valid && !L1.dgl ? __ldg(A.bmirror + L1.u) : make_int2(0, 0);
         // stage 3: tile t0 (a tile without an active code skips the compaction and the fold)
-        flat_tile<FX, V>(A, X, src, scode, lane, L, bm0, mir0, cr0, cr1, code0, code0b, code0c,
+        flat_tile<FX, PF, V>(A, X, src, scode, lane, L, bm0, mir0, cr0, cr1, code0, code0b, code0c,
                          tile_live(cr0, cr1, code0, code0b, code0c), true);
         // advance the pipeline
         L = L1;
@@ -329,15 +352,26 @@ __global__ void k_tile_flags(const uint8_t *__restrict__ mask, const int32_t *__
     }
 }
 
+template <int WARPS, bool FX, bool ZF, int PF>
+int launch_flat(Ctx *c, const FoldArgs &A, const FxArgs &X, cudaStream_t s) {
+    const void *kern = (const void *)k_fold_flat<WARPS, FX, ZF, PF>;
+    const int grid = persistent_grid(c, kern, WARPS * 32, c->ntiles * 32, true);
+    k_fold_flat<WARPS, FX, ZF, PF><<<grid, WARPS * 32, 0, s>>>(A, c->ftile, c->ntiles, X, c->tflag);
+    STA_CUDA_TRY(cudaGetLastError());
+    return STA_OK;
+}
+
+template <bool FX, bool ZF, int PF>
+int launch_flat_shape(Ctx *c, const FoldArgs &A, const FxArgs &X, cudaStream_t s) {
+    if (c->block_threads == 64) return launch_flat<2, FX, ZF, PF>(c, A, X, s);
+    if (c->block_threads == 256) return launch_flat<8, FX, ZF, PF>(c, A, X, s);
+    return launch_flat<4, FX, ZF, PF>(c, A, X, s);
+}
+
 template <bool FX, bool ZF>
 int launch_fold(Ctx *c, cudaStream_t s) {
     const FxArgs X{c->fx_q, c->fx_e, c->fx_s};
     const FoldArgs A = fold_args(c);
-    const int threads = c->block_threads == 64 || c->block_threads == 256 ? c->block_threads : 128;
-    const void *kern = threads == 64    ? (const void *)k_fold_flat<2, FX, ZF>
-                       : threads == 256 ? (const void *)k_fold_flat<8, FX, ZF>
-                                        : (const void *)k_fold_flat<4, FX, ZF>;
-    const int grid = persistent_grid(c, kern, threads, c->ntiles * 32, true);
     if (ZF) {
         if (c->eps != 0.0)  // every diagonal tile writes eps
             STA_CUDA_TRY(cudaMemcpyAsync(c->tflag, c->tdiag, (size_t)c->ntiles,
@@ -348,11 +382,8 @@ int launch_fold(Ctx *c, cudaStream_t s) {
                                                     c->val, FX ? c->fx_s : nullptr, c->nnz);
         STA_CUDA_TRY(cudaGetLastError());
     }
-    if (threads == 64) k_fold_flat<2, FX, ZF><<<grid, threads, 0, s>>>(A, c->ftile, c->ntiles, X, c->tflag);
-    else if (threads == 256) k_fold_flat<8, FX, ZF><<<grid, threads, 0, s>>>(A, c->ftile, c->ntiles, X, c->tflag);
-    else k_fold_flat<4, FX, ZF><<<grid, threads, 0, s>>>(A, c->ftile, c->ntiles, X, c->tflag);
-    STA_CUDA_TRY(cudaGetLastError());
-    return STA_OK;
+    return c->fold_depth == 6 ? launch_flat_shape<FX, ZF, 6>(c, A, X, s)
+                              : launch_flat_shape<FX, ZF, 4>(c, A, X, s);
 }
 
 }  // namespace
@@ -366,8 +397,9 @@ int rebuild_form_of(const Ctx *c) {
 }
 
 // Full rebuild: the flat entry-parallel fold over all tiles, with the context's launch shape
-// (block_threads 64, 128 or 256; blocks_per_sm 0 = occupancy maximum) and rebuild form
-// (rebuild_form_of: fused, or zero fill + fold of the tiles with an active contributor).
+// (block_threads 64, 128 or 256; blocks_per_sm 0 = occupancy maximum; fold_depth 4 or 6
+// operand loads in flight) and rebuild form (rebuild_form_of: fused, or zero fill + fold of the
+// tiles with an active contributor).
 int launch_rebuild(Ctx *c, cudaStream_t s) {
     if (c->ntiles == 0) return STA_OK;
     const bool fx = c->policy == STA_POLICY_FIXED;

@@ -106,7 +106,8 @@ def test_entry_points_reject_null_context_and_bad_meshes_on_the_host(lib):
         L.sta_apply_edits(None, None, 0, None), L.sta_full_rebuild(None, None, 0, None),
         L.sta_refold(None, None), L.sta_graph_enable(None, 1, None),
         L.sta_set_rebuild_form(None, 0), L.sta_get_rebuild_form(None, C.byref(i32)),
-        L.sta_set_launch(None, 128, 0), L.sta_last_touched(None, None, None),
+        L.sta_set_launch(None, 128, 0), L.sta_set_fold_depth(None, 4),
+        L.sta_last_touched(None, None, None),
     ]
     assert all(r == lib.STA_EINVAL for r in calls), calls
     for tets in (np.array([[0, 1, 2, 2]]), np.array([[0, 1, 2, 9]]), np.array([[-1, 1, 2, 3]])):

@@ -106,11 +106,13 @@ def test_graph_mode_matches_plain_launches(sta):
 @pytest.mark.parametrize("threads", [64, 128, 256])
 @pytest.mark.parametrize("per_sm", [0, 1, 3])
 @pytest.mark.parametrize("form", [1, 2])  # STA_REBUILD_FUSED, STA_REBUILD_ZERO_FILL
-def test_launch_shape_does_not_change_values(sta, threads, per_sm, form):
+@pytest.mark.parametrize("depth", [4, 6])  # operand loads in flight
+def test_launch_shape_does_not_change_values(sta, threads, per_sm, form, depth):
     wl = W.prefractured_block(N=10, sites=6, frames=3)
     ref = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu)
     got = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu, block_threads=threads, blocks_per_sm=per_sm)
     got.set_rebuild_form(form)
+    got.set_fold_depth(depth)
     ref.full_rebuild(wl.mask0)
     got.full_rebuild(wl.mask0)
     assert _eq(ref.values(), got.values())

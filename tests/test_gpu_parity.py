@@ -118,12 +118,14 @@ def test_rebuild_device_mask_and_eps(sta, orc):
     asm.close()
 
 
+@pytest.mark.parametrize("depth", [4, 6])
 @pytest.mark.parametrize("form", ["fused", "zero_fill"])
-def test_rebuild_forms_bitwise(sta, orc, form):
-    """Both rebuild forms give the oracle's values bit for bit: on a mostly inactive superset
-    (a small refinement hierarchy) and a mostly active one, with eps = 0 and eps != 0 (the
-    zero-fill form still writes eps on the diagonal of units without an active contributor),
-    after streaming, under the fixed-point policy, and captured in graph mode."""
+def test_rebuild_forms_bitwise(sta, orc, form, depth):
+    """Both rebuild forms, with either fold depth (operand loads in flight), give the oracle's
+    values bit for bit: on a mostly inactive superset (a small refinement hierarchy) and a
+    mostly active one, with eps = 0 and eps != 0 (the zero-fill form still writes eps on the
+    diagonal of units without an active contributor), after streaming, under the fixed-point
+    policy, and captured in graph mode."""
     code = {"fused": sta.STA_REBUILD_FUSED, "zero_fill": sta.STA_REBUILD_ZERO_FILL}[form]
     for wl in (W.refinement_hierarchy(N=6, radius=0.3, frames=4),
                W.prefractured_block(N=8, sites=5, frames=4)):
@@ -134,6 +136,7 @@ def test_rebuild_forms_bitwise(sta, orc, form):
         for eps in (0.0, 0.5):
             asm = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu, eps=eps)
             asm.set_rebuild_form(code)
+            asm.set_fold_depth(depth)
             asm.full_rebuild(masks[0])
             _assert_bitwise(_vals(asm), P.rebuild(Ke, masks[0], eps), f"{wl.name} {form} rebuild")
             for f, ed in enumerate(wl.frames):
@@ -183,15 +186,18 @@ def test_rebuild_form_auto_follows_the_active_fraction(sta):
 def test_rebuild_form_rejections(sta):
     wl = W.plain_small(seed=3, frames=1)
     asm = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu)
-    with pytest.raises(sta.StaError) as e:
-        asm.set_rebuild_form(3)
-    assert e.value.status == sta.STA_EINVAL
+    for call, bad in ((asm.set_rebuild_form, 3), (asm.set_fold_depth, 5), (asm.set_fold_depth, 0)):
+        with pytest.raises(sta.StaError) as e:
+            call(bad)
+        assert e.value.status == sta.STA_EINVAL
     asm.graph_enable(64)
-    with pytest.raises(sta.StaError) as e:
-        asm.set_rebuild_form(sta.STA_REBUILD_FUSED)
-    assert e.value.status == sta.STA_ESTATE
+    for call, arg in ((asm.set_rebuild_form, sta.STA_REBUILD_FUSED), (asm.set_fold_depth, 6)):
+        with pytest.raises(sta.StaError) as e:
+            call(arg)
+        assert e.value.status == sta.STA_ESTATE
     asm.graph_disable()
     asm.set_rebuild_form(sta.STA_REBUILD_AUTO)
+    asm.set_fold_depth(6)
     asm.close()
 
 
