@@ -299,10 +299,15 @@ int rebuild_form_of(const Ctx *c);  // the form the next rebuild takes (AUTO res
 int launch_stream_frame(Ctx *c, FrameHeader *frame, int64_t cap, cudaStream_t s);  // sta_stream.cu
 // whether a streaming frame of this context stores its touched count into h_count_mapped
 bool frame_counts_to_host(const Ctx *c);
+// whether its fold can zero the next frame's counters (the FP64 re-fold of the elasticity
+// operator; the other frames' counters are zeroed by a copy or a memset)
+bool frame_zeroes_next(const Ctx *c);
 // the same with the edited list, its count and the counters at separate addresses (the graph
-// mode's host-mapped frames keep their counters in device memory)
+// mode's host-mapped frames keep their counters in device memory); next_cnt: the counters the
+// fold zeroes for the next frame (when frame_zeroes_next), or nullptr
 int launch_stream_frame(Ctx *c, const int32_t *edited, const int64_t *m_dev,
-                        unsigned long long *cnt, int64_t cap, cudaStream_t s);
+                        unsigned long long *cnt, int64_t cap, cudaStream_t s,
+                        unsigned long long *next_cnt);
 int launch_fx_prepare(Ctx *c, cudaStream_t s);                   // sta_fixed.cu
 int launch_fx_frame(Ctx *c, const int32_t *edited, int64_t m, const int64_t *m_dev, int64_t cap,
                     int32_t *touched, unsigned long long *counters, cudaStream_t s);

@@ -163,10 +163,13 @@ __device__ __forceinline__ void fold_units(const FoldArgs &A, const int32_t *__r
 
 // count[0]: diagonal units | pair units << 32 (the claim kernel's); count[2] gets the frame's
 // touched CSR entries (9 per diagonal unit, 18 = both blocks per pair unit), also stored into
-// the host-mapped word `host_count` when given.  `cap`: the list's length.
+// the host-mapped word `host_count` when given.  `cap`: the list's length.  `next_count`, when
+// given, is the count pair of the next frame (graph mode alternates two), zeroed here so that
+// the captured frame needs no memset node of its own.
 __global__ void __launch_bounds__(ENT_WARPS * 32)
 k_fold_entries(FoldArgs A, const int32_t *__restrict__ list, unsigned long long *count, int64_t cap,
-               int32_t *__restrict__ owner, unsigned long long *host_count) {
+               int32_t *__restrict__ owner, unsigned long long *host_count,
+               unsigned long long *next_count) {
     __shared__ uint32_t sop_all[ENT_WARPS][ENT_SOP];
     __shared__ __align__(16) double stage_all[ENT_WARPS][ENT_STAGE];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -179,6 +182,10 @@ k_fold_entries(FoldArgs A, const int32_t *__restrict__ list, unsigned long long 
         const unsigned long long entries = 9ull * (unsigned long long)nd + 18ull * (unsigned long long)np;
         count[2] = entries;
         if (host_count) *host_count = entries;
+        if (next_count) {
+            next_count[0] = 0;
+            next_count[2] = 0;
+        }
     }
     const bool has_eps = A.eps != 0.0;
     for (int64_t item = warp; item < gd + gp; item += nwarps) {  // warp-uniform
@@ -268,13 +275,15 @@ int persistent_grid(const Ctx *c, const void *kernel, int threads, int64_t items
 }
 
 int launch_fold_list(Ctx *c, const int32_t *list, int64_t cap, unsigned long long *count,
-                     int64_t max_items, cudaStream_t s, unsigned long long *host_count) {
+                     int64_t max_items, cudaStream_t s, unsigned long long *host_count,
+                     unsigned long long *next_count) {
     const int threads = ENT_WARPS * 32;
     // a warp round per 3 units for the largest possible list (all pair units), at most the
     // resident CTAs
     const int grid = persistent_grid(c, (const void *)k_fold_entries, threads,
                                      (max_items + ENT_PG - 1) / ENT_PG * 32);
-    k_fold_entries<<<grid, threads, 0, s>>>(fold_args(c), list, count, cap, c->owner, host_count);
+    k_fold_entries<<<grid, threads, 0, s>>>(fold_args(c), list, count, cap, c->owner, host_count,
+                                            next_count);
     STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;
 }
@@ -300,9 +309,11 @@ int launch_values(Ctx *c, cudaStream_t s) {
 // One streaming frame: claim kernel, then the fold of the touched units.  `frame` is a device
 // frame block (FrameHeader + edited list) already holding the frame; the count is read from
 // it, grids are sized for `cap` edited tetrahedra (so the sequence can be captured once and
-// replayed for any frame up to `cap`).
+// replayed for any frame up to `cap`).  `next_cnt` (FP64 re-fold only, else ignored): the
+// counters of the next frame, which the fold zeroes.
 int launch_stream_frame(Ctx *c, const int32_t *edited, const int64_t *m_dev,
-                        unsigned long long *cnt, int64_t cap, cudaStream_t s) {
+                        unsigned long long *cnt, int64_t cap, cudaStream_t s,
+                        unsigned long long *next_cnt) {
     if (c->op == STA_OP_PROXY)
         return launch_proxy_frame(c, edited, 0, m_dev, cap, c->plist, cnt, s);
     if (c->policy == STA_POLICY_FIXED) {
@@ -318,16 +329,19 @@ int launch_stream_frame(Ctx *c, const int32_t *edited, const int64_t *m_dev,
                                                    c->nunits, cnt);
     STA_CUDA_TRY(cudaGetLastError());
     STA_TRY(launch_fold_list(c, c->touched, c->nunits, cnt + 1, 10 * (cap > 0 ? cap : 1), s,
-                             c->d_count_mapped));
+                             c->d_count_mapped, next_cnt ? next_cnt + 1 : nullptr));
     return launch_dyn_mass_edited(c, edited, 0, m_dev, cap, s);
 }
 
-bool frame_counts_to_host(const Ctx *c) {
-    return c->op == STA_OP_ELASTICITY && c->policy == STA_POLICY_REFOLD && c->d_count_mapped;
+bool frame_zeroes_next(const Ctx *c) {
+    return c->op == STA_OP_ELASTICITY && c->policy == STA_POLICY_REFOLD;
 }
 
+bool frame_counts_to_host(const Ctx *c) { return frame_zeroes_next(c) && c->d_count_mapped; }
+
 int launch_stream_frame(Ctx *c, FrameHeader *frame, int64_t cap, cudaStream_t s) {
-    return launch_stream_frame(c, frame_edited(frame), &frame->m, frame_counters(frame), cap, s);
+    return launch_stream_frame(c, frame_edited(frame), &frame->m, frame_counters(frame), cap, s,
+                               nullptr);
 }
 
 // Streaming update with caller-chosen scratch (the allocation-free entry point): the same two
@@ -349,7 +363,7 @@ int launch_stream_scratch(Ctx *c, int64_t m, const int32_t *d_edited, int32_t *t
                                                        c->ccode, c->mask, c->owner, touched,
                                                        10 * m, counters);
         STA_CUDA_TRY(cudaGetLastError());
-        STA_TRY(launch_fold_list(c, touched, 10 * m, counters + 1, 10 * m, s, nullptr));
+        STA_TRY(launch_fold_list(c, touched, 10 * m, counters + 1, 10 * m, s, nullptr, nullptr));
     }
     if (m > 0) STA_TRY(launch_dyn_mass_edited(c, d_edited, m, nullptr, m, s));
     // touched units and touched entries, for sta_last_touched
