@@ -202,23 +202,30 @@ k_fold_entries(FoldArgs A, const int32_t *__restrict__ list, unsigned long long 
 // thread per (edited tet k, unit slot s): it writes the contributor's new activity bit, and
 // claims the slot's unit with a compare-and-swap on its owner word (INT32_MAX = free); the
 // thread that wins appends the unit to the fold list, a diagonal unit (slots 0-3) at the front
-// and a pair unit at the back of the `cap` entries, both counted by one warp-aggregated atomic
-// on counters[1] = diagonal units | pair units << 32.  The fold releases the claims and counts
+// and a pair unit at the back of the `cap` entries, both counted by one CTA-aggregated atomic
+// on counters[1] = diagonal units | pair units << 32 (a large frame's warps all appending to
+// that one word serialise at the L2; per CTA there are 8 times fewer).  The fold releases the claims and counts
 // the touched entries.  The list order depends on scheduling, the values do not (each unit
 // folds independently).  edited[k] = tet id | (new state << 31); the edited count is *m_dev if
 // m_dev, else m; counters[1] starts at zero; a frame lists at most 10 units per edited tet and
 // at most every unit once, so the two ends never meet when cap >= min(10 m, units).
-__global__ void k_stream_claim(const int32_t *__restrict__ edited, int64_t m,
+constexpr int CLAIM_THREADS = 256;
+
+__global__ void __launch_bounds__(CLAIM_THREADS)
+k_stream_claim(const int32_t *__restrict__ edited, int64_t m,
                                const int64_t *__restrict__ m_dev, int64_t T,
                                const int32_t *__restrict__ tunit,
                                const int32_t *__restrict__ cslot, int32_t *__restrict__ ccode,
                                uint8_t *__restrict__ mask, int32_t *__restrict__ owner,
                                int32_t *__restrict__ list, int64_t cap,
                                unsigned long long *counters) {
+    // per warp of the CTA: its packed winner counts, then its offset; the CTA's base
+    __shared__ unsigned long long s_cnt[CLAIM_THREADS / 32];
+    __shared__ unsigned long long s_base;
     const int64_t n = 10 * (m_dev ? *m_dev : m);
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // warp-uniform
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // CTA-uniform
         const int64_t i = i0 + threadIdx.x;
         bool won = false, diag = false;
         int32_t u = 0;
@@ -237,11 +244,22 @@ __global__ void k_stream_claim(const int32_t *__restrict__ edited, int64_t m,
         }
         const unsigned dball = __ballot_sync(0xffffffffu, won && diag);
         const unsigned pball = __ballot_sync(0xffffffffu, won && !diag);
-        unsigned long long base = 0;
-        if (lane == 0 && (dball | pball))
-            base = atomicAdd(&counters[1], (unsigned long long)__popc(dball) |
-                                               ((unsigned long long)__popc(pball) << 32));
-        base = __shfl_sync(0xffffffffu, base, 0);
+        // packed counts add without carries: each half stays below 2^32
+        if (lane == 0)
+            s_cnt[wid] = (unsigned long long)__popc(dball) | ((unsigned long long)__popc(pball) << 32);
+        __syncthreads();
+        if (threadIdx.x == 0) {  // exclusive prefix over the CTA's warps, one atomic for all
+            unsigned long long tot = 0;
+            for (int w = 0; w < CLAIM_THREADS / 32; ++w) {
+                const unsigned long long v = s_cnt[w];
+                s_cnt[w] = tot;
+                tot += v;
+            }
+            s_base = tot ? atomicAdd(&counters[1], tot) : 0ull;
+        }
+        __syncthreads();
+        const unsigned long long base = s_base + s_cnt[wid];
+        __syncthreads();  // s_cnt and s_base are rewritten in the next round
         const unsigned below = (1u << lane) - 1u;
         if (won && diag) list[(base & 0xffffffffull) + __popc(dball & below)] = u;
         if (won && !diag) list[cap - 1 - (int64_t)((base >> 32) + __popc(pball & below))] = u;
@@ -320,7 +338,7 @@ int launch_stream_frame(Ctx *c, const int32_t *edited, const int64_t *m_dev,
         STA_TRY(launch_fx_frame(c, edited, 0, m_dev, cap, c->touched, cnt, s));
         return launch_dyn_mass_edited(c, edited, 0, m_dev, cap, s);
     }
-    const int threads = 256;
+    const int threads = CLAIM_THREADS;
     int64_t g = (10 * cap + threads - 1) / threads;
     const int64_t gmax = (int64_t)c->num_sms * 16;
     g = g < 1 ? 1 : (g > gmax ? gmax : g);
@@ -356,7 +374,7 @@ int launch_stream_scratch(Ctx *c, int64_t m, const int32_t *d_edited, int32_t *t
     } else if (m > 0 && c->policy == STA_POLICY_FIXED) {
         STA_TRY(launch_fx_frame(c, d_edited, m, nullptr, m, touched, counters, s));
     } else if (m > 0) {
-        const int threads = 256;
+        const int threads = CLAIM_THREADS;
         const int64_t g = (10 * m + threads - 1) / threads;
         // the touched list holds 10 m units (at most 10 per edited tet)
         k_stream_claim<<<(unsigned)g, threads, 0, s>>>(d_edited, m, nullptr, c->T, c->tunit, c->cslot,
