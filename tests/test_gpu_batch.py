@@ -149,3 +149,35 @@ def test_graph_staging_mixed_with_oversized_frames(sta):
     assert b.last_touched() == last
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("policy", [0, 1])  # STA_POLICY_REFOLD, STA_POLICY_FIXED
+def test_graph_counters_across_enable_disable_and_empty_frames(sta, policy):
+    """Graph mode keeps two counter sets; a re-fold frame's fold zeroes the other set for the
+    next frame (the fixed-point frame zeroes its own).  Values and touched counts match plain
+    launches through empty frames, graph mode switched off and on mid-stream, a re-capture at
+    another capacity and a frame past the capacity (the copy path)."""
+    wl = W.plain_small(seed=11, frames=16)
+    empty = np.zeros((0, 3), np.int32)
+    sizes = [int(ed.shape[0] + (ed[:, 0] == 2).sum()) for ed in wl.frames]
+    a = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu)
+    b = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu)
+    for x in (a, b):
+        x.set_policy(policy)
+        x.full_rebuild(wl.mask0)
+    b.graph_enable(max_edited=max(sizes))
+    for f, ed in enumerate(wl.frames):
+        if f == 4:
+            b.graph_disable()
+        if f == 7:
+            b.graph_enable(max_edited=max(sizes))
+        if f == 11:  # a smaller capacity: the largest frames take the copy path
+            b.graph_disable()
+            b.graph_enable(max_edited=sorted(sizes)[len(sizes) // 2])
+        for frame in ((ed, empty) if f % 3 == 0 else (ed,)):
+            a.apply_edits(frame)
+            b.apply_edits(frame)
+            assert _eq(a.values(), b.values()), f"frame {f}"
+            assert a.last_touched() == b.last_touched(), f"frame {f}"
+    a.close()
+    b.close()
