@@ -615,6 +615,8 @@ int build_pattern(Ctx *c, cudaStream_t s) {
                                          cudaMemcpyHostToDevice, s));
             STA_CUDA_TRY(cudaMemcpyAsync(c->tdiag, htd.data(), (size_t)c->ntiles,
                                          cudaMemcpyHostToDevice, s));
+            // zero between rebuilds (the zero-fill fold clears each flag it reads)
+            STA_CUDA_TRY(cudaMemsetAsync(c->tflag, 0, (size_t)c->ntiles, s));
             STA_CUDA_TRY(cudaStreamSynchronize(s));  // host vectors go out of scope
         }
         STA_CUDA_TRY(cudaMemcpyAsync(c->ftile, htiles.data(), sizeof(int4) * c->ntiles,

@@ -167,7 +167,7 @@ struct Ctx {
     // per tile whether its units are diagonal, and its flag "fold this tile"
     int32_t *utile = nullptr;      // nunits
     uint8_t *tdiag = nullptr;      // ntiles
-    uint8_t *tflag = nullptr;      // ntiles
+    uint8_t *tflag = nullptr;      // ntiles: zero-fill flags, all zero between rebuilds
     int4 *bmeta = nullptr;         // nunits: {value offset of (a,b), rs_a << 1 | diagonal, c0, c1}
     int2 *bmirror = nullptr;       // nunits: {value offset of (b,a), rs_b}
     int32_t *ccode = nullptr;      // 10 T: unit contributor words (word_offset), ascending tet id

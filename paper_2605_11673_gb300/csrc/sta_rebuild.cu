@@ -200,18 +200,21 @@ __device__ __forceinline__ bool tile_live(int32_t cr0, int32_t cr1, int32_t c0, 
 
 // The zero-fill form's tiles of one warp: the positions k = 0, 1, ... of its stripe (tile
 // w + k W) whose flag is set.  The flags of 32 positions are read at once (one per lane),
-// those of the next 32 one step ahead, and handed out from a ballot.
+// those of the next 32 one step ahead, and handed out from a ballot.  Every flag is read by
+// the one warp whose stripe holds it, and that lane clears it: once the fold has run, all
+// flags are zero again for the next rebuild's flag pass.
 struct FlagStream {
     int32_t base;    // stripe position of bit 0 of `mask`
     unsigned mask;   // set flags of positions base .. base+31 not yet handed out
     uint8_t ahead;   // this lane's flag of position base + 32 + lane
-    __device__ __forceinline__ void load_ahead(const uint8_t *__restrict__ flags, int32_t w,
+    __device__ __forceinline__ void load_ahead(uint8_t *__restrict__ flags, int32_t w,
                                                int32_t W, int32_t ntiles, int lane) {
         const int64_t t = w + (int64_t)(base + 32 + lane) * W;
-        ahead = t < ntiles ? __ldg(flags + t) : 0;
+        ahead = t < ntiles ? flags[t] : 0;
+        if (ahead) flags[t] = 0;
     }
     // the next flagged tile, or ntiles past the end of the stripe
-    __device__ __forceinline__ int32_t next(const uint8_t *__restrict__ flags, int32_t w,
+    __device__ __forceinline__ int32_t next(uint8_t *__restrict__ flags, int32_t w,
                                             int32_t W, int32_t ntiles, int lane) {
         while (mask == 0) {  // warp-uniform
             base += 32;
@@ -237,7 +240,7 @@ struct FlagStream {
 template <int WARPS, bool FX, bool ZF, int PF>  // warps per CTA: 2, 4 or 8
 __global__ void __launch_bounds__(WARPS * 32, (PF == 4 ? 32 : 24) / WARPS)
 k_fold_flat(FoldArgs A, const int4 *__restrict__ trec, int64_t ntiles, FxArgs X,
-            const uint8_t *__restrict__ tflag) {
+            uint8_t *__restrict__ tflag) {
     using V = typename std::conditional<FX, long long, double>::type;
     const V *__restrict__ src;
     if constexpr (FX) src = X.Kq; else src = A.Ke;
@@ -308,26 +311,24 @@ k_fold_flat(FoldArgs A, const int4 *__restrict__ trec, int64_t ntiles, FxArgs X,
     }
 }
 
-// Zero-fill form, first pass.  Sets every value (and, for the fixed-point fold, every integer
-// sum) to zero with 16-byte stores, and flags the tiles the fold must visit -- every tile
-// holding a fold entry of a unit with an active contributor -- into `tflag`, which holds the
-// diagonal tiles' flags (eps != 0) or zeros at launch.  From the mask: each active
-// tetrahedron's 10 units, each in one tile or two consecutive ones.  A thread reads the mask
-// of 4 tetrahedra at once.  The flags are plain byte stores of 1 (any order, no atomics).
+// Zero-fill form, first pass.  Flags the tiles the fold must visit -- every tile holding a fold
+// entry of a unit with an active contributor, and with eps != 0 every diagonal tile (`tdiag`,
+// else null) -- into `tflag`, which is all zero at launch (the previous fold cleared what it
+// read), and sets every value (and, for the fixed-point fold, every integer sum) to zero with
+// 16-byte stores.  The flags come from the mask: each active
+// tetrahedron's 10 units, each in one tile or two consecutive ones; a thread reads the mask of 4
+// tetrahedra at once and an active tetrahedron's 10 unit words together.  The flags are plain
+// byte stores of 1 (any order, no atomics).  Flags first: the warps with active tetrahedra wait
+// on their loads while the others are already filling.
 __global__ void k_tile_flags(const uint8_t *__restrict__ mask, const int32_t *__restrict__ tunit,
                              const int32_t *__restrict__ utile, int64_t T, uint8_t *__restrict__ tflag,
+                             const uint8_t *__restrict__ tdiag, int64_t ntiles,
                              double *__restrict__ val, long long *__restrict__ S, int64_t nnz) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-    // zero fill (both arrays are cudaMalloc'd, 256-byte aligned; an odd last word alone)
-    for (int64_t i = tid; i < (nnz >> 1); i += nthreads) {
-        reinterpret_cast<double2 *>(val)[i] = make_double2(0.0, 0.0);
-        if (S) reinterpret_cast<longlong2 *>(S)[i] = make_longlong2(0, 0);
-    }
-    if (tid == 0 && (nnz & 1)) {
-        val[nnz - 1] = 0.0;
-        if (S) S[nnz - 1] = 0;
-    }
+    if (tdiag)  // eps on the diagonal: every diagonal tile is folded
+        for (int64_t t = tid; t < ntiles; t += nthreads)
+            if (__ldg(tdiag + t)) tflag[t] = 1;
     // tile flags: tetrahedra 4q .. 4q+3 per step (the mask is cudaMalloc'd, so its 4-byte
     // words are aligned; the last word may be partial)
     for (int64_t q = tid; 4 * q < T; q += nthreads) {
@@ -342,13 +343,33 @@ __global__ void k_tile_flags(const uint8_t *__restrict__ mask, const int32_t *__
         for (int k = 0; k < 4; ++k) {
             if (!((m4 >> (8 * k)) & 0xffu)) continue;
             const int64_t t = 4 * q + k;
+            // the tet's 10 unit words (40 bytes at 10 t of a cudaMalloc'd array: 8-byte aligned)
+            const int2 *tu2 = reinterpret_cast<const int2 *>(tunit + 10 * t);
+            int32_t uu[10], ut[10];
+#pragma unroll
+            for (int h = 0; h < 5; ++h) {
+                const int2 v = __ldg(tu2 + h);
+                uu[2 * h] = v.x;
+                uu[2 * h + 1] = v.y;
+            }
+#pragma unroll
+            for (int sl = 0; sl < 10; ++sl) ut[sl] = __ldg(utile + uu[sl]);
+#pragma unroll
             for (int sl = 0; sl < 10; ++sl) {
-                const int32_t ut = __ldg(utile + __ldg(tunit + 10 * t + sl));
-                const int32_t t0 = ut & INT32_MAX;
+                const int32_t t0 = ut[sl] & INT32_MAX;
                 tflag[t0] = 1;
-                if (ut < 0) tflag[t0 + 1] = 1;  // the unit reaches into the next tile
+                if (ut[sl] < 0) tflag[t0 + 1] = 1;  // the unit reaches into the next tile
             }
         }
+    }
+    // zero fill (both arrays are cudaMalloc'd, 256-byte aligned; an odd last word alone)
+    for (int64_t i = tid; i < (nnz >> 1); i += nthreads) {
+        reinterpret_cast<double2 *>(val)[i] = make_double2(0.0, 0.0);
+        if (S) reinterpret_cast<longlong2 *>(S)[i] = make_longlong2(0, 0);
+    }
+    if (tid == 0 && (nnz & 1)) {
+        val[nnz - 1] = 0.0;
+        if (S) S[nnz - 1] = 0;
     }
 }
 
@@ -372,13 +393,9 @@ template <bool FX, bool ZF>
 int launch_fold(Ctx *c, cudaStream_t s) {
     const FxArgs X{c->fx_q, c->fx_e, c->fx_s};
     const FoldArgs A = fold_args(c);
-    if (ZF) {
-        if (c->eps != 0.0)  // every diagonal tile writes eps
-            STA_CUDA_TRY(cudaMemcpyAsync(c->tflag, c->tdiag, (size_t)c->ntiles,
-                                         cudaMemcpyDeviceToDevice, s));
-        else
-            STA_CUDA_TRY(cudaMemsetAsync(c->tflag, 0, (size_t)c->ntiles, s));
+    if (ZF) {  // the flags are all zero here: the previous zero-fill fold cleared them
         k_tile_flags<<<c->num_sms * 8, 256, 0, s>>>(c->mask, c->tunit, c->utile, c->T, c->tflag,
+                                                    c->eps != 0.0 ? c->tdiag : nullptr, c->ntiles,
                                                     c->val, FX ? c->fx_s : nullptr, c->nnz);
         STA_CUDA_TRY(cudaGetLastError());
     }
