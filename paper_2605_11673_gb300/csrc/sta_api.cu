@@ -339,8 +339,14 @@ int sta_apply_edits(sta_ctx *x, const sta_edit *edits, int64_t n_edits, void *st
     if (n_edits < 0 || (n_edits > 0 && !edits)) return fail(STA_EINVAL, "bad edit list");
     if (n_edits > (INT32_MAX / 32)) return fail(STA_ERANGE, "too many edits in one call");
     cudaStream_t s = (cudaStream_t)stream;
-    int64_t m = n_edits;  // edited tetrahedra: a swap edits two
-    for (int64_t e = 0; e < n_edits; ++e) m += edits[e].op == STA_SWAP;
+    // edited tetrahedra (a swap edits two): 2 n_edits bounds them, which is all graph mode needs
+    // to know when it is within the capacity; otherwise they are counted first.  Staging
+    // counts them exactly either way.
+    int64_t m = 2 * n_edits;
+    if (!c->graph_on || m > c->gcap) {
+        m = n_edits;
+        for (int64_t e = 0; e < n_edits; ++e) m += edits[e].op == STA_SWAP;
+    }
 
     // the frame block to stage into: one of the graph mode's two host-mapped blocks (fixed
     // capacity), or the context's pinned block (grown on demand)
@@ -440,6 +446,7 @@ int sta_apply_edits(sta_ctx *x, const sta_edit *edits, int64_t n_edits, void *st
         return fail(STA_EINVAL, "edit " + std::to_string(e) + ": " + why);
     }
     c->n_active += dact;
+    m = k;
 
     // header (count, zeroed counters) before the list: in graph mode the captured kernels read
     // the host-mapped block itself; otherwise block and list go to the device in one copy
