@@ -156,6 +156,16 @@ def _host(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
 
 
+def _ptr(a) -> int:
+    """Address of a non-empty C-contiguous host array's data: through the buffer protocol,
+    which costs half of `a.ctypes.data` on the per-frame path; read-only arrays take the
+    latter."""
+    try:
+        return C.addressof(C.c_char.from_buffer(a))
+    except TypeError:
+        return a.ctypes.data
+
+
 # The C-ABI takes plain pointers and cannot see the length of what they point to, so the
 # binding checks every array it passes against the context's sizes: a wrong length raises
 # here instead of reading or writing past the end of a buffer.
@@ -360,9 +370,11 @@ def sta_full_rebuild(h: int, mask, stream=None) -> None:
 
 def sta_apply_edits(h: int, edits, stream=None) -> None:
     """edits: (m, 3) int32 rows (op, tet, tet2) in host memory."""
-    e = _host(edits, np.int32).reshape(-1, 3)
-    _check(load_library().sta_apply_edits(h, e.ctypes.data if e.shape[0] else None, e.shape[0],
-                                          _stream_handle(stream)))
+    e = _host(edits, np.int32)
+    if e.ndim != 2 or e.shape[1] != 3:
+        e = e.reshape(-1, 3)
+    n = e.shape[0]
+    _check(load_library().sta_apply_edits(h, _ptr(e) if n else None, n, _stream_handle(stream)))
 
 
 def sta_apply_edits_noalloc(h: int, edits, stream=None) -> None:
