@@ -64,11 +64,20 @@ KEYS = ["gpu__time_duration.sum", "dram__bytes_read.sum", "dram__bytes_write.sum
         "smsp__average_warps_issue_stalled_math_pipe_throttle_per_issue_active.ratio"]
 
 
+def code_of(text: str) -> str:
+    """C/CUDA source without its comments, trailing blanks and empty lines: what the compiler
+    sees, so that a record stays current through a comment-only edit."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
 def source_sha(kernel: str) -> str:
-    """Hash of the current sources of a recorded kernel (KERNEL_SOURCES)."""
+    """Hash of the current code (comments left out) of the sources of a recorded kernel
+    (KERNEL_SOURCES)."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES[kernel]:
-        h.update((CSRC / name).read_bytes())
+        h.update(code_of((CSRC / name).read_text()).encode())
     return h.hexdigest()[:16]
 
 

@@ -235,8 +235,9 @@ struct Ctx {
     cudaGraphExec_t g_refold = nullptr, g_rebuild = nullptr;
     // graph mode stages frames in two host-mapped pinned blocks that the captured kernels read
     // directly (no copy call per frame), used alternately; each has its own captured sequence,
-    // its own device counters (zeroed by a memset node of that sequence) and an event recorded
-    // after its launch, waited on before the block is written again
+    // its own device counters (zeroed by the other sequence's fold in the FP64 re-fold, by a
+    // memset node of its own sequence otherwise) and an event recorded after its launch, waited
+    // on before the block is written again
     int64_t gcap = 0;
     cudaGraphExec_t g_streams[2] = {nullptr, nullptr};
     FrameHeader *h_gframe[2] = {nullptr, nullptr};  // host-mapped pinned, gcap entries each

@@ -44,3 +44,9 @@ def test_record_sums_the_launches_of_one_sequence(tmp_path, monkeypatch):
     assert rec["duration_us_cold"] == 100.0
     assert rec["source_sha"] == N.source_sha("rebuild") and out.exists()
     assert N.current_record("rebuild", "wl", tmp_path)["dram_bytes_per_launch"] == 160e6 + 24.2e6
+
+
+def test_record_hash_ignores_comments_only():
+    code = "int f(int x) {\n    return x + 1;  // one more\n}\n"
+    assert N.code_of(code) == N.code_of("/* a\n note */\nint f(int x) {\n\n    return x + 1;\n}\n")
+    assert N.code_of(code) != N.code_of(code.replace("x + 1", "x + 2"))
