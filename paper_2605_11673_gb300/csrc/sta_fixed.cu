@@ -18,6 +18,7 @@
 //
 // Entries are keyed by the value index of their upper block (unit (a, b), a <= b); the mirror
 // block folds the same contributions and is written with the same value.
+#include "sta_claim.cuh"
 #include "sta_fold.cuh"
 
 namespace sta {
@@ -113,7 +114,10 @@ __device__ __forceinline__ void fx_write(const FoldArgs &A, const int16_t *__res
 // Fixed-point frame, phase 1: as k_stream_claim (activity bits, mask, first-wins unit claims,
 // fold list, entry counts), and each (edited tet, slot) thread adds its quantised contributions
 // to the unit's integer sums (+q on activation, -q on deactivation).
-__global__ void k_fx_claim(const int32_t *__restrict__ edited, int64_t m,
+constexpr int FX_CLAIM_THREADS = 256;
+
+__global__ void __launch_bounds__(FX_CLAIM_THREADS)
+k_fx_claim(const int32_t *__restrict__ edited, int64_t m,
                            const int64_t *__restrict__ m_dev, int64_t T,
                            const int32_t *__restrict__ tunit, const int32_t *__restrict__ cslot,
                            int32_t *__restrict__ ccode, uint8_t *__restrict__ mask,
@@ -123,7 +127,7 @@ __global__ void k_fx_claim(const int32_t *__restrict__ edited, int64_t m,
     const int64_t n = 10 * (m_dev ? *m_dev : m);
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // warp-uniform
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // CTA-uniform
         const int64_t i = i0 + threadIdx.x;
         bool won = false, diag = false;
         int32_t u = 0;
@@ -148,22 +152,23 @@ __global__ void k_fx_claim(const int32_t *__restrict__ edited, int64_t m,
         }
         const unsigned ball = __ballot_sync(0xffffffffu, won);
         const unsigned dball = __ballot_sync(0xffffffffu, won && diag);
-        unsigned long long base = 0;
-        if (lane == 0 && ball) {
-            base = atomicAdd(&counters[1], (unsigned long long)__popc(ball));
-            atomicAdd(&counters[3], (unsigned long long)(18 * __popc(ball) - 9 * __popc(dball)));
-        }
-        base = __shfl_sync(0xffffffffu, base, 0);
+        const unsigned long long base = cta_append<FX_CLAIM_THREADS>(
+            counters, __popc(ball), 18 * __popc(ball) - 9 * __popc(dball));
         if (won) list[base + __popc(ball & ((1u << lane) - 1u))] = u;
     }
 }
 
 // Fixed-point frame, phase 2: convert the touched units' entries and release the claims.
-// 9 lanes per listed unit (6 used by a diagonal unit), 3 units per warp.
+// 9 lanes per listed unit (6 used by a diagonal unit), 3 units per warp.  `next_count`, when
+// given, is the next frame's count pair (graph mode alternates two), zeroed here.
 __global__ void k_fx_convert(FoldArgs A, const int32_t *__restrict__ list,
                              const unsigned long long *__restrict__ count,
                              const int16_t *__restrict__ e, const long long *__restrict__ S,
-                             int32_t *__restrict__ owner) {
+                             int32_t *__restrict__ owner, unsigned long long *next_count) {
+    if (next_count && blockIdx.x == 0 && threadIdx.x == 0) {
+        next_count[0] = 0;
+        next_count[2] = 0;
+    }
     const int lane = threadIdx.x & 31;
     const int g = lane / 9, q = lane % 9;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -213,13 +218,15 @@ int launch_fx_prepare(Ctx *c, cudaStream_t s) {
 }
 
 int launch_fx_frame(Ctx *c, const int32_t *edited, int64_t m, const int64_t *m_dev, int64_t cap,
-                    int32_t *touched, unsigned long long *counters, cudaStream_t s) {
-    const int threads = 256;
+                    int32_t *touched, unsigned long long *counters, cudaStream_t s,
+                    unsigned long long *next_cnt) {
+    const int threads = FX_CLAIM_THREADS;
     k_fx_claim<<<grid_cap(c, 10 * cap, threads), threads, 0, s>>>(
         edited, m, m_dev, c->T, c->tunit, c->cslot, c->ccode, c->mask, c->owner, touched,
         counters, c->bmeta, c->fx_q, c->fx_s);
     k_fx_convert<<<grid_cap(c, (10 * (cap > 0 ? cap : 1) + 2) / 3 * 32, 128), 128, 0, s>>>(
-        fold_args(c), touched, counters + 1, c->fx_e, c->fx_s, c->owner);
+        fold_args(c), touched, counters + 1, c->fx_e, c->fx_s, c->owner,
+        next_cnt ? next_cnt + 1 : nullptr);
     STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;
 }

@@ -93,23 +93,18 @@ extern "C" int sta_graph_enable(sta_ctx *x, int64_t max_edited, void *stream) {
     }
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(STA_ECUDA, "graph stream"));
-    // both counter sets start at zero; an FP64 re-fold frame's fold then zeroes the other set
-    // for the frame after it (the two sequences alternate), so those sequences carry no memset
-    // node (a memset node at the head of the graph delayed its first kernel by about 2 us);
-    // the other policies' sequences zero their own counters first
+    // both counter sets start at zero; each frame's last kernel then zeroes the other set for
+    // the frame after it (the two sequences alternate), so the sequences carry no memset node
+    // (a memset node at the head of the graph delayed its first kernel by about 2 us)
     if (cudaMemsetAsync(c->d_gcnt, 0, 8 * sizeof(unsigned long long), cs) != cudaSuccess ||
         cudaStreamSynchronize(cs) != cudaSuccess)
         return bail(fail(STA_ECUDA, "graph counters"));
     c->gcap = max_edited;
-    const bool zero_next = frame_zeroes_next(c);
     for (int b = 0; b < 2; ++b) {
         unsigned long long *cnt = c->d_gcnt + 4 * b, *next = c->d_gcnt + 4 * (b ^ 1);
         FrameHeader *fb = c->m_gframe[b];
         if ((rc = capture(cs, [&](cudaStream_t s) {
-                 if (!zero_next)
-                     STA_CUDA_TRY(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), s));
-                 return launch_stream_frame(c, frame_edited(fb), &fb->m, cnt, c->gcap, s,
-                                            zero_next ? next : nullptr);
+                 return launch_stream_frame(c, frame_edited(fb), &fb->m, cnt, c->gcap, s, next);
              }, &c->g_streams[b])))
             return bail(rc);
     }

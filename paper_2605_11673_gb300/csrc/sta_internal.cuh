@@ -235,9 +235,8 @@ struct Ctx {
     cudaGraphExec_t g_refold = nullptr, g_rebuild = nullptr;
     // graph mode stages frames in two host-mapped pinned blocks that the captured kernels read
     // directly (no copy call per frame), used alternately; each has its own captured sequence,
-    // its own device counters (zeroed by the other sequence's fold in the FP64 re-fold, by a
-    // memset node of its own sequence otherwise) and an event recorded after its launch, waited
-    // on before the block is written again
+    // its own device counters (zeroed by the other sequence's last kernel) and an event
+    // recorded after its launch, waited on before the block is written again
     int64_t gcap = 0;
     cudaGraphExec_t g_streams[2] = {nullptr, nullptr};
     FrameHeader *h_gframe[2] = {nullptr, nullptr};  // host-mapped pinned, gcap entries each
@@ -300,18 +299,16 @@ int rebuild_form_of(const Ctx *c);  // the form the next rebuild takes (AUTO res
 int launch_stream_frame(Ctx *c, FrameHeader *frame, int64_t cap, cudaStream_t s);  // sta_stream.cu
 // whether a streaming frame of this context stores its touched count into h_count_mapped
 bool frame_counts_to_host(const Ctx *c);
-// whether its fold can zero the next frame's counters (the FP64 re-fold of the elasticity
-// operator; the other frames' counters are zeroed by a copy or a memset)
-bool frame_zeroes_next(const Ctx *c);
 // the same with the edited list, its count and the counters at separate addresses (the graph
 // mode's host-mapped frames keep their counters in device memory); next_cnt: the counters the
-// fold zeroes for the next frame (when frame_zeroes_next), or nullptr
+// frame's last kernel zeroes for the next frame, or nullptr
 int launch_stream_frame(Ctx *c, const int32_t *edited, const int64_t *m_dev,
                         unsigned long long *cnt, int64_t cap, cudaStream_t s,
                         unsigned long long *next_cnt);
 int launch_fx_prepare(Ctx *c, cudaStream_t s);                   // sta_fixed.cu
 int launch_fx_frame(Ctx *c, const int32_t *edited, int64_t m, const int64_t *m_dev, int64_t cap,
-                    int32_t *touched, unsigned long long *counters, cudaStream_t s);
+                    int32_t *touched, unsigned long long *counters, cudaStream_t s,
+                    unsigned long long *next_cnt);
 int launch_mask_bits(Ctx *c, cudaStream_t s);                    // codes <- mask
 int launch_values(Ctx *c, cudaStream_t s);  // the operator's rebuild (elasticity or proxy)
 int launch_dyn_qmass(Ctx *c, cudaStream_t s);     // sta_dyn.cu (no-ops unless set up)
@@ -323,7 +320,8 @@ int launch_dyn_step(Ctx *c, double tol, int32_t max_iter, int32_t *iters, double
 int build_proxy_maps(Ctx *c, const int32_t *tblk, cudaStream_t s);  // sta_proxy.cu
 int launch_proxy_rebuild(Ctx *c, cudaStream_t s);
 int launch_proxy_frame(Ctx *c, const int32_t *edited, int64_t m, const int64_t *m_dev,
-                       int64_t cap, int32_t *list, unsigned long long *counters, cudaStream_t s);
+                       int64_t cap, int32_t *list, unsigned long long *counters, cudaStream_t s,
+                       unsigned long long *next_cnt);
 int launch_stream_scratch(Ctx *c, int64_t m, const int32_t *d_edited, int32_t *touched,
                           unsigned long long *counters, cudaStream_t s);
 

@@ -17,7 +17,7 @@
 // Under STA_POLICY_REFOLD a frame instead recounts each touched edge over the tetrahedra
 // incident to it and each touched node's degree over its row (the paper's local_recompute,
 // O(|Delta| kappa)); same values and state.
-#include "sta_internal.cuh"
+#include "sta_claim.cuh"
 
 namespace sta {
 namespace {
@@ -132,8 +132,10 @@ __global__ void k_proxy_diag(int64_t n, const int32_t *__restrict__ pdiag,
 
 // Streaming, part 1 (Eqs. 5-7, Algorithm 1): one thread per (edited tet, slot).  Writes the
 // mask, moves multiplicities and degrees, and claims each touched block once into `list`
-// (counters[1]: blocks, counters[3]: entries -- 2 per edge, 1 per diagonal).
-__global__ void k_proxy_claim(const int32_t *__restrict__ edited, int64_t m,
+// (counters[1]: blocks, counters[3]: entries -- 2 per edge, 1 per diagonal; one atomic on
+// each per CTA).
+__global__ void __launch_bounds__(PX_TPB)
+k_proxy_claim(const int32_t *__restrict__ edited, int64_t m,
                               const int64_t *__restrict__ m_dev, const int4 *__restrict__ tets,
                               const int32_t *__restrict__ ptblk, int32_t *__restrict__ mult,
                               int32_t *__restrict__ deg, uint32_t *__restrict__ flag,
@@ -142,9 +144,8 @@ __global__ void k_proxy_claim(const int32_t *__restrict__ edited, int64_t m,
     const int64_t items = 10 * (m_dev ? *m_dev : m);
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < items;
-         base += stride) {
-        const int64_t i = base + lane;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < items; i0 += stride) {  // CTA-uniform
+        const int64_t i = i0 + threadIdx.x;
         bool won = false, edge = false;
         int32_t g = 0;
         if (i < items) {
@@ -171,12 +172,8 @@ __global__ void k_proxy_claim(const int32_t *__restrict__ edited, int64_t m,
         }
         const unsigned ball = __ballot_sync(0xffffffffu, won);
         const unsigned eball = __ballot_sync(0xffffffffu, won && edge);
-        unsigned long long pos = 0;
-        if (lane == 0 && ball) {
-            pos = atomicAdd(&counters[1], (unsigned long long)__popc(ball));
-            atomicAdd(&counters[3], (unsigned long long)(__popc(ball) + __popc(eball)));
-        }
-        pos = __shfl_sync(0xffffffffu, pos, 0);
+        const unsigned long long pos =
+            cta_append<PX_TPB>(counters, __popc(ball), __popc(ball) + __popc(eball));
         if (won) list[pos + __popc(ball & ((1u << lane) - 1u))] = g;
     }
 }
@@ -189,7 +186,12 @@ __global__ void k_proxy_write(const int32_t *__restrict__ list,
                               const int32_t *__restrict__ pmir, const int32_t *__restrict__ mult,
                               int32_t *__restrict__ deg, double eps,
                               uint32_t *__restrict__ flag, double *__restrict__ val,
-                              const int32_t *__restrict__ adj_ptr, const int32_t *__restrict__ pup) {
+                              const int32_t *__restrict__ adj_ptr, const int32_t *__restrict__ pup,
+                              unsigned long long *next_count) {
+    if (next_count && blockIdx.x == 0 && threadIdx.x == 0) {  // the next graph frame's counts
+        next_count[0] = 0;
+        next_count[2] = 0;
+    }
     const int64_t cnt = (int64_t)*count;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -285,7 +287,8 @@ int launch_proxy_rebuild(Ctx *c, cudaStream_t s) {
 // sized for `cap`); `list` has room for min(10 cap, nblocks) blocks; counters[1] and [3] are
 // zero on entry.
 int launch_proxy_frame(Ctx *c, const int32_t *edited, int64_t m, const int64_t *m_dev,
-                       int64_t cap, int32_t *list, unsigned long long *counters, cudaStream_t s) {
+                       int64_t cap, int32_t *list, unsigned long long *counters, cudaStream_t s,
+                       unsigned long long *next_cnt) {
     const int64_t items = 10 * (cap > 0 ? cap : 1);
     int32_t *deg = c->pmult + c->nblocks;
     const bool rescan = c->policy == STA_POLICY_REFOLD;  // local recompute instead of +-1
@@ -300,7 +303,8 @@ int launch_proxy_frame(Ctx *c, const int32_t *edited, int64_t m, const int64_t *
     k_proxy_write<<<px_grid(c, most, 16), PX_TPB, 0, s>>>(list, counters + 1, c->block_node,
                                                           c->adj, c->pmir, c->pmult, deg, c->eps,
                                                           c->pflag, c->val,
-                                                          rescan ? c->adj_ptr : nullptr, c->pup);
+                                                          rescan ? c->adj_ptr : nullptr, c->pup,
+                                                          next_cnt ? next_cnt + 1 : nullptr);
     STA_CUDA_TRY(cudaGetLastError());
     return STA_OK;
 }

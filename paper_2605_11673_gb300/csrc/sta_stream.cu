@@ -327,15 +327,15 @@ int launch_values(Ctx *c, cudaStream_t s) {
 // One streaming frame: claim kernel, then the fold of the touched units.  `frame` is a device
 // frame block (FrameHeader + edited list) already holding the frame; the count is read from
 // it, grids are sized for `cap` edited tetrahedra (so the sequence can be captured once and
-// replayed for any frame up to `cap`).  `next_cnt` (FP64 re-fold only, else ignored): the
-// counters of the next frame, which the fold zeroes.
+// replayed for any frame up to `cap`).  `next_cnt`: the counters of the next frame, which the
+// frame's last kernel zeroes (graph mode), or nullptr.
 int launch_stream_frame(Ctx *c, const int32_t *edited, const int64_t *m_dev,
                         unsigned long long *cnt, int64_t cap, cudaStream_t s,
                         unsigned long long *next_cnt) {
     if (c->op == STA_OP_PROXY)
-        return launch_proxy_frame(c, edited, 0, m_dev, cap, c->plist, cnt, s);
+        return launch_proxy_frame(c, edited, 0, m_dev, cap, c->plist, cnt, s, next_cnt);
     if (c->policy == STA_POLICY_FIXED) {
-        STA_TRY(launch_fx_frame(c, edited, 0, m_dev, cap, c->touched, cnt, s));
+        STA_TRY(launch_fx_frame(c, edited, 0, m_dev, cap, c->touched, cnt, s, next_cnt));
         return launch_dyn_mass_edited(c, edited, 0, m_dev, cap, s);
     }
     const int threads = CLAIM_THREADS;
@@ -351,11 +351,9 @@ int launch_stream_frame(Ctx *c, const int32_t *edited, const int64_t *m_dev,
     return launch_dyn_mass_edited(c, edited, 0, m_dev, cap, s);
 }
 
-bool frame_zeroes_next(const Ctx *c) {
-    return c->op == STA_OP_ELASTICITY && c->policy == STA_POLICY_REFOLD;
+bool frame_counts_to_host(const Ctx *c) {
+    return c->op == STA_OP_ELASTICITY && c->policy == STA_POLICY_REFOLD && c->d_count_mapped;
 }
-
-bool frame_counts_to_host(const Ctx *c) { return frame_zeroes_next(c) && c->d_count_mapped; }
 
 int launch_stream_frame(Ctx *c, FrameHeader *frame, int64_t cap, cudaStream_t s) {
     return launch_stream_frame(c, frame_edited(frame), &frame->m, frame_counters(frame), cap, s,
@@ -370,9 +368,9 @@ int launch_stream_scratch(Ctx *c, int64_t m, const int32_t *d_edited, int32_t *t
                           unsigned long long *counters, cudaStream_t s) {
     STA_CUDA_TRY(cudaMemsetAsync(counters + 1, 0, 3 * sizeof(unsigned long long), s));
     if (m > 0 && c->op == STA_OP_PROXY) {
-        STA_TRY(launch_proxy_frame(c, d_edited, m, nullptr, m, touched, counters, s));
+        STA_TRY(launch_proxy_frame(c, d_edited, m, nullptr, m, touched, counters, s, nullptr));
     } else if (m > 0 && c->policy == STA_POLICY_FIXED) {
-        STA_TRY(launch_fx_frame(c, d_edited, m, nullptr, m, touched, counters, s));
+        STA_TRY(launch_fx_frame(c, d_edited, m, nullptr, m, touched, counters, s, nullptr));
     } else if (m > 0) {
         const int threads = CLAIM_THREADS;
         const int64_t g = (10 * m + threads - 1) / threads;

@@ -151,17 +151,20 @@ def test_graph_staging_mixed_with_oversized_frames(sta):
     b.close()
 
 
-@pytest.mark.parametrize("policy", [0, 1])  # STA_POLICY_REFOLD, STA_POLICY_FIXED
-def test_graph_counters_across_enable_disable_and_empty_frames(sta, policy):
-    """Graph mode keeps two counter sets; a re-fold frame's fold zeroes the other set for the
-    next frame (the fixed-point frame zeroes its own).  Values and touched counts match plain
-    launches through empty frames, graph mode switched off and on mid-stream, a re-capture at
-    another capacity and a frame past the capacity (the copy path)."""
+@pytest.mark.parametrize("case", ["refold", "fixed", "proxy", "proxy_refold"])
+def test_graph_counters_across_enable_disable_and_empty_frames(sta, case):
+    """Graph mode keeps two counter sets; each frame's last kernel zeroes the other set for the
+    next frame.  Values and touched counts match plain launches through empty frames, graph
+    mode switched off and on mid-stream, a re-capture at another capacity and a frame past the
+    capacity (the copy path), for both operators and both policies."""
     wl = W.plain_small(seed=11, frames=16)
     empty = np.zeros((0, 3), np.int32)
     sizes = [int(ed.shape[0] + (ed[:, 0] == 2).sum()) for ed in wl.frames]
-    a = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu)
-    b = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu)
+    if case.startswith("proxy"):
+        a, b = (sta.ProxyAssembler(wl.n_nodes, wl.tets, eps=1e-3) for _ in range(2))
+    else:
+        a, b = (sta.Assembler(wl.X, wl.tets, wl.E, wl.nu) for _ in range(2))
+    policy = sta.STA_POLICY_FIXED if case in ("fixed", "proxy") else sta.STA_POLICY_REFOLD
     for x in (a, b):
         x.set_policy(policy)
         x.full_rebuild(wl.mask0)
