@@ -295,14 +295,15 @@ int sta_batch_apply_edits(sta_ctx *ctx, const int64_t *counts, const sta_edit *e
 
 /*
  * sta_graph_enable -- capture the per-frame device work of the context into CUDA graphs: the
- * streaming update (mask and activity update, touched-block dedupe, fold; edit count read
- * from device memory, grids sized for max_edited), the refold, and the fold of a full
- * rebuild.  Afterwards sta_apply_edits (frames of at most max_edited edited tetrahedra; a
+ * streaming update (mask and activity update, touched-block dedupe, fold; the edit count and
+ * list read from the staging block below, grids sized for max_edited), the refold, and the
+ * fold of a full rebuild.  Afterwards sta_apply_edits (frames of at most max_edited edited tetrahedra; a
  * swap counts two), sta_refold and sta_full_rebuild replay them with one cudaGraphLaunch each;
  * results are unchanged.  A frame is staged in one of two host-mapped pinned blocks (used in
  * turn) that the captured kernels read directly, so it costs no copy call; the block is
- * reused once the frame two calls back has finished.  Allocates those blocks and device
- * counters and synchronises `stream`.  sta_graph_disable releases them and returns to plain
+ * reused once the frame two calls back has finished.  Allocates those blocks and two sets of
+ * device counters (each frame's last kernel zeroes the set of the frame after it) and
+ * synchronises `stream`.  sta_graph_disable releases them and returns to plain
  * launches.
  */
 int sta_graph_enable(sta_ctx *ctx, int64_t max_edited, void *stream);
