@@ -305,14 +305,22 @@ def test_set_params_then_rebuild(sta, orc):
 
 # ---------------------------------------------------------------- full-size workloads
 
-def _full_size(sta, orc, wl, frames_to_oracle):
+def _full_size(sta, orc, wl, frames_to_oracle, form=None, depth=None, graph=False):
     P = orc.Pattern(wl.n_nodes, wl.tets)
     Ke, bad = orc.element_all(wl.X, wl.tets, wl.E, wl.nu)
     assert bad == 0
     asm = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu)
     _check_pattern(asm, P)
     reb = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu)
+    for x in (asm, reb):  # the rebuild schedule under test (the values do not depend on it)
+        if form is not None:
+            x.set_rebuild_form(form)
+        if depth is not None:
+            x.set_fold_depth(depth)
     masks = wl.masks()
+    if graph:
+        asm.graph_enable(max(int(e.shape[0] + (e[:, 0] == 2).sum()) for e in wl.frames))
+        reb.graph_enable(1)
     asm.full_rebuild(masks[0])
     for f, ed in enumerate(wl.frames):
         asm.apply_edits(ed)
@@ -331,3 +339,11 @@ def test_full_size_prefractured_block(sta, orc):
 
 def test_full_size_refinement(sta, orc):
     _full_size(sta, orc, W.refinement_hierarchy(), {0, 23})
+
+
+def test_full_size_refinement_r040_tuned_schedule(sta, orc):
+    """The "up to ~460k active" case with the schedule the autotuner picks for it on GB300 (zero
+    fill, 6 operand loads in flight) and CUDA graphs: streamed ≡ rebuilt every frame, ≡ the
+    oracle on three frames."""
+    _full_size(sta, orc, W.refinement_hierarchy(radius=0.40), {0, 12, 23},
+               form=sta.STA_REBUILD_ZERO_FILL, depth=6, graph=True)
