@@ -347,3 +347,59 @@ def test_full_size_refinement_r040_tuned_schedule(sta, orc):
     oracle on three frames."""
     _full_size(sta, orc, W.refinement_hierarchy(radius=0.40), {0, 12, 23},
                form=sta.STA_REBUILD_ZERO_FILL, depth=6, graph=True)
+
+
+def _random_frame(rng, mask, most=6):
+    """A valid edit frame drawn at random: some deactivations, activations and swaps (an active
+    tet for an inactive one) over disjoint tetrahedra, rows shuffled; possibly empty."""
+    act = rng.permutation(np.flatnonzero(mask))
+    ina = rng.permutation(np.flatnonzero(mask == 0))
+    k_off = int(rng.integers(0, min(act.size, most) + 1))
+    k_on = int(rng.integers(0, min(ina.size, most) + 1))
+    k_sw = int(rng.integers(0, min(act.size - k_off, ina.size - k_on, most) + 1))
+    ed = W.make_edits(off=act[:k_off], on=ina[:k_on],
+                      swaps=zip(act[k_off:k_off + k_sw], ina[k_on:k_on + k_sw]))
+    return ed[rng.permutation(ed.shape[0])] if ed.shape[0] else ed
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_edit_streams(sta, orc, seed):
+    """Random masks and random frames mixing all three edit kinds, on small supersets of the
+    three shapes (plain, pre-fractured, refinement), each seed with its own schedule (rebuild
+    form, fold depth, eps, graph mode with a capacity some frames exceed): streamed values ≡
+    the oracle's rebuild every frame, the touched count and the mask exact, a refold every third
+    frame ≡ the same values."""
+    rng = np.random.default_rng(7000 + seed)
+    wl = (W.plain_small(seed=seed, N=3, frames=1),
+          W.prefractured_block(seed=seed, N=4, sites=4, frames=1),
+          W.refinement_hierarchy(seed=seed, N=3, radius=0.4, frames=1))[seed % 3]
+    eps = (0.0, 1e-3)[seed % 2]
+    form = (sta.STA_REBUILD_AUTO, sta.STA_REBUILD_FUSED, sta.STA_REBUILD_ZERO_FILL)[(seed // 3) % 3]
+    depth = (4, 6)[int(rng.integers(2))]
+    graph = bool(rng.integers(2))
+    P = orc.Pattern(wl.n_nodes, wl.tets)
+    Ke, bad = orc.element_all(wl.X, wl.tets, wl.E, wl.nu)
+    assert bad == 0
+    asm = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu, eps=eps)
+    asm.set_rebuild_form(form)
+    asm.set_fold_depth(depth)
+    mask = (rng.random(wl.n_tets) < rng.uniform(0.2, 0.9)).astype(np.uint8)
+    asm.full_rebuild(mask)
+    _assert_bitwise(_vals(asm), P.rebuild(Ke, mask, eps), f"seed {seed}: initial rebuild")
+    if graph:
+        asm.graph_enable(max_edited=12)  # frames of more edited tets take the copy path
+    for f in range(16):
+        ed = _random_frame(rng, mask)
+        asm.apply_edits(ed)
+        mask = W.apply_edits_to_mask(mask, ed)
+        ref = P.rebuild(Ke, mask, eps)
+        what = f"seed {seed} frame {f} ({ed.shape[0]} edits, form {form}, depth {depth}, graph {graph})"
+        _assert_bitwise(_vals(asm), ref, what)
+        assert np.array_equal(asm.mask().cpu().numpy(), mask), what
+        edited = np.concatenate([ed[:, 1], ed[ed[:, 0] == 2, 2]]) if ed.shape[0] else ed[:, 1]
+        expect = np.unique(P.scat[edited].reshape(-1)).size if edited.size else 0
+        assert asm.last_touched() == expect, what
+        if f % 3 == 2:
+            asm.refold()
+            _assert_bitwise(_vals(asm), ref, what + ", refold")
+    asm.close()
