@@ -96,3 +96,15 @@ def test_fixed_point_policy_rejected_in_graph_mode(sta):
     with pytest.raises(sta.StaError):
         asm.set_policy(7)
     asm.close()
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_fixed_point_random_edit_streams(sta, orc, seed):
+    """Random masks and frames mixing all three edit kinds on small supersets of the three
+    shapes: the fixed-point frame ≡ the oracle's definition every frame (eps and graph mode
+    alternating over the seeds)."""
+    base = (W.plain_small(seed=seed, N=3, frames=1),
+            W.prefractured_block(seed=seed, N=4, sites=4, frames=1),
+            W.refinement_hierarchy(seed=seed, N=3, radius=0.4, frames=1))[seed % 3]
+    _run_fixed(sta, orc, W.randomized(base, seed), eps=(0.0, 1e-3)[seed % 2],
+               graph=bool(seed & 2))

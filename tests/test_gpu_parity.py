@@ -349,19 +349,6 @@ def test_full_size_refinement_r040_tuned_schedule(sta, orc):
                form=sta.STA_REBUILD_ZERO_FILL, depth=6, graph=True)
 
 
-def _random_frame(rng, mask, most=6):
-    """A valid edit frame drawn at random: some deactivations, activations and swaps (an active
-    tet for an inactive one) over disjoint tetrahedra, rows shuffled; possibly empty."""
-    act = rng.permutation(np.flatnonzero(mask))
-    ina = rng.permutation(np.flatnonzero(mask == 0))
-    k_off = int(rng.integers(0, min(act.size, most) + 1))
-    k_on = int(rng.integers(0, min(ina.size, most) + 1))
-    k_sw = int(rng.integers(0, min(act.size - k_off, ina.size - k_on, most) + 1))
-    ed = W.make_edits(off=act[:k_off], on=ina[:k_on],
-                      swaps=zip(act[k_off:k_off + k_sw], ina[k_on:k_on + k_sw]))
-    return ed[rng.permutation(ed.shape[0])] if ed.shape[0] else ed
-
-
 @pytest.mark.parametrize("seed", range(24))
 def test_random_edit_streams(sta, orc, seed):
     """Random masks and random frames mixing all three edit kinds, on small supersets of the
@@ -369,10 +356,11 @@ def test_random_edit_streams(sta, orc, seed):
     form, fold depth, eps, graph mode with a capacity some frames exceed): streamed values ≡
     the oracle's rebuild every frame, the touched count and the mask exact, a refold every third
     frame ≡ the same values."""
-    rng = np.random.default_rng(7000 + seed)
-    wl = (W.plain_small(seed=seed, N=3, frames=1),
-          W.prefractured_block(seed=seed, N=4, sites=4, frames=1),
-          W.refinement_hierarchy(seed=seed, N=3, radius=0.4, frames=1))[seed % 3]
+    base = (W.plain_small(seed=seed, N=3, frames=1),
+            W.prefractured_block(seed=seed, N=4, sites=4, frames=1),
+            W.refinement_hierarchy(seed=seed, N=3, radius=0.4, frames=1))[seed % 3]
+    wl = W.randomized(base, seed)
+    rng = np.random.default_rng(7000 + seed)  # the schedule
     eps = (0.0, 1e-3)[seed % 2]
     form = (sta.STA_REBUILD_AUTO, sta.STA_REBUILD_FUSED, sta.STA_REBUILD_ZERO_FILL)[(seed // 3) % 3]
     depth = (4, 6)[int(rng.integers(2))]
@@ -383,13 +371,12 @@ def test_random_edit_streams(sta, orc, seed):
     asm = sta.Assembler(wl.X, wl.tets, wl.E, wl.nu, eps=eps)
     asm.set_rebuild_form(form)
     asm.set_fold_depth(depth)
-    mask = (rng.random(wl.n_tets) < rng.uniform(0.2, 0.9)).astype(np.uint8)
+    mask = wl.mask0.copy()
     asm.full_rebuild(mask)
     _assert_bitwise(_vals(asm), P.rebuild(Ke, mask, eps), f"seed {seed}: initial rebuild")
     if graph:
         asm.graph_enable(max_edited=12)  # frames of more edited tets take the copy path
-    for f in range(16):
-        ed = _random_frame(rng, mask)
+    for f, ed in enumerate(wl.frames):
         asm.apply_edits(ed)
         mask = W.apply_edits_to_mask(mask, ed)
         ref = P.rebuild(Ke, mask, eps)

@@ -220,3 +220,14 @@ def test_proxy_full_size_local_recompute_and_solve(sta, orc):
     assert rel <= 1e-10 and it > 0
     assert np.linalg.norm((A @ xn - b)[free]) <= 10 * 1e-10 * np.linalg.norm(b)
     px.close()
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_proxy_random_edit_streams(sta, orc, seed):
+    """Random masks and frames mixing all three edit kinds: values, multiplicities, degrees and
+    visited counts ≡ the oracle every frame, both policies and graph mode over the seeds."""
+    base = (W.plain_small(seed=seed, N=3, frames=1),
+            W.prefractured_block(seed=seed, N=4, sites=4, frames=1),
+            W.refinement_hierarchy(seed=seed, N=3, radius=0.4, frames=1))[seed % 3]
+    _run(sta, orc, W.randomized(base, seed), eps=(0.0, 1e-3)[seed % 2], graph=bool(seed & 2),
+         policy=sta.STA_POLICY_REFOLD if seed & 4 else None)

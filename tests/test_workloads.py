@@ -56,3 +56,25 @@ def test_batched_and_adjoint_recipes(orc):
     a = W.adjoint_block()
     assert (a.n_tets, a.n_nodes, len(a.frames)) == (20 ** 3 * 6, 21 ** 3, 24)
     _valid_stream(orc, a)
+
+
+def test_random_edit_streams_are_valid_frames():
+    """The randomized parity tests' input: every frame names each tetrahedron once, deactivates
+    active ones, activates inactive ones and swaps an active one for an inactive one; some
+    frames are empty and every edit kind occurs."""
+    base = W.prefractured_block(seed=0, N=4, sites=4, frames=1)
+    kinds, empty = set(), 0
+    for seed in range(6):
+        wl = W.randomized(base, seed)
+        m = wl.mask0.copy()
+        for ed in wl.frames:
+            empty += ed.shape[0] == 0
+            tets = np.concatenate([ed[:, 1], ed[ed[:, 0] == W.SWAP, 2]])
+            assert np.unique(tets).size == tets.size
+            for op, t, t2 in ed:
+                kinds.add(int(op))
+                assert m[t] == (op != W.ACTIVATE)
+                if op == W.SWAP:
+                    assert m[t2] == 0
+            m = W.apply_edits_to_mask(m, ed)
+    assert kinds == {W.DEACTIVATE, W.ACTIVATE, W.SWAP} and empty > 0

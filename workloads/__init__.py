@@ -169,6 +169,38 @@ def deact_react_stream(rng, T: int, mask0: np.ndarray, frames: int, rate_off: fl
     return out
 
 
+def random_edit_stream(rng, mask0: np.ndarray, frames: int, most: int = 6):
+    """Test input, not a paper workload: each frame draws up to `most` deactivations, `most`
+    activations and `most` swaps (an active tet for an inactive one) over disjoint tetrahedra
+    from the mask at frame start, rows shuffled; one frame in eight (on average) is empty."""
+    m = mask0.copy()
+    out = []
+    for _ in range(frames):
+        if rng.random() < 0.125:
+            out.append(make_edits())
+            continue
+        act = rng.permutation(np.flatnonzero(m))
+        ina = rng.permutation(np.flatnonzero(m == 0))
+        k_off = int(rng.integers(0, min(act.size, most) + 1))
+        k_on = int(rng.integers(0, min(ina.size, most) + 1))
+        k_sw = int(rng.integers(0, min(act.size - k_off, ina.size - k_on, most) + 1))
+        ed = make_edits(off=act[:k_off], on=ina[:k_on],
+                        swaps=zip(act[k_off:k_off + k_sw], ina[k_on:k_on + k_sw]))
+        ed = ed[rng.permutation(ed.shape[0])] if ed.shape[0] else ed
+        out.append(ed)
+        m = apply_edits_to_mask(m, ed)
+    return out
+
+
+def randomized(wl: Workload, seed: int, frames: int = 16, most: int = 6) -> Workload:
+    """The superset of `wl` with a random initial mask (active fraction drawn in [0.2, 0.9])
+    and a random_edit_stream: the randomized parity tests' input."""
+    rng = rng_for(90, seed)
+    mask0 = (rng.random(wl.n_tets) < rng.uniform(0.2, 0.9)).astype(np.uint8)
+    return Workload(f"{wl.name}_random{seed}", wl.X, wl.tets, wl.E, wl.nu, mask0,
+                    random_edit_stream(rng, mask0, frames, most), dict(wl.meta))
+
+
 # ----------------------------------------------------------------------------------------
 # Configurations
 # ----------------------------------------------------------------------------------------
