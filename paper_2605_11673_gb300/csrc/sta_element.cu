@@ -1,4 +1,4 @@
-// Element stiffness kernel (a1): the 12x12 linear-tetrahedron elasticity matrix K^(tau)
+// Element stiffness kernel: the 12x12 linear-tetrahedron elasticity matrix K^(tau)
 // (STA-FEM Sec. 3.4 and Sec. 5.2; the standard P1 isotropic small-strain element,
 // K = V B^T D B), 78 unique entries per tetrahedron written to the element cache.
 //
@@ -178,7 +178,7 @@ k_elements(const double4_32a *__restrict__ X, const int4 *__restrict__ tets,
 
 
 // ------------------------------------------------------------------------------------------
-// Adjoint (a5): dL/dE, dL/dnu and per-element dL/dx for an upstream gradient dL/dA given per
+// Adjoint: dL/dE, dL/dnu and per-element dL/dx for an upstream gradient dL/dA given per
 // CSR entry.  With G = dL/dK^(tau) gathered through the node-pair blocks of the tetrahedron and
 // K = V (lam A + mu B), A[ai][bj] = g_a[i] g_b[j], B[ai][bj] = g_a[j] g_b[i] + d_ij g_a.g_b:
 //   SA = sum_ab g_a^T G_ab g_b,   SB = sum_ab (g_b^T G_ab g_a + tr(G_ab) g_a.g_b)

@@ -1,4 +1,4 @@
-// Fold kernels: full rebuild (a2) and streaming update (a3).
+// Fold kernels: the full rebuild and the streaming update.
 //
 // Both evaluate, for a node-pair block (a, b) of the superset pattern, the 9 CSR values
 //   A[3a+i][3b+j] = fold_{tau active, ascending id} K^(tau)[3 la + i][3 lb + j]   (+ eps)

@@ -147,7 +147,7 @@ struct Ctx {
     int4 *tets = nullptr;   // T
     double2 *mat = nullptr; // T, (E, nu)
 
-    // pattern (a0)
+    // pattern
     int32_t *adj_ptr = nullptr;    // n + 1: first block of node a
     int32_t *adj = nullptr;        // nblocks: neighbour node of each block (ascending per node)
     int32_t *block_node = nullptr; // nblocks: owner node of each block

@@ -1,4 +1,4 @@
-// Full rebuild (a2 of Algorithm 1; the full_rebuild policy of Sec. 3.5): every value of the
+// Full rebuild (the full_rebuild policy of Sec. 3.5): every value of the
 // superset pattern folded from the element cache over the active mask, one lane per fold
 // entry (k_fold_flat), in FP64 or, under STA_POLICY_FIXED, as the fixed-point integer sum.
 // Fold definition and shared device code: sta_fold.cuh.

@@ -1,4 +1,4 @@
-// Streaming update (a3 of Algorithm 1, Sec. 3.2; the local_recompute policy of Sec. 3.5 made
+// Streaming update (Sec. 3.2, Algorithm 1; the local_recompute policy of Sec. 3.5 made
 // bitwise): apply a frame's mask changes, collect the fold units its edits touch, and re-fold
 // exactly those with the rebuild's operands, order and operations.  Also the mask-to-activity
 // pass of a full rebuild with a new mask.  Fold definition and shared device code:
