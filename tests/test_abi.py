@@ -134,6 +134,8 @@ int main(void) {
     if (strcmp(sta_status_string(STA_OK), "ok") != 0) return 4;
     if (sta_destroy(NULL) != STA_OK) return 5;
     if (sta_apply_edits(NULL, NULL, 0, NULL) != STA_EINVAL) return 6;
+    if (sta_set_rebuild_form(NULL, STA_REBUILD_ZERO_FILL) != STA_EINVAL) return 7;
+    if (sta_set_fold_depth(NULL, 6) != STA_EINVAL) return 8;
     puts("ok");
     return 0;
 }
